@@ -1,0 +1,212 @@
+/*
+ * fhash.h - C ABI of the F-Hash hot path for one GB300 GPU (sm_103a).
+ *
+ * F-Hash (feature-based multi-resolution Tesseract encoding, arXiv 2507.03836) learns an implicit
+ * neural representation of a time-varying volume: given the volume's dimensions, its time steps,
+ * a feature mask and a level schedule (Section 3.1, Section 3.2.1-3.2.2), every (x, y, z, t)
+ * query is encoded per level by locating its 4D cell, mapping the cell's 16 corners through the
+ * collision-free F-Hash of Eq. 9 to rows of compact per-level embedding tables and interpolating
+ * the F embeddings quadrilinearly (Section 3.2.4, Eqs. 10-12); a shallow MLP decodes the
+ * concatenated levels (Section 3.2.4, Section 4.2), trained with Adam (Section 5.1.3), and the
+ * trained model is rendered by sample streaming with adaptive ray marching (Section 3.3,
+ * Algorithm 1).
+ *
+ * Conventions shared by every call:
+ *  - Pointers marked "device" must be device memory of the model's GPU; pointers marked
+ *    "host or device" are inspected with cudaPointerGetAttributes and host memory is staged
+ *    through the model's own device buffers (pinned host memory avoids a bounce copy).
+ *  - The caller owns every input and output buffer.  The model owns its tables, MLP, Adam state,
+ *    occupancy grid and scratch buffers (device memory allocated by fhash_build and grown on
+ *    demand), and frees them in fhash_destroy.
+ *  - Work is enqueued on `stream` (a cudaStream_t; 0 = legacy default stream) and is
+ *    asynchronous unless stated otherwise.  Calls on one model must not overlap in time on
+ *    different streams: the model's scratch buffers are shared.
+ *  - Arguments are validated on the host before any launch; a bad argument returns FHASH_EINVAL
+ *    and launches nothing.  Nothing aborts or traps.  fhash_last_error() returns a
+ *    thread-local message for the last failing call on the calling thread.
+ *  - Coordinates are FBB-normalised points u in [0,1]^4, stored [n][4] float32 as (x, y, z, t):
+ *    u = 0 / 1 are the first / last vertex of the Feature Bounding Box on x, y, z and the first /
+ *    last time step on t.  Values outside [0,1] are clamped and NaN is read as 0 (a documented
+ *    behaviour, not an error).
+ *  - Table rows are stored level after level (coarsest first); within level l the row of grid
+ *    vertex (x, y, z, t) is base[l] + F-Hash^l(t, x, y, z) (Eq. 9), each row holding F values.
+ *    The flat parameter vector is [rows * F table values | MLP parameters], the MLP stored
+ *    layer by layer as W[out][in] followed by b[out].
+ */
+#ifndef FHASH_H
+#define FHASH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fhash_model fhash_model;
+typedef void* fhash_stream; /* cudaStream_t */
+
+typedef enum {
+    FHASH_OK = 0,
+    FHASH_EINVAL = 1,   /* invalid argument or unsupported configuration; nothing launched */
+    FHASH_ENOMEM = 2,   /* device or host allocation failed */
+    FHASH_ECUDA = 3,    /* a CUDA runtime call failed (message in fhash_last_error) */
+    FHASH_EDEVICE = 4,  /* a kernel reported an error through the model's device error word */
+    FHASH_ETIMEOUT = 5, /* a bounded device wait ran out */
+    FHASH_EBUSY = 6,    /* serving: no slot or memory budget free for the request right now */
+    FHASH_EIO = 7       /* checkpoint file could not be read or written */
+} fhash_status;
+
+enum { FHASH_FP32 = 0, FHASH_BF16 = 1 };
+enum { FHASH_SCHED_FOLD = 0, FHASH_SCHED_EXPLICIT = 1, FHASH_SCHED_GEOMETRIC = 2 };
+enum { FHASH_LEVELS_MAX = 0, FHASH_LEVELS_MIN = 1 };
+
+#define FHASH_MAX_LEVELS 24
+#define FHASH_MAX_HIDDEN 4
+
+/*
+ * Level schedule (Section 3.2.1-3.2.2).  All levels are listed COARSE -> FINE and count grid
+ * vertices per axis (a level with R vertices has R-1 cells; vertex j sits at u = j/(R-1)).
+ *  FHASH_SCHED_FOLD: the fold policy of Eqs. 4-8 on the Feature Bounding Box size S (Eq. 4),
+ *    L_d = ceil(log_fold S_d) (Eq. 5), L_s = max_d L_d (Eq. 6; levels_rule FHASH_LEVELS_MAX) or
+ *    min_d L_d (the level counts Table 3 prints; FHASH_LEVELS_MIN); each coarser level divides the
+ *    previous one by fold, rounding up, while it exceeds fold, else takes 2 (Eqs. 7-8).  The time
+ *    axis follows the same recursion from nt (Section 3.2.2).
+ *  FHASH_SCHED_EXPLICIT: res[0..n_levels-1] = (Rx, Ry, Rz, Rt) per level.
+ *  FHASH_SCHED_GEOMETRIC: R_l = floor(r0 * (r1/r0)^(l/(n_levels-1)) + 0.5) per axis in double.
+ */
+typedef struct {
+    int32_t mode;
+    int32_t fold;
+    int32_t levels_rule;
+    int32_t n_levels;
+    int32_t res[FHASH_MAX_LEVELS][4];
+    int32_t r0[4];
+    int32_t r1[4];
+} fhash_schedule;
+
+/*
+ * Model description for fhash_build (Section 3.1 and 3.2).
+ *  nx, ny, nz: volume vertex counts (>= 2); nt: number of time steps / key frames (>= 1).
+ *  mask: HOST pointer to [nt][nz][ny][nx] bytes, nonzero where a vertex belongs to the extracted
+ *    feature; NULL means every vertex.  It is read during the call only.  The build dilates it
+ *    by the 26-neighbourhood per time step (feature dilation, Section 3.1), takes the union of
+ *    the per-frame boxes as the Feature Bounding Box and keeps the dilated mask as the bit
+ *    occupancy grid used by the renderer.  An all-zero mask is FHASH_EINVAL.
+ *  F: embedding size, 1..8.  dtype: FHASH_FP32, or FHASH_BF16 (tables and MLP read as bf16
+ *    shadows of float32 master weights; MLP on the tensor cores with float32 accumulation).
+ *  mlp_hidden_layers (1..FHASH_MAX_HIDDEN) hidden layers of mlp_width (16, 32 or 64) with ReLU,
+ *    then a linear scalar output; every layer has a bias.
+ *  seed, init_range: tables start U(-init_range, init_range) (Section 3.2.4: uniform
+ *    initialisation); the MLP starts with PyTorch's nn.Linear bounds U(-1/sqrt(fan_in),
+ *    1/sqrt(fan_in)).  Values come from SplitMix64 used as a counter-based generator: element i
+ *    of the table is output i of SplitMix64 seeded with key = output 200 of SplitMix64 seeded
+ *    with `seed`, top 24 bits as U in [0,1), value = (float)(lo + (hi - lo) * U) in double; MLP
+ *    layer k uses streams 300 + 2k (W) and 301 + 2k (b).
+ */
+typedef struct {
+    int64_t nx, ny, nz, nt;
+    const uint8_t* mask;
+    fhash_schedule sched;
+    int32_t F;
+    int32_t dtype;
+    int32_t mlp_hidden_layers;
+    int32_t mlp_width;
+    uint64_t seed;
+    float init_range;
+} fhash_build_desc;
+
+/* Read-only description of a built model. */
+typedef struct {
+    int32_t n_levels, F, dtype, n_mlp_layers;
+    int32_t mlp_dims[FHASH_MAX_HIDDEN + 2];  /* L*F, width, ..., width, 1 */
+    int32_t res[FHASH_MAX_LEVELS][4];        /* (Rx, Ry, Rz, Rt), coarse -> fine */
+    uint64_t base[FHASH_MAX_LEVELS];         /* first row of each level */
+    uint64_t total_rows;                     /* sum of Rx*Ry*Rz*Rt */
+    uint64_t n_table_params;                 /* total_rows * F */
+    uint64_t n_mlp_params;
+    int64_t fbb_lo[3], fbb_size[3];          /* Feature Bounding Box, vertices, (x, y, z) */
+    int64_t nt;                              /* time steps of the occupancy grid */
+    int64_t step;                            /* Adam steps taken */
+    uint64_t device_bytes;                   /* device memory held by the model */
+} fhash_info;
+
+/* Adam hyper-parameters (Section 5.1.3 uses lr = 0.01).  PyTorch semantics: dense update of every
+ * parameter, bias correction, eps added to sqrt of the corrected second moment, no weight decay. */
+typedef struct {
+    float lr, beta1, beta2, eps;
+} fhash_adam;
+
+/*
+ * Build a model (Section 3.1 feature dilation, bounding box and temporal fusion, occupancy grid;
+ * Section 3.2.1-3.2.3 schedule and table sizing) on the current CUDA device and initialise its
+ * parameters.  Synchronous: returns after the model is ready.  *out receives the model (owned by
+ * the caller, released with fhash_destroy).  Errors: FHASH_EINVAL for bad dimensions, schedule,
+ * F, MLP shape or an empty mask; FHASH_ENOMEM if the device cannot hold tables, gradients and the
+ * two Adam moments (4 x rows x F x 4 bytes, plus bf16 shadows in FHASH_BF16).
+ */
+fhash_status fhash_build(const fhash_build_desc* desc, fhash_stream stream, fhash_model** out);
+
+/* Release every device and host resource of the model (synchronises the device first). */
+void fhash_destroy(fhash_model* model);
+
+/* Thread-local text of the last error returned to this thread ("" if none). */
+const char* fhash_last_error(void);
+
+fhash_status fhash_get_info(const fhash_model* model, fhash_info* out);
+
+/*
+ * Encoding steps 1-3 of Section 3.2.4 for inspection: per sample and level, the 16 corner rows
+ * through Eq. 9 (with level base) and their quadrilinear weights (Eqs. 10-12), corner index
+ * c = i + 2j + 4k + 8s (i, j, k: upper corner on x, y, z; s = 1 for t_Next).
+ *  coords: device [n][4]; rows: device [n][L][16] uint64; weights: device [n][L][16] float or NULL.
+ */
+fhash_status fhash_lookup(fhash_model* model, const float* coords, int64_t n, uint64_t* rows, float* weights,
+                          fhash_stream stream);
+
+/* Multi-resolution Tesseract encoding (Section 3.2.4, Eqs. 9-12): enc[n][L*F] float32, level 0
+ * (coarsest) first.  coords: device [n][4]; enc: device.  n = 0 is a no-op. */
+fhash_status fhash_encode(fhash_model* model, const float* coords, int64_t n, float* enc, fhash_stream stream);
+
+/* Encoding fused with the MLP decoder (Section 3.2.4): out[n] float32.
+ * coords: host or device [n][4]; out: host or device [n]. */
+fhash_status fhash_forward(fhash_model* model, const float* coords, int64_t n, float* out, fhash_stream stream);
+
+/*
+ * Forward + MSE loss + backward without the optimiser: leaves d(loss)/d(parameter) in the model's
+ * gradient buffer (read it with fhash_read_state(FHASH_STATE_GRAD)).  loss = mean((y - target)^2)
+ * reduced in float64 (host or device double*, may be NULL).  coords, target: host or device.
+ */
+fhash_status fhash_compute_grads(fhash_model* model, const float* coords, const float* target, int64_t n,
+                                 double* loss, fhash_stream stream);
+
+/* One Adam step (Section 5.1.3) over every parameter using the gradient buffer, which it then
+ * clears to zero; increments the step count. */
+fhash_status fhash_apply_adam(fhash_model* model, const fhash_adam* adam, fhash_stream stream);
+
+/* One full training step: fhash_compute_grads followed by fhash_apply_adam. */
+fhash_status fhash_train_step(fhash_model* model, const float* coords, const float* target, int64_t n,
+                              const fhash_adam* adam, double* loss, fhash_stream stream);
+
+enum { FHASH_STATE_PARAM = 0, FHASH_STATE_GRAD = 1, FHASH_STATE_ADAM_M = 2, FHASH_STATE_ADAM_V = 3 };
+
+/* Copy n float32 elements starting at flat element `offset` of a state vector ([table | MLP]
+ * layout above) to / from `buf` (host or device).  Writing FHASH_STATE_PARAM refreshes the bf16
+ * shadows of FHASH_BF16 models.  Offsets beyond the vector are FHASH_EINVAL. */
+fhash_status fhash_read_state(fhash_model* model, int32_t which, uint64_t offset, uint64_t n, float* buf,
+                              fhash_stream stream);
+fhash_status fhash_write_state(fhash_model* model, int32_t which, uint64_t offset, uint64_t n, const float* buf,
+                               fhash_stream stream);
+
+/* Occupancy grid of time step t (Section 3.1) over the Feature Bounding Box as bytes 0/1,
+ * out: host or device [Sz][Sy][Sx]. */
+fhash_status fhash_read_occupancy(fhash_model* model, int64_t t, uint8_t* out, fhash_stream stream);
+
+/* Synchronise `stream` and report FHASH_EDEVICE if a kernel of this model raised the device
+ * error word since the last check (the word is then cleared). */
+fhash_status fhash_check(fhash_model* model, fhash_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FHASH_H */
