@@ -1,0 +1,284 @@
+#!/usr/bin/env python
+"""Benchmark of the F-Hash training step on one GB300 (replicas over N GPUs).
+
+One step = one full pass of the training hot path over one batch of 2^18 synthetic samples of the
+256^3 x 64 workload: encode (16 levels, F=2) -> MLP 2x64 forward -> MSE -> MLP backward -> table
+scatter-add -> dense Adam over all 3.56e9 parameters.  Inputs are resident in HBM before the timed
+region; the 57 GB of training state streamed every step is far larger than L2, so no extra flush is
+needed.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload large|small]
+"""
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")  # the oracle legs are timed single-threaded
+
+import argparse
+import json
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "train samples/s (enc+MLP fwd+bwd); render p50/p99 ms; BF16 vs FP32 @PSNR"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.rows, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows if len(r) >= 9 for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def _workload(name):
+    from synth import workloads
+    return workloads.LARGE if name == "large" else workloads.SMALL
+
+
+def _levels(w):
+    from oracle import schedule
+    s = w["schedule"]
+    if s["mode"] == "geometric":
+        return schedule.geometric_schedule(s["r0"], s["r1"], s["n_levels"])
+    return [list(r) for r in s["res"]]
+
+
+def oracle_step_sample(w, n_sample, seed=0, adam_slice=1 << 20):
+    """Times the oracle on a bounded sample of one step: encode -> MLP -> MSE -> backward -> scatter for
+    n_sample samples, plus dense Adam on a slice of adam_slice parameters.  Returns (seconds for the
+    whole step extrapolated to the full batch and parameter count, description)."""
+    import synth
+    from oracle import adam, rng, schedule, train
+    lv = _levels(w)
+    b, rows = schedule.bases(lv)
+    F = w["F"]
+    dims = [len(lv) * F] + [w["width"]] * w["hidden"] + [1]
+    n_params = rows * F + sum(dims[k] * dims[k + 1] + dims[k + 1] for k in range(len(dims) - 1))
+    table = rng.InitTable(seed, F, w["init_range"])
+    p = synth.init_mlp(seed, dims).astype(np.float64)
+    c = synth.coords(1000 + seed, n_sample)
+    tgt = synth.uniform(seed, 77, n_sample)
+    t0 = time.perf_counter()
+    train.loss_and_grads(lv, b, F, dims, table, p, c, tgt)
+    t1 = time.perf_counter()
+    z = np.zeros(adam_slice)
+    P = synth.uniform(seed, 78, adam_slice).astype(np.float64)
+    adam.step(P, P * 1e-3, z, z, 1)
+    t2 = time.perf_counter()
+    full = (t1 - t0) * w["batch"] / n_sample + (t2 - t1) * n_params / adam_slice
+    desc = ("oracle (numpy FP64, 1 thread): encode+MLP+MSE+backward+scatter on %d of %d samples and dense Adam on "
+            "%d of %d parameters, extrapolated linearly to one full step" % (n_sample, w["batch"], adam_slice, n_params))
+    return full, desc
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle as it stands, on the host cores, bounded samples per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = _workload(args.workload)
+    n_sample = 4096
+    for k in range(args.warmup):
+        oracle_step_sample(w, n_sample, seed=k)
+    times = []
+    desc = ""
+    for k in range(args.steps):
+        t, desc = oracle_step_sample(w, n_sample, seed=100 + k)
+        times.append(t)
+    sec = float(np.mean(times))
+    v = w["batch"] / sec
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "global_batch": w["batch"]},
+        "cpu_baseline": {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large", choices=["large", "small"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import synth
+    import paper_2507_03836_gb300 as fh
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    w = _workload(args.workload)
+    from synth import workloads
+    t0 = time.time()
+    field, mask = workloads.make_field_and_mask(w)
+    nx, ny, nz, nt = w["dims"]
+    model = fh.fhash_build(nx, ny, nz, nt, mask=mask, schedule=fh.make_schedule(**w["schedule"]), F=w["F"],
+                           mlp_hidden_layers=w["hidden"], mlp_width=w["width"], seed=1 + rank,
+                           init_range=w["init_range"])
+    del mask
+    info = fh.fhash_get_info(model)
+    setup_s = time.time() - t0
+
+    # batches: coords uniform in [0,1]^4 (FBB-normalised), targets sampled from the field
+    B = w["batch"]
+    nb = args.warmup + args.steps
+    coords_h = [synth.coords(10_000 + 100 * rank + k, B) for k in range(nb)]
+    tgt_h = [synth.sample(field, info["fbb_lo"], info["fbb_size"], c) for c in coords_h]
+    coords_d = [torch.from_numpy(c).cuda() for c in coords_h]
+    tgt_d = [torch.from_numpy(t).cuda() for t in tgt_h]
+    loss_d = torch.zeros(nb, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    hp = w["adam"]
+
+    for k in range(args.warmup):
+        fh.fhash_compute_grads(model, coords_d[k], tgt_d[k], loss_d[k:k + 1])
+        fh.fhash_apply_adam(model, hp)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    e_start.record(st)
+    for k in range(K):
+        i = args.warmup + k
+        ev[k][0].record(st)
+        fh.fhash_compute_grads(model, coords_d[i], tgt_d[i], loss_d[i:i + 1])
+        ev[k][1].record(st)
+        fh.fhash_apply_adam(model, hp)
+        ev[k][2].record(st)
+    e_end.record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed = e_start.elapsed_time(e_end) / 1e3
+    if dist:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    grads_ms = float(np.mean([ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]))
+    adam_ms = float(np.mean([ev[k][1].elapsed_time(ev[k][2]) for k in range(K)]))
+    losses = loss_d.cpu().numpy()
+
+    # end to end through the public API: host (pinned) inputs copied in, loss read back, every step
+    pin_c = [torch.from_numpy(c).pin_memory() for c in coords_h[:K]]
+    pin_t = [torch.from_numpy(t).pin_memory() for t in tgt_h[:K]]
+    lh = np.zeros(1, np.float64)
+    for k in range(min(2, K)):
+        fh.fhash_train_step(model, pin_c[k].numpy(), pin_t[k].numpy(), hp, lh)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t1 = time.perf_counter()
+    for k in range(K):
+        fh.fhash_train_step(model, pin_c[k].numpy(), pin_t[k].numpy(), hp, lh)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t1
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    fh.fhash_check(model)
+
+    n_params = info["n_table_params"] + info["n_mlp_params"]
+    peaks, peak_kind = _peaks()
+    adam_bytes = 32.0 * n_params  # read p, g, m, v; write p, m, v and the cleared g
+    achieved = adam_bytes / (adam_ms / 1e3) / 1e9
+    value = world * B * K / elapsed
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": elapsed / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w["name"], "global_batch": B * world, "levels": len(info["res"]), "F": info["F"],
+                   "mlp": info["mlp_dims"], "table_params": info["n_table_params"],
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (%.1f GB of training state streamed per step)" % (adam_bytes / 1e9)},
+        "phases_ms": {"encode_mlp_fwd_bwd_scatter": grads_ms, "adam": adam_ms},
+        "gpu_launches": K * (4 + 2 * (w["hidden"] + 1)),
+        "roofline": {"kernel": "k_adam", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "peak_source": peak_kind, "bytes_per_launch": adam_bytes},
+        "clocks": clk,
+        "e2e": {"value": world * B * K / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": B * 20,
+                "d2h_bytes_per_step": 8},
+        "loss_first_last": [float(losses[0]), float(losses[-1])],
+        "setup_s": setup_s,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t, desc = oracle_step_sample(w, 32768, adam_slice=1 << 25)
+        out["cpu_baseline"] = {"value": B / t, "unit": "samples/s", "cores": 1, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,229 @@
+"""Python binding of libfhash (include/fhash.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does nothing but
+convert arguments (torch CUDA tensors or numpy host arrays -> raw pointers, the current
+torch stream -> cudaStream_t) and turn a non-zero status into FHashError.  All
+computation runs in the CUDA library; if libfhash.so is missing, importing this package
+fails - there is no fallback.  Build it with ``python -m paper_2507_03836_gb300.build``.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfhash.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libfhash.so is not built (run python -m paper_2507_03836_gb300.build): %s" % LIB_PATH)
+_lib = ctypes.CDLL(LIB_PATH)
+
+MAX_LEVELS = 24
+MAX_HIDDEN = 4
+FP32, BF16 = 0, 1
+SCHED_FOLD, SCHED_EXPLICIT, SCHED_GEOMETRIC = 0, 1, 2
+LEVELS_MAX, LEVELS_MIN = 0, 1
+STATE_PARAM, STATE_GRAD, STATE_ADAM_M, STATE_ADAM_V = 0, 1, 2, 3
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EDEVICE", 5: "ETIMEOUT", 6: "EBUSY", 7: "EIO"}
+
+
+class FHashError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class fhash_schedule(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("fold", ctypes.c_int32), ("levels_rule", ctypes.c_int32),
+                ("n_levels", ctypes.c_int32), ("res", (ctypes.c_int32 * 4) * MAX_LEVELS),
+                ("r0", ctypes.c_int32 * 4), ("r1", ctypes.c_int32 * 4)]
+
+
+class fhash_build_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64), ("nt", ctypes.c_int64),
+                ("mask", ctypes.c_void_p), ("sched", fhash_schedule), ("F", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("mlp_hidden_layers", ctypes.c_int32), ("mlp_width", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("init_range", ctypes.c_float)]
+
+
+class fhash_info(ctypes.Structure):
+    _fields_ = [("n_levels", ctypes.c_int32), ("F", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("n_mlp_layers", ctypes.c_int32), ("mlp_dims", ctypes.c_int32 * (MAX_HIDDEN + 2)),
+                ("res", (ctypes.c_int32 * 4) * MAX_LEVELS), ("base", ctypes.c_uint64 * MAX_LEVELS),
+                ("total_rows", ctypes.c_uint64), ("n_table_params", ctypes.c_uint64),
+                ("n_mlp_params", ctypes.c_uint64), ("fbb_lo", ctypes.c_int64 * 3), ("fbb_size", ctypes.c_int64 * 3),
+                ("nt", ctypes.c_int64), ("step", ctypes.c_int64), ("device_bytes", ctypes.c_uint64)]
+
+
+class fhash_adam(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float)]
+
+
+_vp, _i64, _u64, _i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32
+_SIGS = {
+    "fhash_build": [ctypes.POINTER(fhash_build_desc), _vp, ctypes.POINTER(_vp)],
+    "fhash_destroy": [_vp],
+    "fhash_get_info": [_vp, ctypes.POINTER(fhash_info)],
+    "fhash_lookup": [_vp, _vp, _i64, _vp, _vp, _vp],
+    "fhash_encode": [_vp, _vp, _i64, _vp, _vp],
+    "fhash_forward": [_vp, _vp, _i64, _vp, _vp],
+    "fhash_compute_grads": [_vp, _vp, _vp, _i64, _vp, _vp],
+    "fhash_apply_adam": [_vp, ctypes.POINTER(fhash_adam), _vp],
+    "fhash_train_step": [_vp, _vp, _vp, _i64, ctypes.POINTER(fhash_adam), _vp, _vp],
+    "fhash_read_state": [_vp, _i32, _u64, _u64, _vp, _vp],
+    "fhash_write_state": [_vp, _i32, _u64, _u64, _vp, _vp],
+    "fhash_read_occupancy": [_vp, _i64, _vp, _vp],
+    "fhash_check": [_vp, _vp],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = None if _name == "fhash_destroy" else ctypes.c_int
+_lib.fhash_last_error.restype = ctypes.c_char_p
+_lib.fhash_last_error.argtypes = []
+
+
+def fhash_last_error():
+    return _lib.fhash_last_error().decode()
+
+
+def _ok(status):
+    if status != 0:
+        raise FHashError(status, fhash_last_error())
+
+
+def _ptr(x):
+    """Raw pointer of a torch tensor (device or host) or a numpy array; None -> NULL."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError("expected a torch tensor or numpy array, got %r" % type(x))
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+
+
+class Model:
+    """Owning handle of an fhash_model*; released by fhash_destroy."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            _lib.fhash_destroy(self.handle)
+            self.handle = None
+
+    @property
+    def _as_parameter_(self):
+        return self.handle
+
+
+def make_schedule(mode="explicit", res=None, fold=2, levels_rule=LEVELS_MAX, n_levels=0, r0=None, r1=None):
+    s = fhash_schedule()
+    s.mode = {"fold": SCHED_FOLD, "explicit": SCHED_EXPLICIT, "geometric": SCHED_GEOMETRIC}[mode]
+    s.fold = fold
+    s.levels_rule = levels_rule
+    if res is not None:
+        s.n_levels = len(res)
+        for l, R in enumerate(res):
+            for d in range(4):
+                s.res[l][d] = int(R[d])
+    else:
+        s.n_levels = n_levels
+    for d in range(4):
+        s.r0[d] = int(r0[d]) if r0 is not None else 0
+        s.r1[d] = int(r1[d]) if r1 is not None else 0
+    return s
+
+
+def fhash_build(nx, ny, nz, nt, mask=None, schedule=None, F=2, dtype=FP32, mlp_hidden_layers=2, mlp_width=64,
+                seed=0, init_range=1e-4, stream=None):
+    """fhash_build: mask is a host numpy uint8 array [nt][nz][ny][nx] or None."""
+    d = fhash_build_desc()
+    d.nx, d.ny, d.nz, d.nt = int(nx), int(ny), int(nz), int(nt)
+    if mask is not None:
+        mask = np.ascontiguousarray(mask, np.uint8)
+        if mask.shape != (nt, nz, ny, nx):
+            raise ValueError("mask shape %s != (nt, nz, ny, nx)" % (mask.shape,))
+    d.mask = _ptr(mask)
+    d.sched = schedule if schedule is not None else make_schedule()
+    d.F, d.dtype = int(F), int(dtype)
+    d.mlp_hidden_layers, d.mlp_width = int(mlp_hidden_layers), int(mlp_width)
+    d.seed, d.init_range = int(seed), float(init_range)
+    h = _vp()
+    _ok(_lib.fhash_build(ctypes.byref(d), _stream(stream), ctypes.byref(h)))
+    return Model(h.value)
+
+
+def fhash_get_info(model):
+    info = fhash_info()
+    _ok(_lib.fhash_get_info(model.handle, ctypes.byref(info)))
+    L = info.n_levels
+    return dict(n_levels=L, F=info.F, dtype=info.dtype, mlp_dims=list(info.mlp_dims[:info.n_mlp_layers + 1]),
+                res=[list(info.res[l]) for l in range(L)], base=[int(info.base[l]) for l in range(L)],
+                total_rows=int(info.total_rows), n_table_params=int(info.n_table_params),
+                n_mlp_params=int(info.n_mlp_params), fbb_lo=list(info.fbb_lo), fbb_size=list(info.fbb_size),
+                nt=int(info.nt), step=int(info.step), device_bytes=int(info.device_bytes))
+
+
+def fhash_lookup(model, coords, rows, weights=None, stream=None):
+    _ok(_lib.fhash_lookup(model.handle, _ptr(coords), coords.shape[0], _ptr(rows), _ptr(weights), _stream(stream)))
+
+
+def fhash_encode(model, coords, enc, stream=None):
+    _ok(_lib.fhash_encode(model.handle, _ptr(coords), coords.shape[0], _ptr(enc), _stream(stream)))
+
+
+def fhash_forward(model, coords, out, stream=None):
+    _ok(_lib.fhash_forward(model.handle, _ptr(coords), coords.shape[0], _ptr(out), _stream(stream)))
+
+
+def _adam(adam):
+    a = fhash_adam()
+    a.lr, a.beta1, a.beta2, a.eps = adam if adam is not None else (1e-2, 0.9, 0.99, 1e-8)
+    return a
+
+
+def fhash_compute_grads(model, coords, target, loss=None, stream=None):
+    _ok(_lib.fhash_compute_grads(model.handle, _ptr(coords), _ptr(target), coords.shape[0], _ptr(loss),
+                                 _stream(stream)))
+
+
+def fhash_apply_adam(model, adam=None, stream=None):
+    a = _adam(adam)
+    _ok(_lib.fhash_apply_adam(model.handle, ctypes.byref(a), _stream(stream)))
+
+
+def fhash_train_step(model, coords, target, adam=None, loss=None, stream=None):
+    a = _adam(adam)
+    _ok(_lib.fhash_train_step(model.handle, _ptr(coords), _ptr(target), coords.shape[0], ctypes.byref(a),
+                              _ptr(loss), _stream(stream)))
+
+
+def fhash_read_state(model, which, offset, buf, stream=None):
+    n = buf.numel() if hasattr(buf, "numel") else buf.size
+    _ok(_lib.fhash_read_state(model.handle, which, int(offset), int(n), _ptr(buf), _stream(stream)))
+
+
+def fhash_write_state(model, which, offset, buf, stream=None):
+    n = buf.numel() if hasattr(buf, "numel") else buf.size
+    _ok(_lib.fhash_write_state(model.handle, which, int(offset), int(n), _ptr(buf), _stream(stream)))
+
+
+def fhash_read_occupancy(model, t, out, stream=None):
+    _ok(_lib.fhash_read_occupancy(model.handle, int(t), _ptr(out), _stream(stream)))
+
+
+def fhash_check(model, stream=None):
+    _ok(_lib.fhash_check(model.handle, _stream(stream)))

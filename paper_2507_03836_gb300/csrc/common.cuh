@@ -1,0 +1,166 @@
+// Internal definitions shared by the library's translation units (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "fhash.h"
+
+namespace fh {
+
+// ------------------------------------------------------------------ errors
+fhash_status set_error(fhash_status s, const char* fmt, ...);
+fhash_status cuda_error(cudaError_t e, const char* what);
+#define FH_CUDA(call)                                                   \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return ::fh::cuda_error(e_, #call);      \
+    } while (0)
+#define FH_TRY(call)                                                    \
+    do {                                                                \
+        fhash_status s_ = (call);                                       \
+        if (s_ != FHASH_OK) return s_;                                  \
+    } while (0)
+
+// ------------------------------------------------------------------ level table
+// One level of the Tesseract grid.  Rows of the level: base + t*st + z*sz + y*sy + x (Eq. 9).
+struct Level {
+    int32_t R[4];     // vertices per axis (x, y, z, t)
+    float Rm1[4];     // (float)(R - 1), the scale of the float32 cell step
+    uint32_t sy, sz;  // Rx, Rx*Ry
+    uint64_t st;      // Rx*Ry*Rz
+    uint64_t base;    // first row of the level
+};
+
+struct Levels {
+    int32_t L, F;
+    Level lv[FHASH_MAX_LEVELS];
+};
+
+// MLP shape: dims[0] = L*F, dims[1..nh] = width, dims[nh+1] = 1.  Flat offsets into the MLP block.
+struct MlpShape {
+    int32_t in, width, nh;  // nh hidden layers
+    int32_t n_params;
+    int32_t w_off[FHASH_MAX_HIDDEN + 1], b_off[FHASH_MAX_HIDDEN + 1];
+};
+
+// ------------------------------------------------------------------ model
+struct Scratch {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace fh
+
+struct fhash_model {
+    int device = 0;
+    fhash_build_desc desc{};
+    fh::Levels lv{};
+    fh::MlpShape mlp{};
+    uint64_t total_rows = 0, n_table = 0, n_params = 0;  // n_params = n_table + mlp params
+    int64_t fbb_lo[3]{}, fbb_size[3]{};
+    int64_t nt = 1;
+    int64_t step = 0;
+
+    // flat state vectors [n_params] float32 (table values then MLP)
+    float* param = nullptr;
+    float* grad = nullptr;
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
+    __nv_bfloat16* shadow = nullptr;  // bf16 copy of param (FHASH_BF16 only)
+
+    // occupancy over the FBB: bricks of 8^3 voxels, 16 x u32 words each (Morton order inside)
+    uint32_t* occ = nullptr;
+    uint8_t* occ_any = nullptr;  // per brick: any bit set
+    int64_t nbx = 0, nby = 0, nbz = 0;
+
+    int* err_word = nullptr;  // device error word (0 = ok)
+
+    // scratch (grown on demand; owned by the model)
+    fh::Scratch s_coords, s_target, s_out, s_acts, s_gacts, s_partial, s_loss, s_misc;
+    uint64_t device_bytes = 0;
+};
+
+namespace fh {
+
+fhash_status grow(fhash_model* m, Scratch& s, size_t bytes);
+bool is_device_ptr(const void* p);
+// Copies a host-or-device input into `s` when it is host memory; returns the device pointer to use.
+fhash_status stage_in(fhash_model* m, Scratch& s, const void* p, size_t bytes, cudaStream_t st, const void** dev);
+
+// ------------------------------------------------------------------ device helpers
+// Float32 cell step (Section 3.2.4 steps 1-2): c = clamp(floor(u*(R-1)), 0, R-2), w = u*(R-1) - c,
+// upper corner min(c+1, R-1).  u is clamped to [0,1] first, NaN -> 0.  Round-to-nearest multiply,
+// no contraction, so rows are bit-identical to any IEEE float32 evaluation of the same steps.
+__device__ __forceinline__ void cell(float u, int R, float Rm1, int& c, int& d1, float& w) {
+    u = fminf(fmaxf(u, 0.0f), 1.0f);
+    float p = __fmul_rn(u, Rm1);
+    int ci = (int)floorf(p);
+    ci = min(ci, R - 2);
+    ci = max(ci, 0);
+    w = __fsub_rn(p, (float)ci);
+    c = ci;
+    d1 = (ci + 1 <= R - 1) ? 1 : 0;  // 0 only on single-vertex axes
+}
+
+// Per-level corner geometry of one sample: base row (lower corner at t_Previous), the row offsets of
+// the upper corners on each axis, and the four axis fractions.
+struct Corners {
+    uint64_t r0;
+    uint32_t ox, oy, oz;
+    uint64_t ot;
+    float wx, wy, wz, wt;
+};
+
+__device__ __forceinline__ Corners corners(const Level& L, float4 u) {
+    int cx, cy, cz, ct, dx, dy, dz, dt;
+    Corners k;
+    cell(u.x, L.R[0], L.Rm1[0], cx, dx, k.wx);
+    cell(u.y, L.R[1], L.Rm1[1], cy, dy, k.wy);
+    cell(u.z, L.R[2], L.Rm1[2], cz, dz, k.wz);
+    cell(u.w, L.R[3], L.Rm1[3], ct, dt, k.wt);
+    k.r0 = L.base + (uint64_t)ct * L.st + (uint64_t)cz * L.sz + (uint64_t)cy * L.sy + (uint64_t)cx;
+    k.ox = dx;
+    k.oy = dy ? L.sy : 0u;
+    k.oz = dz ? L.sz : 0u;
+    k.ot = dt ? L.st : 0ull;
+    return k;
+}
+
+__device__ __forceinline__ void raise_error(int* word, int code) {
+    if (word) atomicCAS(word, 0, code);
+}
+
+// Vector reductions to global memory (no return value); addresses aligned to the vector size.
+__device__ __forceinline__ void red_add(float* a, float v) { atomicAdd(a, v); }
+__device__ __forceinline__ void red_add2(float* a, float x, float y) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(a), "f"(x), "f"(y) : "memory");
+}
+__device__ __forceinline__ void red_add4(float* a, float x, float y, float z, float w) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(a), "f"(x), "f"(y), "f"(z), "f"(w)
+                 : "memory");
+}
+
+inline int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+// ------------------------------------------------------------------ launchers (encode.cu)
+fhash_status launch_lookup(fhash_model* m, const float* coords, int64_t n, uint64_t* rows, float* w, cudaStream_t st);
+fhash_status launch_encode(fhash_model* m, const float* coords, int64_t n, float* enc, cudaStream_t st);
+fhash_status launch_forward(fhash_model* m, const float* coords, int64_t n, float* out, cudaStream_t st);
+fhash_status launch_grads(fhash_model* m, const float* coords, const float* target, int64_t n, double* loss_dev,
+                          cudaStream_t st);
+fhash_status launch_adam(fhash_model* m, const fhash_adam* a, cudaStream_t st);
+fhash_status refresh_shadow(fhash_model* m, uint64_t off, uint64_t n, cudaStream_t st);
+
+}  // namespace fh

@@ -1,0 +1,339 @@
+// Host glue and small kernels of the float32 path: encode / lookup launches, MLP weight gradients,
+// loss reduction and Adam (Section 5.1.3), and the C-ABI entry points for encode, forward and training.
+#include <math.h>
+
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace fh {
+
+// Encoding steps 1-3 (Section 3.2.4) for inspection: 16 corner rows (Eq. 9) and weights per sample-level.
+__global__ void k_lookup(const __grid_constant__ Levels lv, const float* __restrict__ coords, int64_t n,
+                         uint64_t* __restrict__ rows, float* __restrict__ w) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * lv.L) return;
+    int64_t s = idx / lv.L;
+    int l = (int)(idx % lv.L);
+    Corners k = corners(lv.lv[l], load_coord(coords, s));
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+        rows[idx * 16 + c] = corner_row(k, c);
+        if (w) w[idx * 16 + c] = corner_weight(k, c);
+    }
+}
+// Weight gradient of one layer over a chunk of samples: partial[chunk][e], e < fo*fi -> dW[o][i],
+// e >= fo*fi -> db[o].  a: [fi][n] column-major activations, d: [fo][n] deltas.
+__global__ void k_dw_partial(const float* __restrict__ a, const float* __restrict__ d, int fi, int fo, int64_t n,
+                             int64_t chunk, float* __restrict__ partial) {
+    constexpr int TS = 32;
+    __shared__ float sa[64][TS + 1];
+    __shared__ float sd[64][TS + 1];
+    const int ne = fo * fi + fo;
+    const int64_t n0 = blockIdx.x * chunk, n1 = min(n, n0 + chunk);
+    float acc[17];
+#pragma unroll
+    for (int j = 0; j < 17; ++j) acc[j] = 0.0f;
+    for (int64_t t0 = n0; t0 < n1; t0 += TS) {
+        __syncthreads();
+        for (int q = threadIdx.x; q < (fi + fo) * TS; q += blockDim.x) {
+            int r = q / TS, c = q % TS;
+            int64_t s = t0 + c;
+            float v = 0.0f;
+            if (s < n1) v = (r < fi) ? a[(int64_t)r * n + s] : d[(int64_t)(r - fi) * n + s];
+            if (r < fi) sa[r][c] = v; else sd[r - fi][c] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 17; ++j) {
+            int e = threadIdx.x + j * blockDim.x;
+            if (e < ne) {
+                float x = acc[j];
+                if (e < fo * fi) {
+                    int o = e / fi, i = e % fi;
+#pragma unroll 8
+                    for (int c = 0; c < TS; ++c) x = fmaf(sd[o][c], sa[i][c], x);
+                } else {
+                    int o = e - fo * fi;
+#pragma unroll 8
+                    for (int c = 0; c < TS; ++c) x += sd[o][c];
+                }
+                acc[j] = x;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 17; ++j) {
+        int e = threadIdx.x + j * blockDim.x;
+        if (e < ne) partial[(int64_t)blockIdx.x * ne + e] = acc[j];
+    }
+}
+
+// grad[e] += sum over chunks of partial[c][e] (fixed order: deterministic).
+__global__ void k_dw_reduce(const float* __restrict__ partial, int nchunk, int ne, float* __restrict__ grad) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    float s = 0.0f;
+    for (int c = 0; c < nchunk; ++c) s += partial[(int64_t)c * ne + e];
+    grad[e] += s;
+}
+
+// loss = (sum of per-block partial sums of squared residuals) / n, float64, fixed order.
+__global__ void k_loss(const double* __restrict__ partial, int nb, int64_t n, double* __restrict__ loss) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partial[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = red[0] / (double)n;
+}
+
+// Adam (PyTorch semantics, dense): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+// p -= (lr / bc1) * m / (sqrt(v) / sqrt(bc2) + eps); the gradient is cleared for the next step.
+// Streams p, g, m, v once: 16 bytes read + 16 bytes written per parameter.
+__device__ __forceinline__ void adam1(float& p, float& g, float& m, float& v, float b1, float b2, float step_size,
+                                      float sqrt_bc2, float eps) {
+    m = fmaf(b1, m, (1.0f - b1) * g);
+    v = fmaf(b2, v, (1.0f - b2) * (g * g));
+    float denom = __fdiv_rn(sqrtf(v), sqrt_bc2) + eps;
+    p = p - step_size * __fdiv_rn(m, denom);
+    g = 0.0f;
+}
+
+__global__ void __launch_bounds__(256) k_adam(float* __restrict__ P, float* __restrict__ G, float* __restrict__ M,
+                                              float* __restrict__ V, uint64_t n, float b1, float b2, float step_size,
+                                              float sqrt_bc2, float eps, __nv_bfloat16* __restrict__ shadow) {
+    const uint64_t n4 = n / 4;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    float4* P4 = reinterpret_cast<float4*>(P);
+    float4* G4 = reinterpret_cast<float4*>(G);
+    float4* M4 = reinterpret_cast<float4*>(M);
+    float4* V4 = reinterpret_cast<float4*>(V);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n4; i += stride) {
+        float4 p = __ldcs(P4 + i), g = __ldcs(G4 + i), m = __ldcs(M4 + i), v = __ldcs(V4 + i);
+        adam1(p.x, g.x, m.x, v.x, b1, b2, step_size, sqrt_bc2, eps);
+        adam1(p.y, g.y, m.y, v.y, b1, b2, step_size, sqrt_bc2, eps);
+        adam1(p.z, g.z, m.z, v.z, b1, b2, step_size, sqrt_bc2, eps);
+        adam1(p.w, g.w, m.w, v.w, b1, b2, step_size, sqrt_bc2, eps);
+        __stcs(P4 + i, p);
+        __stcs(G4 + i, g);
+        __stcs(M4 + i, m);
+        __stcs(V4 + i, v);
+        if (shadow) {
+            __nv_bfloat162* s2 = reinterpret_cast<__nv_bfloat162*>(shadow) + 2 * i;
+            s2[0] = __floats2bfloat162_rn(p.x, p.y);
+            s2[1] = __floats2bfloat162_rn(p.z, p.w);
+        }
+    }
+    for (uint64_t i = 4 * n4 + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        float p = P[i], g = G[i], m = M[i], v = V[i];
+        adam1(p, g, m, v, b1, b2, step_size, sqrt_bc2, eps);
+        P[i] = p; G[i] = g; M[i] = m; V[i] = v;
+        if (shadow) shadow[i] = __float2bfloat16_rn(p);
+    }
+}
+
+cudaError_t run_fused_any(int F, int which, const FusedArgs& a);
+
+static cudaError_t dispatch_fused(fhash_model* m, int which, FusedArgs& a) {
+    a.lv = &m->lv;
+    a.sh = &m->mlp;
+    a.T = m->param;
+    a.G = m->grad;
+    a.Pm = m->param + m->n_table;
+    int64_t blocks = (a.n + TB - 1) / TB;
+    a.grid = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)num_sms() * 16));
+    return run_fused_any(m->lv.F, which, a);
+}
+
+fhash_status launch_lookup(fhash_model* m, const float* coords, int64_t n, uint64_t* rows, float* w, cudaStream_t st) {
+    int64_t tot = n * m->lv.L;
+    k_lookup<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(m->lv, coords, n, rows, w);
+    FH_CUDA(cudaGetLastError());
+    return FHASH_OK;
+}
+
+fhash_status launch_encode(fhash_model* m, const float* coords, int64_t n, float* enc, cudaStream_t st) {
+    int64_t tot = n * m->lv.L;
+    unsigned g = (unsigned)((tot + 255) / 256);
+    switch (m->lv.F) {
+        case 1: k_encode<1><<<g, 256, 0, st>>>(m->lv, m->param, coords, n, enc); break;
+        case 2: k_encode<2><<<g, 256, 0, st>>>(m->lv, m->param, coords, n, enc); break;
+        case 4: k_encode<4><<<g, 256, 0, st>>>(m->lv, m->param, coords, n, enc); break;
+        case 8: k_encode<8><<<g, 256, 0, st>>>(m->lv, m->param, coords, n, enc); break;
+        default: return set_error(FHASH_EINVAL, "F=%d has no kernel (supported: 1, 2, 4, 8)", m->lv.F);
+    }
+    FH_CUDA(cudaGetLastError());
+    return FHASH_OK;
+}
+
+fhash_status launch_forward(fhash_model* m, const float* coords, int64_t n, float* out, cudaStream_t st) {
+    FusedArgs a{};
+    a.coords = coords;
+    a.n = n;
+    a.out = out;
+    a.st = st;
+    FH_CUDA(dispatch_fused(m, 0, a));
+    return FHASH_OK;
+}
+
+fhash_status launch_grads(fhash_model* m, const float* coords, const float* target, int64_t n, double* loss_dev,
+                          cudaStream_t st) {
+    const MlpShape& sh = m->mlp;
+    const int W = sh.width;
+    const int64_t A = sh.in + (int64_t)sh.nh * W;  // activation rows
+    const int64_t D = (int64_t)sh.nh * W + 1;       // delta rows
+    FH_TRY(grow(m, m->s_acts, (size_t)(A * n * 4)));
+    FH_TRY(grow(m, m->s_gacts, (size_t)((D + 1) * n * 4)));
+    const int nb_loss = (int)std::max<int64_t>(1, std::min<int64_t>((n + TB - 1) / TB, (int64_t)num_sms() * 16));
+    const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 2));
+    const int64_t chunk = ((n + nchunk - 1) / nchunk + 31) / 32 * 32;
+    int ne_max = 0;
+    for (int j = 0; j <= sh.nh; ++j) {
+        int fi = j == 0 ? sh.in : W, fo = j == sh.nh ? 1 : W;
+        ne_max = std::max(ne_max, fo * fi + fo);
+    }
+    FH_TRY(grow(m, m->s_partial, (size_t)nchunk * ne_max * 4 + (size_t)nb_loss * 8 + 64));
+    FH_TRY(grow(m, m->s_loss, 64));
+    float* acts = (float*)m->s_acts.p;
+    float* gy = (float*)m->s_gacts.p;
+    float* dl = gy + n;
+    double* lpart = (double*)m->s_partial.p;
+    float* wpart = (float*)((char*)m->s_partial.p + ((size_t)nb_loss * 8 + 63) / 64 * 64);
+
+    FusedArgs a{};
+    a.coords = coords;
+    a.target = target;
+    a.n = n;
+    a.acts = acts;
+    a.gy = gy;
+    a.dl = dl;
+    a.partial = lpart;
+    a.st = st;
+    FH_CUDA(dispatch_fused(m, 1, a));
+    if (a.grid != nb_loss) return set_error(FHASH_ECUDA, "internal: loss grid mismatch");
+    k_loss<<<1, 256, 0, st>>>(lpart, nb_loss, n, loss_dev ? loss_dev : (double*)m->s_loss.p);
+    FH_CUDA(cudaGetLastError());
+    FH_CUDA(dispatch_fused(m, 2, a));
+    // weight gradients, layer by layer
+    float* gm = m->grad + m->n_table;
+    for (int j = 0; j <= sh.nh; ++j) {
+        int fi = j == 0 ? sh.in : W, fo = j == sh.nh ? 1 : W;
+        const float* aj = (j == 0) ? acts : acts + (int64_t)(sh.in + (j - 1) * W) * n;
+        const float* dj = dl + (int64_t)j * W * n;
+        k_dw_partial<<<nchunk, 256, 0, st>>>(aj, dj, fi, fo, n, chunk, wpart);
+        int ne = fo * fi + fo;
+        k_dw_reduce<<<(ne + 255) / 256, 256, 0, st>>>(wpart, nchunk, ne, gm + sh.w_off[j]);
+    }
+    FH_CUDA(cudaGetLastError());
+    return FHASH_OK;
+}
+
+fhash_status launch_adam(fhash_model* m, const fhash_adam* ad, cudaStream_t st) {
+    m->step += 1;
+    const double k = (double)m->step;
+    const double bc1 = 1.0 - pow((double)ad->beta1, k), bc2 = 1.0 - pow((double)ad->beta2, k);
+    const int grid = num_sms() * 8;
+    k_adam<<<grid, 256, 0, st>>>(m->param, m->grad, m->adam_m, m->adam_v, m->n_params, ad->beta1, ad->beta2,
+                                 (float)(ad->lr / bc1), (float)sqrt(bc2), ad->eps, m->shadow);
+    FH_CUDA(cudaGetLastError());
+    return FHASH_OK;
+}
+
+}  // namespace fh
+
+using namespace fh;
+
+static fhash_status check_model(fhash_model* m, const char* fn) {
+    if (!m) return set_error(FHASH_EINVAL, "%s: null model", fn);
+    return FHASH_OK;
+}
+
+extern "C" {
+
+fhash_status fhash_lookup(fhash_model* m, const float* coords, int64_t n, uint64_t* rows, float* w, fhash_stream stream) {
+    FH_TRY(check_model(m, "fhash_lookup"));
+    if (n < 0 || (n && (!coords || !rows))) return set_error(FHASH_EINVAL, "fhash_lookup: bad arguments");
+    if (n == 0) return FHASH_OK;
+    if (!is_device_ptr(coords) || !is_device_ptr(rows) || (w && !is_device_ptr(w)))
+        return set_error(FHASH_EINVAL, "fhash_lookup: buffers must be device memory");
+    return launch_lookup(m, coords, n, rows, w, (cudaStream_t)stream);
+}
+
+fhash_status fhash_encode(fhash_model* m, const float* coords, int64_t n, float* enc, fhash_stream stream) {
+    FH_TRY(check_model(m, "fhash_encode"));
+    if (n < 0 || (n && (!coords || !enc))) return set_error(FHASH_EINVAL, "fhash_encode: bad arguments");
+    if (n == 0) return FHASH_OK;
+    if (!is_device_ptr(coords) || !is_device_ptr(enc)) return set_error(FHASH_EINVAL, "fhash_encode: buffers must be device memory");
+    return launch_encode(m, coords, n, enc, (cudaStream_t)stream);
+}
+
+fhash_status fhash_forward(fhash_model* m, const float* coords, int64_t n, float* out, fhash_stream stream) {
+    FH_TRY(check_model(m, "fhash_forward"));
+    if (n < 0 || (n && (!coords || !out))) return set_error(FHASH_EINVAL, "fhash_forward: bad arguments");
+    if (n == 0) return FHASH_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const void* dc;
+    FH_TRY(stage_in(m, m->s_coords, coords, (size_t)n * 16, st, &dc));
+    bool host_out = !is_device_ptr(out);
+    float* dout = out;
+    if (host_out) { FH_TRY(grow(m, m->s_out, (size_t)n * 4)); dout = (float*)m->s_out.p; }
+    FH_TRY(launch_forward(m, (const float*)dc, n, dout, st));
+    if (host_out) {
+        FH_CUDA(cudaMemcpyAsync(out, dout, (size_t)n * 4, cudaMemcpyDeviceToHost, st));
+        FH_CUDA(cudaStreamSynchronize(st));
+    }
+    return FHASH_OK;
+}
+
+fhash_status fhash_compute_grads(fhash_model* m, const float* coords, const float* target, int64_t n, double* loss,
+                                 fhash_stream stream) {
+    FH_TRY(check_model(m, "fhash_compute_grads"));
+    if (n <= 0 || !coords || !target) return set_error(FHASH_EINVAL, "fhash_compute_grads: need n > 0, coords and target");
+    cudaStream_t st = (cudaStream_t)stream;
+    const void *dc, *dt;
+    FH_TRY(stage_in(m, m->s_coords, coords, (size_t)n * 16, st, &dc));
+    FH_TRY(stage_in(m, m->s_target, target, (size_t)n * 4, st, &dt));
+    FH_TRY(grow(m, m->s_loss, 64));
+    bool dev_loss = loss && is_device_ptr(loss);
+    FH_TRY(launch_grads(m, (const float*)dc, (const float*)dt, n, dev_loss ? loss : (double*)m->s_loss.p, st));
+    if (loss && !dev_loss) {
+        FH_CUDA(cudaMemcpyAsync(loss, m->s_loss.p, 8, cudaMemcpyDeviceToHost, st));
+        FH_CUDA(cudaStreamSynchronize(st));
+    }
+    return FHASH_OK;
+}
+
+fhash_status fhash_apply_adam(fhash_model* m, const fhash_adam* a, fhash_stream stream) {
+    FH_TRY(check_model(m, "fhash_apply_adam"));
+    if (!a || !(a->lr >= 0.0f) || !(a->beta1 >= 0.0f && a->beta1 < 1.0f) || !(a->beta2 >= 0.0f && a->beta2 < 1.0f) ||
+        !(a->eps > 0.0f))
+        return set_error(FHASH_EINVAL, "fhash_apply_adam: bad hyper-parameters");
+    return launch_adam(m, a, (cudaStream_t)stream);
+}
+
+fhash_status fhash_train_step(fhash_model* m, const float* coords, const float* target, int64_t n, const fhash_adam* a,
+                              double* loss, fhash_stream stream) {
+    FH_TRY(check_model(m, "fhash_train_step"));
+    if (!a) return set_error(FHASH_EINVAL, "fhash_train_step: null adam");
+    if (n <= 0 || !coords || !target) return set_error(FHASH_EINVAL, "fhash_train_step: need n > 0, coords and target");
+    cudaStream_t st = (cudaStream_t)stream;
+    const void *dc, *dt;
+    FH_TRY(stage_in(m, m->s_coords, coords, (size_t)n * 16, st, &dc));
+    FH_TRY(stage_in(m, m->s_target, target, (size_t)n * 4, st, &dt));
+    FH_TRY(grow(m, m->s_loss, 64));
+    bool dev_loss = loss && is_device_ptr(loss);
+    FH_TRY(launch_grads(m, (const float*)dc, (const float*)dt, n, dev_loss ? loss : (double*)m->s_loss.p, st));
+    FH_TRY(fhash_apply_adam(m, a, stream));
+    if (loss && !dev_loss) {
+        FH_CUDA(cudaMemcpyAsync(loss, m->s_loss.p, 8, cudaMemcpyDeviceToHost, st));
+        FH_CUDA(cudaStreamSynchronize(st));
+    }
+    return FHASH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,494 @@
+// Model construction and state access: feature dilation, Feature Bounding Box, occupancy grid
+// (Section 3.1), level schedule and table sizing (Section 3.2.1-3.2.3), parameter initialisation
+// (Section 3.2.4), and the C-ABI entry points that move state in and out of the model.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <array>
+
+#include "common.cuh"
+
+namespace fh {
+
+static thread_local std::string g_err;
+
+fhash_status set_error(fhash_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+fhash_status cuda_error(cudaError_t e, const char* what) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return set_error(FHASH_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    }
+    return set_error(FHASH_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static fhash_status dev_alloc(fhash_model* m, void** p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return set_error(FHASH_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    m->device_bytes += bytes;
+    return FHASH_OK;
+}
+
+fhash_status grow(fhash_model* m, Scratch& s, size_t bytes) {
+    if (s.bytes >= bytes) return FHASH_OK;
+    if (s.p) {
+        FH_CUDA(cudaDeviceSynchronize());  // buffer may still be read by queued work
+        cudaFree(s.p);
+        m->device_bytes -= s.bytes;
+        s.p = nullptr;
+        s.bytes = 0;
+    }
+    size_t want = bytes + bytes / 4;
+    FH_TRY(dev_alloc(m, &s.p, want));
+    s.bytes = want;
+    return FHASH_OK;
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+fhash_status stage_in(fhash_model* m, Scratch& s, const void* p, size_t bytes, cudaStream_t st, const void** dev) {
+    if (bytes == 0 || is_device_ptr(p)) {
+        *dev = p;
+        return FHASH_OK;
+    }
+    FH_TRY(grow(m, s, bytes));
+    FH_CUDA(cudaMemcpyAsync(s.p, p, bytes, cudaMemcpyHostToDevice, st));
+    *dev = s.p;
+    return FHASH_OK;
+}
+
+// ------------------------------------------------------------------ SplitMix64 (device + host)
+// Steele, Lea, Flood (OOPSLA 2014).  Output i of the generator seeded with s: mix(s + (i+1)*gamma).
+#define FH_GAMMA 0x9E3779B97F4A7C15ULL
+__host__ __device__ __forceinline__ uint64_t sm_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t sm_at(uint64_t seed, uint64_t i) { return sm_mix(seed + (i + 1) * FH_GAMMA); }
+__host__ __device__ __forceinline__ float sm_uniform(uint64_t key, uint64_t i, double lo, double hi) {
+    double u = (double)(sm_at(key, i) >> 40) * (1.0 / 16777216.0);
+    return (float)(lo + (hi - lo) * u);
+}
+
+__global__ void k_init_uniform(float* p, uint64_t n, uint64_t key, double lo, double hi) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        p[i] = sm_uniform(key, i, lo, hi);
+}
+
+__global__ void k_to_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict__ q, uint64_t n) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        q[i] = __float2bfloat16_rn(p[i]);
+}
+
+fhash_status refresh_shadow(fhash_model* m, uint64_t off, uint64_t n, cudaStream_t st) {
+    if (!m->shadow || n == 0) return FHASH_OK;
+    k_to_bf16<<<num_sms() * 8, 256, 0, st>>>(m->param + off, m->shadow + off, n);
+    FH_CUDA(cudaGetLastError());
+    return FHASH_OK;
+}
+
+// ------------------------------------------------------------------ feature dilation + boxes
+// d(v) = OR of f over the 3x3x3 spatial neighbourhood of v, clipped at the border (Section 3.1).
+// Also folds the per-frame bounding box of d into box[6] = (minx, miny, minz, maxx, maxy, maxz).
+__global__ void k_dilate(const uint8_t* __restrict__ f, uint8_t* __restrict__ d, int nx, int ny, int nz, int* box) {
+    __shared__ int sb[6];
+    if (threadIdx.x < 6) sb[threadIdx.x] = (threadIdx.x < 3) ? INT32_MAX : -1;
+    __syncthreads();
+    int64_t n3 = (int64_t)nx * ny * nz;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n3) {
+        int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((int64_t)nx * ny));
+        uint8_t v = 0;
+        for (int dz = -1; dz <= 1 && !v; ++dz) {
+            int zz = z + dz;
+            if (zz < 0 || zz >= nz) continue;
+            for (int dy = -1; dy <= 1 && !v; ++dy) {
+                int yy = y + dy;
+                if (yy < 0 || yy >= ny) continue;
+                const uint8_t* row = f + ((int64_t)zz * ny + yy) * nx;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int xx = x + dx;
+                    if (xx >= 0 && xx < nx && row[xx]) { v = 1; break; }
+                }
+            }
+        }
+        d[i] = v;
+        if (v) {
+            atomicMin(&sb[0], x); atomicMin(&sb[1], y); atomicMin(&sb[2], z);
+            atomicMax(&sb[3], x); atomicMax(&sb[4], y); atomicMax(&sb[5], z);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 3 && sb[threadIdx.x] != INT32_MAX) atomicMin(&box[threadIdx.x], sb[threadIdx.x]);
+    if (threadIdx.x >= 3 && threadIdx.x < 6 && sb[threadIdx.x] >= 0) atomicMax(&box[threadIdx.x], sb[threadIdx.x]);
+}
+
+// Morton index inside an 8^3 brick: bit 3k+0 from x, 3k+1 from y, 3k+2 from z.
+__host__ __device__ __forceinline__ void morton_decode(int mi, int& x, int& y, int& z) {
+    x = (mi & 1) | ((mi >> 2) & 2) | ((mi >> 4) & 4);
+    y = ((mi >> 1) & 1) | ((mi >> 3) & 2) | ((mi >> 5) & 4);
+    z = ((mi >> 2) & 1) | ((mi >> 4) & 2) | ((mi >> 6) & 4);
+}
+
+// One block (512 threads) per brick of one time step: 16 ballots -> 16 words, plus the any-bit.
+__global__ void k_occupancy(const uint8_t* __restrict__ d, int nx, int ny, int lx, int ly, int lz, int sx, int sy,
+                            int sz, int nbx, int nby, uint32_t* __restrict__ words, uint8_t* __restrict__ any) {
+    int b = blockIdx.x;
+    int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
+    int mi = threadIdx.x, x, y, z;
+    morton_decode(mi, x, y, z);
+    x += bx * 8; y += by * 8; z += bz * 8;
+    int v = 0;
+    if (x < sx && y < sy && z < sz) v = d[((int64_t)(lz + z) * ny + (ly + y)) * nx + (lx + x)] != 0;
+    unsigned word = __ballot_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0) words[(int64_t)b * 16 + (threadIdx.x >> 5)] = word;
+    int a = __syncthreads_or(v);
+    if (threadIdx.x == 0) any[b] = (uint8_t)a;
+}
+
+__global__ void k_occ_read(const uint32_t* __restrict__ words, int sx, int sy, int sz, int nbx, int nby,
+                           uint8_t* __restrict__ out) {
+    int64_t n = (int64_t)sx * sy * sz;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int x = (int)(i % sx), y = (int)((i / sx) % sy), z = (int)(i / ((int64_t)sx * sy));
+        int b = ((z >> 3) * nby + (y >> 3)) * nbx + (x >> 3);
+        int lx = x & 7, ly = y & 7, lz = z & 7, mi = 0;
+        for (int k = 0; k < 3; ++k) mi |= (((lx >> k) & 1) << (3 * k)) | (((ly >> k) & 1) << (3 * k + 1)) | (((lz >> k) & 1) << (3 * k + 2));
+        out[i] = (uint8_t)((words[(int64_t)b * 16 + (mi >> 5)] >> (mi & 31)) & 1u);
+    }
+}
+
+// ------------------------------------------------------------------ schedule (host)
+static int ceil_log(int f, int64_t s) {
+    int L = 0;
+    int64_t p = 1;
+    while (p < s) { p *= f; ++L; }
+    return L;
+}
+
+static fhash_status make_schedule(const fhash_schedule& sc, const int64_t S[3], int64_t nt,
+                                  std::vector<std::array<int64_t, 4>>& out) {
+    out.clear();
+    if (sc.mode == FHASH_SCHED_EXPLICIT) {
+        if (sc.n_levels < 1 || sc.n_levels > FHASH_MAX_LEVELS) return set_error(FHASH_EINVAL, "explicit schedule: n_levels %d", sc.n_levels);
+        for (int l = 0; l < sc.n_levels; ++l) out.push_back({sc.res[l][0], sc.res[l][1], sc.res[l][2], sc.res[l][3]});
+    } else if (sc.mode == FHASH_SCHED_GEOMETRIC) {
+        int L = sc.n_levels;
+        if (L < 1 || L > FHASH_MAX_LEVELS) return set_error(FHASH_EINVAL, "geometric schedule: n_levels %d", L);
+        for (int d = 0; d < 4; ++d)
+            if (sc.r0[d] < 1 || sc.r1[d] < 1) return set_error(FHASH_EINVAL, "geometric schedule: r0/r1 must be >= 1");
+        for (int l = 0; l < L; ++l) {
+            std::array<int64_t, 4> r;
+            for (int d = 0; d < 4; ++d)
+                r[d] = (L == 1) ? sc.r1[d]
+                                : (int64_t)floor(sc.r0[d] * pow((double)sc.r1[d] / sc.r0[d], (double)l / (L - 1)) + 0.5);
+            out.push_back(r);
+        }
+    } else if (sc.mode == FHASH_SCHED_FOLD) {
+        int f = sc.fold;
+        if (f < 2) return set_error(FHASH_EINVAL, "fold must be >= 2");
+        int Ld[3] = {ceil_log(f, S[0]), ceil_log(f, S[1]), ceil_log(f, S[2])};
+        int L = (sc.levels_rule == FHASH_LEVELS_MIN) ? std::min(Ld[0], std::min(Ld[1], Ld[2]))
+                                                     : std::max(Ld[0], std::max(Ld[1], Ld[2]));
+        L = std::max(L, 1);
+        if (L > FHASH_MAX_LEVELS) return set_error(FHASH_EINVAL, "fold schedule needs %d levels (max %d)", L, FHASH_MAX_LEVELS);
+        std::vector<std::array<int64_t, 4>> fine;  // paper order: level 1 = native FBB resolution
+        fine.push_back({S[0], S[1], S[2], nt});
+        for (int l = 2; l <= L; ++l) {
+            std::array<int64_t, 4> r = fine.back();
+            for (int d = 0; d < 4; ++d) r[d] = (r[d] > f) ? (r[d] + f - 1) / f : 2;
+            fine.push_back(r);
+        }
+        out.assign(fine.rbegin(), fine.rend());
+    } else {
+        return set_error(FHASH_EINVAL, "unknown schedule mode %d", sc.mode);
+    }
+    for (auto& r : out)
+        for (int d = 0; d < 4; ++d)
+            if (r[d] < 1 || r[d] > (1 << 24)) return set_error(FHASH_EINVAL, "level resolution %lld out of range", (long long)r[d]);
+    return FHASH_OK;
+}
+
+static void destroy_model(fhash_model* m) {
+    if (!m) return;
+    cudaDeviceSynchronize();
+    void* ps[] = {m->param, m->grad, m->adam_m, m->adam_v, m->shadow, m->occ, m->occ_any, m->err_word,
+                  m->s_coords.p, m->s_target.p, m->s_out.p, m->s_acts.p, m->s_gacts.p, m->s_partial.p,
+                  m->s_loss.p, m->s_misc.p};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    delete m;
+}
+
+}  // namespace fh
+
+using namespace fh;
+
+extern "C" {
+
+const char* fhash_last_error(void) { return g_err.c_str(); }
+
+void fhash_destroy(fhash_model* m) { destroy_model(m); }
+
+fhash_status fhash_build(const fhash_build_desc* d, fhash_stream stream, fhash_model** out) {
+    if (!d || !out) return set_error(FHASH_EINVAL, "fhash_build: null argument");
+    *out = nullptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (d->nx < 2 || d->ny < 2 || d->nz < 2 || d->nt < 1 || d->nx > (1 << 20) || d->ny > (1 << 20) || d->nz > (1 << 20))
+        return set_error(FHASH_EINVAL, "volume dims must be >= 2 (space) and >= 1 (time)");
+    if (d->F < 1 || d->F > 8) return set_error(FHASH_EINVAL, "F must be in 1..8");
+    if (d->dtype != FHASH_FP32 && d->dtype != FHASH_BF16) return set_error(FHASH_EINVAL, "dtype");
+    if (d->mlp_hidden_layers < 1 || d->mlp_hidden_layers > FHASH_MAX_HIDDEN)
+        return set_error(FHASH_EINVAL, "mlp_hidden_layers must be in 1..%d", FHASH_MAX_HIDDEN);
+    if (d->mlp_width != 16 && d->mlp_width != 32 && d->mlp_width != 64)
+        return set_error(FHASH_EINVAL, "mlp_width must be 16, 32 or 64");
+    if (!(d->init_range >= 0.0f)) return set_error(FHASH_EINVAL, "init_range");
+
+    fhash_model* m = new fhash_model();
+    m->desc = *d;
+    m->desc.mask = nullptr;
+    cudaGetDevice(&m->device);
+    m->nt = d->nt;
+    struct Guard {
+        fhash_model*& m;
+        ~Guard() { if (m) destroy_model(m); }
+    } guard{m};
+
+    FH_TRY(dev_alloc(m, (void**)&m->err_word, sizeof(int)));
+    FH_CUDA(cudaMemsetAsync(m->err_word, 0, sizeof(int), st));
+
+    // ---- feature dilation, per-frame boxes, FBB (Section 3.1)
+    const int64_t nx = d->nx, ny = d->ny, nz = d->nz, nt = d->nt, n3 = nx * ny * nz;
+    uint8_t* dil = nullptr;  // dilated mask, all frames
+    if (d->mask) {
+        uint8_t* stage = nullptr;
+        int* boxes = nullptr;
+        FH_CUDA(cudaMalloc(&stage, n3));
+        cudaError_t e = cudaMalloc(&dil, (size_t)(n3 * nt));
+        if (e != cudaSuccess) { cudaFree(stage); return cuda_error(e, "cudaMalloc(dilated mask)"); }
+        e = cudaMalloc(&boxes, sizeof(int) * 6 * nt);
+        if (e != cudaSuccess) { cudaFree(stage); cudaFree(dil); return cuda_error(e, "cudaMalloc(boxes)"); }
+        std::vector<int> hb(6 * nt);
+        for (int64_t t = 0; t < nt; ++t) { hb[6 * t + 0] = hb[6 * t + 1] = hb[6 * t + 2] = INT32_MAX; hb[6 * t + 3] = hb[6 * t + 4] = hb[6 * t + 5] = -1; }
+        cudaMemcpyAsync(boxes, hb.data(), sizeof(int) * 6 * nt, cudaMemcpyHostToDevice, st);
+        for (int64_t t = 0; t < nt && e == cudaSuccess; ++t) {
+            e = cudaMemcpyAsync(stage, d->mask + t * n3, n3, cudaMemcpyHostToDevice, st);
+            k_dilate<<<(unsigned)((n3 + 255) / 256), 256, 0, st>>>(stage, dil + t * n3, (int)nx, (int)ny, (int)nz, boxes + 6 * t);
+            if (e == cudaSuccess) e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), boxes, sizeof(int) * 6 * nt, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFree(stage);
+        cudaFree(boxes);
+        if (e != cudaSuccess) { cudaFree(dil); return cuda_error(e, "feature dilation"); }
+        int64_t lo[3] = {INT64_MAX, INT64_MAX, INT64_MAX}, hi[3] = {-1, -1, -1};
+        for (int64_t t = 0; t < nt; ++t) {
+            if (hb[6 * t + 3] < 0) continue;  // empty frame
+            for (int a = 0; a < 3; ++a) { lo[a] = std::min<int64_t>(lo[a], hb[6 * t + a]); hi[a] = std::max<int64_t>(hi[a], hb[6 * t + 3 + a]); }
+        }
+        if (hi[0] < 0) { cudaFree(dil); return set_error(FHASH_EINVAL, "feature mask is empty"); }
+        for (int a = 0; a < 3; ++a) { m->fbb_lo[a] = lo[a]; m->fbb_size[a] = hi[a] - lo[a] + 1; }
+    } else {
+        m->fbb_lo[0] = m->fbb_lo[1] = m->fbb_lo[2] = 0;
+        m->fbb_size[0] = nx; m->fbb_size[1] = ny; m->fbb_size[2] = nz;
+    }
+
+    // ---- occupancy bricks over the FBB, one set per time step
+    const int64_t sx = m->fbb_size[0], sy = m->fbb_size[1], sz = m->fbb_size[2];
+    m->nbx = (sx + 7) / 8; m->nby = (sy + 7) / 8; m->nbz = (sz + 7) / 8;
+    const int64_t nbrick = m->nbx * m->nby * m->nbz;
+    fhash_status s = dev_alloc(m, (void**)&m->occ, (size_t)(nbrick * 16 * 4 * nt));
+    if (s == FHASH_OK) s = dev_alloc(m, (void**)&m->occ_any, (size_t)(nbrick * nt));
+    if (s != FHASH_OK) { if (dil) cudaFree(dil); return s; }
+    if (dil) {
+        for (int64_t t = 0; t < nt; ++t)
+            k_occupancy<<<(unsigned)nbrick, 512, 0, st>>>(dil + t * n3, (int)nx, (int)ny, (int)m->fbb_lo[0], (int)m->fbb_lo[1],
+                                                          (int)m->fbb_lo[2], (int)sx, (int)sy, (int)sz, (int)m->nbx, (int)m->nby,
+                                                          m->occ + t * nbrick * 16, m->occ_any + t * nbrick);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFree(dil);
+        if (e != cudaSuccess) return cuda_error(e, "occupancy");
+    } else {
+        // every voxel occupied; unused bits of partial bricks are never read
+        FH_CUDA(cudaMemsetAsync(m->occ, 0xff, (size_t)(nbrick * 16 * 4 * nt), st));
+        FH_CUDA(cudaMemsetAsync(m->occ_any, 1, (size_t)(nbrick * nt), st));
+    }
+
+    // ---- schedule and table sizing (Section 3.2.1-3.2.3)
+    std::vector<std::array<int64_t, 4>> res;
+    FH_TRY(make_schedule(d->sched, m->fbb_size, nt, res));
+    const int L = (int)res.size();
+    if (L * d->F > 64) return set_error(FHASH_EINVAL, "L*F = %d exceeds 64 (MLP input width)", L * d->F);
+    m->lv.L = L;
+    m->lv.F = d->F;
+    uint64_t acc = 0;
+    for (int l = 0; l < L; ++l) {
+        Level& v = m->lv.lv[l];
+        for (int a = 0; a < 4; ++a) { v.R[a] = (int32_t)res[l][a]; v.Rm1[a] = (float)(res[l][a] - 1); }
+        uint64_t sxy = (uint64_t)res[l][0] * res[l][1];
+        if (sxy >= (1ull << 32)) return set_error(FHASH_EINVAL, "level %d: Rx*Ry too large", l);
+        v.sy = (uint32_t)res[l][0];
+        v.sz = (uint32_t)sxy;
+        uint64_t sxyz = sxy * res[l][2];
+        if (sxyz >= (1ull << 32)) return set_error(FHASH_EINVAL, "level %d: Rx*Ry*Rz too large", l);
+        v.st = sxyz;
+        v.base = acc;
+        acc += sxyz * (uint64_t)res[l][3];
+    }
+    m->total_rows = acc;
+    m->n_table = acc * (uint64_t)d->F;
+
+    MlpShape& sh = m->mlp;
+    sh.in = L * d->F;
+    sh.width = d->mlp_width;
+    sh.nh = d->mlp_hidden_layers;
+    int off = 0;
+    for (int k = 0; k <= sh.nh; ++k) {
+        int fi = (k == 0) ? sh.in : sh.width, fo = (k == sh.nh) ? 1 : sh.width;
+        sh.w_off[k] = off; off += fi * fo;
+        sh.b_off[k] = off; off += fo;
+    }
+    sh.n_params = off;
+    m->n_params = m->n_table + (uint64_t)off;
+
+    // ---- state: param, grad, Adam m and v (+ bf16 shadow)
+    const size_t bytes = (size_t)m->n_params * 4;
+    FH_TRY(dev_alloc(m, (void**)&m->param, bytes));
+    FH_TRY(dev_alloc(m, (void**)&m->grad, bytes));
+    FH_TRY(dev_alloc(m, (void**)&m->adam_m, bytes));
+    FH_TRY(dev_alloc(m, (void**)&m->adam_v, bytes));
+    if (d->dtype == FHASH_BF16) FH_TRY(dev_alloc(m, (void**)&m->shadow, (size_t)m->n_params * 2));
+    FH_CUDA(cudaMemsetAsync(m->grad, 0, bytes, st));
+    FH_CUDA(cudaMemsetAsync(m->adam_m, 0, bytes, st));
+    FH_CUDA(cudaMemsetAsync(m->adam_v, 0, bytes, st));
+
+    // tables U(-r, r) from stream 200; MLP with nn.Linear bounds, streams 300+2k (W) / 301+2k (b)
+    double r = d->init_range;
+    k_init_uniform<<<num_sms() * 8, 256, 0, st>>>(m->param, m->n_table, sm_at(d->seed, 200), -r, r);
+    FH_CUDA(cudaGetLastError());
+    std::vector<float> hm(sh.n_params);
+    for (int k = 0; k <= sh.nh; ++k) {
+        int fi = (k == 0) ? sh.in : sh.width, fo = (k == sh.nh) ? 1 : sh.width;
+        double bnd = 1.0 / sqrt((double)fi);
+        uint64_t kw = sm_at(d->seed, 300 + 2 * k), kb = sm_at(d->seed, 301 + 2 * k);
+        for (int i = 0; i < fi * fo; ++i) hm[sh.w_off[k] + i] = sm_uniform(kw, i, -bnd, bnd);
+        for (int i = 0; i < fo; ++i) hm[sh.b_off[k] + i] = sm_uniform(kb, i, -bnd, bnd);
+    }
+    FH_CUDA(cudaMemcpyAsync(m->param + m->n_table, hm.data(), sizeof(float) * hm.size(), cudaMemcpyHostToDevice, st));
+    FH_TRY(refresh_shadow(m, 0, m->n_params, st));
+    FH_CUDA(cudaStreamSynchronize(st));
+
+    *out = m;
+    m = nullptr;  // release guard
+    return FHASH_OK;
+}
+
+fhash_status fhash_get_info(const fhash_model* m, fhash_info* o) {
+    if (!m || !o) return set_error(FHASH_EINVAL, "fhash_get_info: null argument");
+    memset(o, 0, sizeof *o);
+    o->n_levels = m->lv.L;
+    o->F = m->lv.F;
+    o->dtype = m->desc.dtype;
+    o->n_mlp_layers = m->mlp.nh + 1;
+    o->mlp_dims[0] = m->mlp.in;
+    for (int k = 1; k <= m->mlp.nh; ++k) o->mlp_dims[k] = m->mlp.width;
+    o->mlp_dims[m->mlp.nh + 1] = 1;
+    for (int l = 0; l < m->lv.L; ++l) {
+        for (int a = 0; a < 4; ++a) o->res[l][a] = m->lv.lv[l].R[a];
+        o->base[l] = m->lv.lv[l].base;
+    }
+    o->total_rows = m->total_rows;
+    o->n_table_params = m->n_table;
+    o->n_mlp_params = (uint64_t)m->mlp.n_params;
+    for (int a = 0; a < 3; ++a) { o->fbb_lo[a] = m->fbb_lo[a]; o->fbb_size[a] = m->fbb_size[a]; }
+    o->nt = m->nt;
+    o->step = m->step;
+    o->device_bytes = m->device_bytes;
+    return FHASH_OK;
+}
+
+static float* state_ptr(fhash_model* m, int which) {
+    switch (which) {
+        case FHASH_STATE_PARAM: return m->param;
+        case FHASH_STATE_GRAD: return m->grad;
+        case FHASH_STATE_ADAM_M: return m->adam_m;
+        case FHASH_STATE_ADAM_V: return m->adam_v;
+        default: return nullptr;
+    }
+}
+
+fhash_status fhash_read_state(fhash_model* m, int32_t which, uint64_t off, uint64_t n, float* buf, fhash_stream stream) {
+    if (!m || (!buf && n)) return set_error(FHASH_EINVAL, "fhash_read_state: null argument");
+    float* p = state_ptr(m, which);
+    if (!p) return set_error(FHASH_EINVAL, "fhash_read_state: unknown state %d", which);
+    if (off > m->n_params || n > m->n_params - off) return set_error(FHASH_EINVAL, "fhash_read_state: range out of bounds");
+    if (n) FH_CUDA(cudaMemcpyAsync(buf, p + off, n * 4, cudaMemcpyDefault, (cudaStream_t)stream));
+    return FHASH_OK;
+}
+
+fhash_status fhash_write_state(fhash_model* m, int32_t which, uint64_t off, uint64_t n, const float* buf, fhash_stream stream) {
+    if (!m || (!buf && n)) return set_error(FHASH_EINVAL, "fhash_write_state: null argument");
+    float* p = state_ptr(m, which);
+    if (!p) return set_error(FHASH_EINVAL, "fhash_write_state: unknown state %d", which);
+    if (off > m->n_params || n > m->n_params - off) return set_error(FHASH_EINVAL, "fhash_write_state: range out of bounds");
+    if (n) FH_CUDA(cudaMemcpyAsync(p + off, buf, n * 4, cudaMemcpyDefault, (cudaStream_t)stream));
+    if (which == FHASH_STATE_PARAM) FH_TRY(refresh_shadow(m, off, n, (cudaStream_t)stream));
+    return FHASH_OK;
+}
+
+fhash_status fhash_read_occupancy(fhash_model* m, int64_t t, uint8_t* out, fhash_stream stream) {
+    if (!m || !out) return set_error(FHASH_EINVAL, "fhash_read_occupancy: null argument");
+    if (t < 0 || t >= m->nt) return set_error(FHASH_EINVAL, "fhash_read_occupancy: t out of range");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = m->fbb_size[0] * m->fbb_size[1] * m->fbb_size[2];
+    const int64_t nbrick = m->nbx * m->nby * m->nbz;
+    uint8_t* dst = out;
+    bool host = !is_device_ptr(out);
+    if (host) { FH_TRY(grow(m, m->s_misc, n)); dst = (uint8_t*)m->s_misc.p; }
+    k_occ_read<<<num_sms() * 8, 256, 0, st>>>(m->occ + t * nbrick * 16, (int)m->fbb_size[0], (int)m->fbb_size[1],
+                                               (int)m->fbb_size[2], (int)m->nbx, (int)m->nby, dst);
+    FH_CUDA(cudaGetLastError());
+    if (host) {
+        FH_CUDA(cudaMemcpyAsync(out, dst, n, cudaMemcpyDeviceToHost, st));
+        FH_CUDA(cudaStreamSynchronize(st));
+    }
+    return FHASH_OK;
+}
+
+fhash_status fhash_check(fhash_model* m, fhash_stream stream) {
+    if (!m) return set_error(FHASH_EINVAL, "fhash_check: null model");
+    FH_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    int w = 0;
+    FH_CUDA(cudaMemcpy(&w, m->err_word, sizeof w, cudaMemcpyDeviceToHost));
+    if (w) {
+        FH_CUDA(cudaMemset(m->err_word, 0, sizeof(int)));
+        return set_error(FHASH_EDEVICE, "device error word %d", w);
+    }
+    return FHASH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,30 @@
+"""Workload descriptions (input recipes) used by the tests and the bench.
+
+Each workload names a synthetic field (kind and seed of synth.field), how its feature mask is
+made, the level schedule, embedding size, MLP shape, batch and Adam settings.  These are
+inputs and hyper-parameters only.
+"""
+import numpy as np
+
+from . import field as _field
+from . import mask as _mask
+from . import quantile as _quantile
+
+# 32^3 x 8 field of 4 moving Gaussian blobs; 4 levels doubling from 4^3x1 to 32^3x8; F=2; MLP 2x32.
+SMALL = dict(name="blobs-32^3x8", kind=1, seed=0, dims=(32, 32, 32, 8), mask=("gt", 0.5),
+             schedule=dict(mode="explicit", res=[[4, 4, 4, 1], [8, 8, 8, 2], [16, 16, 16, 4], [32, 32, 32, 8]]),
+             F=2, hidden=2, width=32, batch=16384, adam=(1e-2, 0.9, 0.99, 1e-8), init_range=1e-4)
+
+# 256^3 x 64 field of 64 advecting blobs + 3-octave value noise; mask above the 80th percentile;
+# 16 levels geometric 8^3x2 -> 256^3x64; F=2; MLP 2x64; batch 2^18; Adam lr 1e-2, betas 0.9/0.99.
+LARGE = dict(name="advect-256^3x64", kind=2, seed=1, dims=(256, 256, 256, 64), mask=("quantile", 0.8),
+             schedule=dict(mode="geometric", n_levels=16, r0=[8, 8, 8, 2], r1=[256, 256, 256, 64]),
+             F=2, hidden=2, width=64, batch=2 ** 18, adam=(1e-2, 0.9, 0.99, 1e-8), init_range=1e-4)
+
+
+def make_field_and_mask(w, dims=None):
+    nx, ny, nz, nt = dims or w["dims"]
+    f = _field(w["kind"], w["seed"], nx, ny, nz, nt)
+    how, q = w["mask"]
+    thr = q if how == "gt" else _quantile(f, q)
+    return f, _mask(f, thr)
