@@ -4,7 +4,7 @@ Every function here has the name of the C entry point it calls and does nothing 
 convert arguments (torch CUDA tensors or numpy host arrays -> raw pointers, the current
 torch stream -> cudaStream_t) and turn a non-zero status into FHashError.  All
 computation runs in the CUDA library; if libfhash.so is missing, importing this package
-fails - there is no fallback.  Build it with ``python -m paper_2507_03836_gb300.build``.
+fails - there is no fallback.  Build it with ``python paper_2507_03836_gb300/build.py``.
 """
 import ctypes
 import os
@@ -14,7 +14,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfhash.so")
 if not os.path.exists(LIB_PATH):
-    raise ImportError("libfhash.so is not built (run python -m paper_2507_03836_gb300.build): %s" % LIB_PATH)
+    raise ImportError("libfhash.so is not built (run python paper_2507_03836_gb300/build.py): %s" % LIB_PATH)
 _lib = ctypes.CDLL(LIB_PATH)
 
 MAX_LEVELS = 24

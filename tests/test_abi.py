@@ -20,8 +20,8 @@ def _declared():
 
 
 def test_library_exports_declared_symbols():
-    from paper_2507_03836_gb300 import build
-    path = build.build()
+    import __graft_entry__
+    path = __graft_entry__._build_module().build()
     lib = ctypes.CDLL(path)
     names = _declared()
     assert "fhash_build" in names and "fhash_train_step" in names
