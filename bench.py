@@ -80,7 +80,7 @@ class Clocks:
 
 def _workload(name):
     from synth import workloads
-    return workloads.LARGE if name == "large" else workloads.SMALL
+    return {"large": workloads.LARGE, "medium": workloads.MEDIUM, "small": workloads.SMALL}[name]
 
 
 def _levels(w):
@@ -150,7 +150,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "small"])
+    ap.add_argument("--workload", default="large", choices=["large", "medium", "small"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

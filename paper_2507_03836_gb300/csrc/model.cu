@@ -88,9 +88,15 @@ __host__ __device__ __forceinline__ uint64_t sm_mix(uint64_t z) {
     return z ^ (z >> 31);
 }
 __host__ __device__ __forceinline__ uint64_t sm_at(uint64_t seed, uint64_t i) { return sm_mix(seed + (i + 1) * FH_GAMMA); }
+// (float)(lo + (hi - lo) * U) with the multiply and the add rounded separately (no FMA contraction).
 __host__ __device__ __forceinline__ float sm_uniform(uint64_t key, uint64_t i, double lo, double hi) {
     double u = (double)(sm_at(key, i) >> 40) * (1.0 / 16777216.0);
-    return (float)(lo + (hi - lo) * u);
+#ifdef __CUDA_ARCH__
+    return (float)__dadd_rn(lo, __dmul_rn(hi - lo, u));
+#else
+    volatile double t = (hi - lo) * u;
+    return (float)(lo + t);
+#endif
 }
 
 __global__ void k_init_uniform(float* p, uint64_t n, uint64_t key, double lo, double hi) {

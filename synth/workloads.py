@@ -21,6 +21,11 @@ LARGE = dict(name="advect-256^3x64", kind=2, seed=1, dims=(256, 256, 256, 64), m
              schedule=dict(mode="geometric", n_levels=16, r0=[8, 8, 8, 2], r1=[256, 256, 256, 64]),
              F=2, hidden=2, width=64, batch=2 ** 18, adam=(1e-2, 0.9, 0.99, 1e-8), init_range=1e-4)
 
+# 128^3 x 32 version of LARGE (same recipe; about 3.3 GB of training state, still larger than L2):
+# the size used for detailed profiler captures and full-launch parity checks.
+MEDIUM = dict(LARGE, name="advect-128^3x32", dims=(128, 128, 128, 32),
+              schedule=dict(mode="geometric", n_levels=16, r0=[8, 8, 8, 2], r1=[128, 128, 128, 32]))
+
 
 def make_field_and_mask(w, dims=None):
     nx, ny, nz, nt = dims or w["dims"]

@@ -25,10 +25,17 @@ def small():
     return dict(field=f, mask=m, model=model, info=info)
 
 
+EDGE = np.array([[0, 0, 0, 0], [1, 1, 1, 1], [0.5, 0.5, 0.5, 0.5], [1, 0, 1, 0], [-0.25, 1.5, 0.3, 2.0],
+                 [np.nan, 0.2, 0.7, np.nan]], np.float32)
+# The C ABI takes float32 hyper-parameters; the oracle is given exactly those values.
+HP32 = tuple(float(np.float32(x)) for x in W1["adam"])
+R32 = float(np.float32(W1["init_range"]))
+
+
 def _coords(n, seed=11):
     c = synth.coords(seed, n)
-    c[:6] = [[0, 0, 0, 0], [1, 1, 1, 1], [0.5, 0.5, 0.5, 0.5], [1, 0, 1, 0], [-0.25, 1.5, 0.3, 2.0],
-             [np.nan, 0.2, 0.7, np.nan]]
+    k = min(n, len(EDGE))
+    c[:k] = EDGE[:k]
     return c
 
 
@@ -79,9 +86,9 @@ def test_initial_parameters(small):
     idx = np.unique(np.concatenate([np.arange(64), np.random.default_rng(0).integers(0, info["n_table_params"], 4000),
                                     [info["n_table_params"] - 1]]))
     got = np.array([read(small["model"], 0, int(i), 1)[0] for i in idx[:64]])
-    assert np.array_equal(got, rng.uniform_range(7, 200, idx[:64].astype(np.uint64), -1e-4, 1e-4))
+    assert np.array_equal(got, rng.uniform_range(7, 200, idx[:64].astype(np.uint64), -R32, R32))
     allt = read(small["model"], 0, 0, info["n_table_params"])
-    assert np.array_equal(allt[idx], rng.uniform_range(7, 200, idx.astype(np.uint64), -1e-4, 1e-4))
+    assert np.array_equal(allt[idx], rng.uniform_range(7, 200, idx.astype(np.uint64), -R32, R32))
     p = read(small["model"], 0, info["n_table_params"], info["n_mlp_params"])
     assert np.array_equal(p, synth.init_mlp(7, info["mlp_dims"]))
 
@@ -185,7 +192,7 @@ def test_adam_parity(small):
     P = np.concatenate([table, p]).astype(np.float64)
     M = np.zeros(n)
     V = np.zeros(n)
-    hp = W1["adam"]
+    hp = HP32
     for k in range(1, 4):
         c = _coords(2048, seed=30 + k)
         tgt = synth.sample(small["field"], info["fbb_lo"], info["fbb_size"], np.nan_to_num(np.clip(c, 0, 1)))
@@ -215,7 +222,7 @@ def test_training_curve_parity(small):
         loss = np.zeros(1, np.float64)
         fh().fhash_train_step(model, to_dev(c), to_dev(tgt), W1["adam"], loss)
         losses_g.append(loss[0])
-        losses_o.append(train.train_step(om, c, tgt, *W1["adam"]))
+        losses_o.append(train.train_step(om, c, tgt, *HP32))
     lg, lo = np.array(losses_g), np.array(losses_o)
     assert lo[-1] < 0.5 * lo[0]
     assert (np.abs(lg - lo) <= 1e-4 * lo).all(), np.max(np.abs(lg - lo) / lo)
