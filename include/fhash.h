@@ -206,6 +206,32 @@ fhash_status fhash_read_occupancy(fhash_model* model, int64_t t, uint8_t* out, f
  * error word since the last check (the word is then cleared). */
 fhash_status fhash_check(fhash_model* model, fhash_stream stream);
 
+/*
+ * Gradient computation that allocates nothing (the paper has no counterpart to this call).
+ *
+ * Same result as fhash_compute_grads (forward, MSE loss, backward, gradients added to the model's
+ * gradient buffer), but its working memory is a fixed array of FHASH_NOALLOC_SCRATCH_BYTES that the
+ * library holds in device global memory from load to exit, on every GPU that loads it.  For callers
+ * that cannot call cudaMalloc: for example an application that has handed all device memory to its
+ * own pool, or a latency-critical loop that cannot afford the implicit device synchronisation of
+ * cudaMalloc/cudaFree (fhash_compute_grads grows its scratch buffers with them).  This call makes no
+ * cudaMalloc, cudaFree or other allocating call.
+ *  - coords [n][4] and target [n] must be DEVICE memory (they are not staged); loss is host or
+ *    device double* or NULL.
+ *  - n must be in 1..FHASH_NOALLOC_MAX_SAMPLES; a model/n combination whose working set exceeds the
+ *    array is rejected with FHASH_EINVAL before anything is launched.
+ *  - The first call on a device, made with that device current, looks up the array's device address
+ *    (cudaGetSymbolAddress) once; make that first call before any stream capture.
+ *  - Every call shares the one array, which keeps the previous call's contents: every scratch byte
+ *    this call reads it has written earlier in the same call, so nothing needs clearing, but calls
+ *    that overlap on the GPU (other streams, other threads, other models) race and must be ordered
+ *    by the caller.
+ */
+#define FHASH_NOALLOC_MAX_SAMPLES 4096
+#define FHASH_NOALLOC_SCRATCH_BYTES (12u << 20)
+fhash_status fhash_compute_grads_noalloc(fhash_model* model, const float* coords, const float* target, int64_t n,
+                                         double* loss, fhash_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

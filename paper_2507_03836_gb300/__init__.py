@@ -73,6 +73,7 @@ _SIGS = {
     "fhash_write_state": [_vp, _i32, _u64, _u64, _vp, _vp],
     "fhash_read_occupancy": [_vp, _i64, _vp, _vp],
     "fhash_check": [_vp, _vp],
+    "fhash_compute_grads_noalloc": [_vp, _vp, _vp, _i64, _vp, _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -223,6 +224,14 @@ def fhash_write_state(model, which, offset, buf, stream=None):
 
 def fhash_read_occupancy(model, t, out, stream=None):
     _ok(_lib.fhash_read_occupancy(model.handle, int(t), _ptr(out), _stream(stream)))
+
+
+def fhash_compute_grads_noalloc(model, coords, target, loss=None, stream=None):
+    _ok(_lib.fhash_compute_grads_noalloc(model.handle, _ptr(coords), _ptr(target), coords.shape[0], _ptr(loss),
+                                         _stream(stream)))
+
+
+NOALLOC_MAX_SAMPLES = 4096
 
 
 def fhash_check(model, stream=None):
