@@ -207,6 +207,53 @@ fhash_status fhash_read_occupancy(fhash_model* model, int64_t t, uint8_t* out, f
 fhash_status fhash_check(fhash_model* model, fhash_stream stream);
 
 /*
+ * Camera of fhash_render, in the world space of the Feature Bounding Box scaled to [-1,1]^3
+ * (Section 3.1, Eqs. 1-2).  Pixel (i, j) of a W x H image (row 0 at the top) looks from eye along
+ * fwd + sx*right + sy*up with sx = (2i+1)/W - 1 and sy = 1 - (2j+1)/H; right and up already carry
+ * the half extents of the image plane at unit distance (field of view and aspect ratio).
+ */
+typedef struct {
+    float eye[3], right[3], up[3], fwd[3];
+} fhash_camera;
+
+typedef struct {
+    int64_t rounds;             /* ARM rounds (Algorithm 1 iterations) */
+    int64_t samples_evaluated;  /* sample slots sent through the encode+MLP kernel */
+    int64_t samples_composited; /* samples used by compositing (before early termination) */
+    int64_t steps_marched;      /* sample positions visited, occupied or not */
+} fhash_render_stats;
+
+/*
+ * Render one image of the model at normalised time t_norm in [0,1] by sample streaming with
+ * adaptive ray marching (Section 3.3, Algorithm 1).  Every round, each alive ray contributes up to
+ * N_s = max(min(N_r / N_a, max_pace), 1) samples (N_r = w*h rays, N_a alive; the paper uses 64 as
+ * the pace limit), all samples of the round go through the fused encode+MLP kernel in one launch,
+ * then each ray applies the transfer function and composites front to back and leaves when it exits
+ * the box or its opacity exceeds 0.99.  Samples lie at spacing 1/(S_max - 1) world units from the
+ * box entry and are evaluated only where the occupancy grid (Section 3.1) is set at the nearest voxel
+ * (at an unseen t: set at either neighbouring key frame).  The image does not depend on max_pace.
+ *  tf: device [256][4] RGBA float32, indexed by the value clamped to [0,1] times 255 with linear
+ *      interpolation; alpha is per sample (already corrected for the spacing).
+ *  rgba: device [h][w][4] float32 = (accumulated colour, opacity); rays missing the box give 0.
+ *  counts: device [h][w] int32 composited samples per pixel, or NULL.  stats: host, or NULL.
+ * Synchronous (the round loop reads the alive count back every round).
+ */
+fhash_status fhash_render(fhash_model* model, const fhash_camera* cam, float t_norm, const float* tf, int32_t w,
+                          int32_t h, int32_t max_pace, float* rgba, int32_t* counts, fhash_render_stats* stats,
+                          fhash_stream stream);
+
+/* Points per axis of fhash_decode's grid: dims[a] = upsample * (S_a - 1) + 1, (x, y, z). */
+fhash_status fhash_decode_dims(const fhash_model* model, int32_t upsample, int64_t dims[3]);
+
+/*
+ * Time-slice decode: the model evaluated on a regular grid over the Feature Bounding Box at
+ * normalised time t_norm (any value in [0,1], including times between key frames: temporal
+ * super-resolution, Section 3.3), upsample = 1..8 points per voxel edge.  Point (x, y, z) is
+ * u = (x/(dims[0]-1), y/(dims[1]-1), z/(dims[2]-1), t_norm); out: device [dims[2]][dims[1]][dims[0]].
+ */
+fhash_status fhash_decode(fhash_model* model, float t_norm, int32_t upsample, float* out, fhash_stream stream);
+
+/*
  * Gradient computation that allocates nothing (the paper has no counterpart to this call).
  *
  * Same result as fhash_compute_grads (forward, MSE loss, backward, gradients added to the model's

@@ -58,6 +58,16 @@ class fhash_adam(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float)]
 
 
+class fhash_camera(ctypes.Structure):
+    _fields_ = [("eye", ctypes.c_float * 3), ("right", ctypes.c_float * 3), ("up", ctypes.c_float * 3),
+                ("fwd", ctypes.c_float * 3)]
+
+
+class fhash_render_stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int64), ("samples_evaluated", ctypes.c_int64),
+                ("samples_composited", ctypes.c_int64), ("steps_marched", ctypes.c_int64)]
+
+
 _vp, _i64, _u64, _i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32
 _SIGS = {
     "fhash_build": [ctypes.POINTER(fhash_build_desc), _vp, ctypes.POINTER(_vp)],
@@ -74,6 +84,10 @@ _SIGS = {
     "fhash_read_occupancy": [_vp, _i64, _vp, _vp],
     "fhash_check": [_vp, _vp],
     "fhash_compute_grads_noalloc": [_vp, _vp, _vp, _i64, _vp, _vp],
+    "fhash_render": [_vp, ctypes.POINTER(fhash_camera), ctypes.c_float, _vp, _i32, _i32, _i32, _vp, _vp,
+                     ctypes.POINTER(fhash_render_stats), _vp],
+    "fhash_decode_dims": [_vp, _i32, ctypes.POINTER(ctypes.c_int64 * 3)],
+    "fhash_decode": [_vp, ctypes.c_float, _i32, _vp, _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -232,6 +246,34 @@ def fhash_compute_grads_noalloc(model, coords, target, loss=None, stream=None):
 
 
 NOALLOC_MAX_SAMPLES = 4096
+
+
+def make_camera(eye, right, up, fwd):
+    c = fhash_camera()
+    for a in range(3):
+        c.eye[a], c.right[a], c.up[a], c.fwd[a] = float(eye[a]), float(right[a]), float(up[a]), float(fwd[a])
+    return c
+
+
+def fhash_render(model, cam, t_norm, tf, w, h, rgba, counts=None, max_pace=64, stream=None):
+    """cam: fhash_camera or (eye, right, up, fwd); tf, rgba, counts: device tensors.  Returns stats dict."""
+    if not isinstance(cam, fhash_camera):
+        cam = make_camera(*cam)
+    st = fhash_render_stats()
+    _ok(_lib.fhash_render(model.handle, ctypes.byref(cam), float(t_norm), _ptr(tf), int(w), int(h), int(max_pace),
+                          _ptr(rgba), _ptr(counts), ctypes.byref(st), _stream(stream)))
+    return dict(rounds=st.rounds, samples_evaluated=st.samples_evaluated,
+                samples_composited=st.samples_composited, steps_marched=st.steps_marched)
+
+
+def fhash_decode_dims(model, upsample):
+    d = (ctypes.c_int64 * 3)()
+    _ok(_lib.fhash_decode_dims(model.handle, int(upsample), ctypes.byref(d)))
+    return [int(d[0]), int(d[1]), int(d[2])]
+
+
+def fhash_decode(model, t_norm, upsample, out, stream=None):
+    _ok(_lib.fhash_decode(model.handle, float(t_norm), int(upsample), _ptr(out), _stream(stream)))
 
 
 def fhash_check(model, stream=None):

@@ -79,7 +79,7 @@ struct fhash_model {
     int* err_word = nullptr;  // device error word (0 = ok)
 
     // scratch (grown on demand; owned by the model)
-    fh::Scratch s_coords, s_target, s_out, s_acts, s_gacts, s_partial, s_loss, s_misc;
+    fh::Scratch s_coords, s_target, s_out, s_acts, s_gacts, s_partial, s_loss, s_misc, s_render;
     uint64_t device_bytes = 0;
 };
 
