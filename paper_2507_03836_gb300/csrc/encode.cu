@@ -139,6 +139,8 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ P, float* __re
 }
 
 cudaError_t run_fused_any(int F, int which, const FusedArgs& a);
+cudaError_t run_tc_any(fhash_model* m, bool train, const FusedArgs& a);
+int tc_grid(int64_t n);
 
 static cudaError_t dispatch_fused(fhash_model* m, int which, FusedArgs& a) {
     a.lv = &m->lv;
@@ -173,12 +175,18 @@ fhash_status launch_encode(fhash_model* m, const float* coords, int64_t n, float
 }
 
 fhash_status launch_forward(fhash_model* m, const float* coords, int64_t n, float* out, cudaStream_t st) {
+    if (n <= 0) return FHASH_OK;
     FusedArgs a{};
     a.coords = coords;
     a.n = n;
     a.out = out;
     a.st = st;
-    FH_CUDA(dispatch_fused(m, 0, a));
+    if (m->shadow) {  // precision form: bf16 tables, MLP on the tensor cores
+        a.grid = tc_grid(n);
+        FH_CUDA(run_tc_any(m, false, a));
+    } else {
+        FH_CUDA(dispatch_fused(m, 0, a));
+    }
     return FHASH_OK;
 }
 
@@ -190,7 +198,8 @@ fhash_status launch_grads(fhash_model* m, const float* coords, const float* targ
     const int64_t D = (int64_t)sh.nh * W + 1;       // delta rows
     FH_TRY(grow(m, m->s_acts, (size_t)(A * n * 4)));
     FH_TRY(grow(m, m->s_gacts, (size_t)((D + 1) * n * 4)));
-    const int nb_loss = (int)std::max<int64_t>(1, std::min<int64_t>((n + TB - 1) / TB, (int64_t)num_sms() * 16));
+    const int nb_loss = m->shadow ? tc_grid(n)
+                                  : (int)std::max<int64_t>(1, std::min<int64_t>((n + TB - 1) / TB, (int64_t)num_sms() * 16));
     const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 2));
     const int64_t chunk = ((n + nchunk - 1) / nchunk + 31) / 32 * 32;
     int ne_max = 0;
@@ -215,10 +224,16 @@ fhash_status launch_grads(fhash_model* m, const float* coords, const float* targ
     a.dl = dl;
     a.partial = lpart;
     a.st = st;
-    FH_CUDA(dispatch_fused(m, 1, a));
+    if (m->shadow) {  // precision form: bf16 forward on the tensor cores, float32 backward
+        a.grid = nb_loss;
+        FH_CUDA(run_tc_any(m, true, a));
+    } else {
+        FH_CUDA(dispatch_fused(m, 1, a));
+    }
     if (a.grid != nb_loss) return set_error(FHASH_ECUDA, "internal: loss grid mismatch");
     k_loss<<<1, 256, 0, st>>>(lpart, nb_loss, n, loss_dev ? loss_dev : (double*)m->s_loss.p);
     FH_CUDA(cudaGetLastError());
+    a.grid = 0;
     FH_CUDA(dispatch_fused(m, 2, a));
     // weight gradients, layer by layer
     float* gm = m->grad + m->n_table;

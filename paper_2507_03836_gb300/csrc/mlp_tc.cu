@@ -1,0 +1,292 @@
+// Precision form: bf16 tables and MLP on the tcgen05 tensor cores with float32 accumulation in TMEM.
+//
+// One CTA of 128 threads owns a tile of 128 samples (the MMA's M).  Each thread encodes its sample
+// from the bf16 shadow of the tables (Section 3.2.4; interpolation weights and accumulation in
+// float32) and writes it as one 128-byte bf16 row of the A operand in shared memory (K-major,
+// 128-byte swizzle).  One thread then issues the layer's tcgen05.mma instructions (M=128, N=64,
+// K=64 as 4 x K=16) against the layer's weight tile, also bf16 in shared memory, accumulating float32
+// in 64 TMEM columns; tcgen05.commit arrives on an mbarrier when they are done.  Each warp reads its
+// 32 TMEM lanes back (tcgen05.ld), adds the bias, applies ReLU and writes the next layer's A rows.
+// The scalar output layer runs on the CUDA cores in float32.  Widths below 64 and inputs below 64 are
+// zero-padded to 64 (the padding multiplies zeros).  Every mbarrier wait is bounded: on timeout the
+// kernel reports through the model's error word, waits once more for its MMAs and frees its TMEM.
+#include <math.h>
+
+#include <algorithm>
+
+#include "kernels.cuh"
+#include "tc.cuh"
+
+namespace fh {
+
+template <int F>
+__device__ __forceinline__ void load_row_bf16(const __nv_bfloat16* __restrict__ T, uint64_t r, float (&v)[F]) {
+    const __nv_bfloat16* p = T + r * F;
+    if constexpr (F == 1) {
+        v[0] = __bfloat162float(p[0]);
+    } else if constexpr (F == 2) {
+        uint32_t w = __ldg(reinterpret_cast<const unsigned int*>(p));
+        __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162*>(&w);
+        float2 f = __bfloat1622float2(b);
+        v[0] = f.x; v[1] = f.y;
+    } else if constexpr (F == 4) {
+        uint2 w = __ldg(reinterpret_cast<const uint2*>(p));
+        float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&w.x));
+        float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&w.y));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    } else {
+        uint4 w = __ldg(reinterpret_cast<const uint4*>(p));
+        uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&ws[q]));
+            v[2 * q] = a.x; v[2 * q + 1] = a.y;
+        }
+    }
+}
+
+template <int F>
+__device__ __forceinline__ void interp_level_bf16(const __nv_bfloat16* __restrict__ T, const Corners& k, float* out) {
+    float v[16][F];
+#pragma unroll
+    for (int c = 0; c < 16; c += 2) {
+        uint64_t r = k.r0 + ((c & 8) ? k.ot : 0ull) + ((c & 4) ? k.oz : 0u) + ((c & 2) ? k.oy : 0u);
+        load_row_bf16<F>(T, r, v[c]);
+        load_row_bf16<F>(T, r + k.ox, v[c + 1]);
+    }
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        float vt[2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            float vz[2];
+#pragma unroll
+            for (int kz = 0; kz < 2; ++kz) {
+                const int c = 8 * s + 4 * kz;
+                float y0 = fmaf(k.wx, v[c + 1][f] - v[c][f], v[c][f]);
+                float y1 = fmaf(k.wx, v[c + 3][f] - v[c + 2][f], v[c + 2][f]);
+                vz[kz] = fmaf(k.wy, y1 - y0, y0);
+            }
+            vt[s] = fmaf(k.wz, vz[1] - vz[0], vz[0]);
+        }
+        out[f] = fmaf(k.wt, vt[1] - vt[0], vt[0]);
+    }
+}
+
+// enc[64] (zero beyond L*F) from the bf16 tables.
+template <int F>
+__device__ __forceinline__ void encode64_bf16(const Levels& lv, const __nv_bfloat16* __restrict__ T, float4 u,
+                                              float (&enc)[64]) {
+#pragma unroll
+    for (int i = 0; i < 64; ++i) enc[i] = 0.0f;
+#pragma unroll
+    for (int l = 0; l < 64 / F; ++l) {
+        if (l < lv.L) {
+            Corners k = corners(lv.lv[l], u);
+            float o[F];
+            interp_level_bf16<F>(T, k, o);
+#pragma unroll
+            for (int f = 0; f < F; ++f) enc[l * F + f] = o[f];
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// Row r of a 128 x 64 bf16 A tile (128-byte swizzle) from 64 floats.
+__device__ __forceinline__ void write_row(uint8_t* tile, int r, const float (&x)[64]) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        uint4 w = make_uint4(pack_bf16x2(x[8 * c + 0], x[8 * c + 1]), pack_bf16x2(x[8 * c + 2], x[8 * c + 3]),
+                             pack_bf16x2(x[8 * c + 4], x[8 * c + 5]), pack_bf16x2(x[8 * c + 6], x[8 * c + 7]));
+        *reinterpret_cast<uint4*>(tile + tc::sw128_off(r, c)) = w;
+    }
+}
+
+struct TcSmem {
+    static constexpr int A = 0;          // 128 x 64 bf16 = 16 KB
+    static constexpr int W = 16384;      // per layer 64 x 64 bf16 = 8 KB
+    __host__ __device__ static int bias(int nh) { return W + nh * 8192; }
+    __host__ __device__ static int wout(int nh) { return bias(nh) + nh * 64 * 4; }
+    __host__ __device__ static int bout(int nh) { return wout(nh) + 64 * 4; }
+    __host__ __device__ static int mbar(int nh) { return bout(nh) + 16; }
+    __host__ __device__ static int slot(int nh) { return mbar(nh) + 8; }
+    __host__ __device__ static int bytes(int nh) { return slot(nh) + 8 + 1024; }  // + alignment slack
+};
+
+constexpr uint32_t kTmemCols = 64;
+
+template <int F, bool TRAIN>
+__global__ void __launch_bounds__(128) k_forward_tc(const __grid_constant__ Levels lv, const __grid_constant__ MlpShape sh,
+                                                    const __nv_bfloat16* __restrict__ Tb,
+                                                    const __nv_bfloat16* __restrict__ Pmb, const float* __restrict__ Pm,
+                                                    const float* __restrict__ coords, const float* __restrict__ target,
+                                                    int64_t n, float* __restrict__ out, float* __restrict__ acts,
+                                                    float* __restrict__ gy, double* __restrict__ partial, float two_over_n,
+                                                    int* __restrict__ err) {
+    extern __shared__ uint8_t smraw[];
+    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+    const int nh = sh.nh, Wd = sh.width;
+    uint8_t* At = sm + TcSmem::A;
+    uint8_t* Wt = sm + TcSmem::W;
+    float* bias = reinterpret_cast<float*>(sm + TcSmem::bias(nh));
+    float* wout = reinterpret_cast<float*>(sm + TcSmem::wout(nh));
+    float* bout = reinterpret_cast<float*>(sm + TcSmem::bout(nh));
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + TcSmem::mbar(nh));
+    uint32_t* slot = reinterpret_cast<uint32_t*>(sm + TcSmem::slot(nh));
+    const int t = threadIdx.x, warp = t >> 5;
+
+    if (warp == 0) tc::tmem_alloc(slot, kTmemCols);
+    if (t == 0) {
+        tc::mbar_init(mbar, 1);
+        tc::fence_mbar_init();
+    }
+    // weights of the hidden-producing layers as 64 x 64 bf16 tiles (rows = outputs, K = inputs)
+    for (int j = 0; j < nh; ++j) {
+        const int fi = j == 0 ? sh.in : Wd;
+        for (int e = t; e < 64 * 8; e += 128) {
+            const int r = e >> 3, c = e & 7;
+            uint32_t w4[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k0 = 8 * c + 2 * q;
+                __nv_bfloat16 lo = __float2bfloat16_rn(0.0f), hi = lo;
+                if (r < Wd && k0 < fi) lo = Pmb[sh.w_off[j] + r * fi + k0];
+                if (r < Wd && k0 + 1 < fi) hi = Pmb[sh.w_off[j] + r * fi + k0 + 1];
+                __nv_bfloat162 h2 = __halves2bfloat162(lo, hi);
+                w4[q] = *reinterpret_cast<uint32_t*>(&h2);
+            }
+            *reinterpret_cast<uint4*>(Wt + j * 8192 + tc::sw128_off(r, c)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        }
+        for (int o = t; o < 64; o += 128) bias[j * 64 + o] = (o < Wd) ? Pm[sh.b_off[j] + o] : 0.0f;
+    }
+    for (int o = t; o < 64; o += 128) wout[o] = (o < Wd) ? Pm[sh.w_off[nh] + o] : 0.0f;
+    if (t == 0) bout[0] = Pm[sh.b_off[nh]];
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *slot;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    constexpr uint32_t idesc = tc::idesc_bf16(128, 64);
+    const uint32_t a_addr = tc::smem_addr(At), w_addr = tc::smem_addr(Wt);
+
+    uint32_t phase = 0;
+    bool bad = false;
+    double lsum = 0.0;
+    for (int64_t tile = blockIdx.x; tile * 128 < n && !bad; tile += gridDim.x) {
+        const int64_t i = tile * 128 + t;
+        const bool valid = i < n;
+        float x[64];
+        {
+            float4 u = valid ? load_coord(coords, i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            encode64_bf16<F>(lv, Tb, u, x);
+        }
+        if (TRAIN && valid) {
+#pragma unroll
+            for (int c = 0; c < 64; ++c)
+                if (c < sh.in) acts[(int64_t)c * n + i] = x[c];
+        }
+        write_row(At, t, x);
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        for (int j = 0; j < nh; ++j) {
+            if (t == 0) {
+                tc::fence_after_sync();
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    tc::mma_bf16(tmem, tc::sdesc_sw128(a_addr + kk * 32), tc::sdesc_sw128(w_addr + j * 8192 + kk * 32),
+                                 idesc, kk > 0 ? 1u : 0u);
+                tc::mma_commit(mbar);
+            }
+            const bool ok = tc::mbar_wait(mbar, phase);
+            phase ^= 1;
+            if (__syncthreads_or(!ok)) { bad = true; break; }
+            tc::fence_after_sync();
+            float v[32];
+            tc::tmem_ld32(lane_base + 0, v);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int q = 0; q < 32; ++q) x[q] = fmaxf(v[q] + bias[j * 64 + q], 0.0f);
+            tc::tmem_ld32(lane_base + 32, v);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int q = 0; q < 32; ++q) x[32 + q] = fmaxf(v[q] + bias[j * 64 + 32 + q], 0.0f);
+            if (TRAIN && valid) {
+                float* a = acts + (int64_t)(sh.in + j * Wd) * n + i;
+#pragma unroll
+                for (int o = 0; o < 64; ++o)
+                    if (o < Wd) a[(int64_t)o * n] = x[o];
+            }
+            if (j + 1 < nh) {
+                write_row(At, t, x);
+                tc::fence_async_smem();
+            }
+            tc::fence_before_sync();
+            __syncthreads();
+        }
+        if (bad) break;
+        float y = bout[0];
+#pragma unroll
+        for (int o = 0; o < 64; ++o) y = fmaf(wout[o], x[o], y);
+        if (valid) {
+            if (TRAIN) {
+                const float r = y - __ldg(target + i);
+                gy[i] = two_over_n * r;
+                lsum += (double)r * (double)r;
+            } else {
+                out[i] = y;
+            }
+        }
+    }
+    if (TRAIN) {
+        const double s = block_sum(lsum);
+        if (t == 0) partial[blockIdx.x] = s;
+    }
+    if (bad && t == 0) {
+        raise_error(err, 0x7C05);
+        tc::mbar_wait(mbar, phase ^ 1);  // one more bounded wait for the MMAs in flight
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+template <int F>
+static cudaError_t run_tc(fhash_model* m, bool train, const FusedArgs& a) {
+    const int smem = TcSmem::bytes(m->mlp.nh);
+    const void* fn = train ? (const void*)k_forward_tc<F, true> : (const void*)k_forward_tc<F, false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const __nv_bfloat16* Tb = m->shadow;
+    const __nv_bfloat16* Pmb = m->shadow + m->n_table;
+    const float* Pm = m->param + m->n_table;
+    if (train)
+        k_forward_tc<F, true><<<a.grid, 128, smem, a.st>>>(m->lv, m->mlp, Tb, Pmb, Pm, a.coords, a.target, a.n, nullptr,
+                                                           a.acts, a.gy, a.partial, 2.0f / (float)a.n, m->err_word);
+    else
+        k_forward_tc<F, false><<<a.grid, 128, smem, a.st>>>(m->lv, m->mlp, Tb, Pmb, Pm, a.coords, nullptr, a.n, a.out,
+                                                            nullptr, nullptr, nullptr, 0.0f, m->err_word);
+    return cudaGetLastError();
+}
+
+// Grid for the tensor-core kernels: persistent, at most 4 CTAs per SM (4 x 64 TMEM columns).
+int tc_grid(int64_t n) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, (int64_t)num_sms() * 4));
+}
+
+cudaError_t run_tc_any(fhash_model* m, bool train, const FusedArgs& a) {
+    switch (m->lv.F) {
+        case 1: return run_tc<1>(m, train, a);
+        case 2: return run_tc<2>(m, train, a);
+        case 4: return run_tc<4>(m, train, a);
+        case 8: return run_tc<8>(m, train, a);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace fh

@@ -213,6 +213,16 @@ static cudaError_t run_decode(fhash_model* m, int nx, int ny, int nz, float t, f
 
 static int64_t decode_n(int64_t S, int up) { return (int64_t)up * (S - 1) + 1; }
 
+// Grid coordinates of points [i0, i0 + cnt) of the decode grid (same float32 steps as k_decode).
+__global__ void k_grid_coords(int nx, int ny, int nz, float t_norm, int64_t i0, int64_t cnt, float4* __restrict__ co) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= cnt) return;
+    int64_t i = i0 + q;
+    int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((int64_t)nx * ny));
+    co[q] = make_float4(__fdiv_rn((float)x, (float)(nx - 1)), __fdiv_rn((float)y, (float)(ny - 1)),
+                        __fdiv_rn((float)z, (float)(nz - 1)), t_norm);
+}
+
 }  // namespace fh
 
 using namespace fh;
@@ -233,6 +243,18 @@ fhash_status fhash_decode(fhash_model* m, float t_norm, int32_t upsample, float*
     for (int a = 0; a < 3; ++a) d[a] = decode_n(m->fbb_size[a], upsample);
     if (d[0] * d[1] * d[2] >= (1ll << 40)) return set_error(FHASH_EINVAL, "fhash_decode: grid too large");
     cudaStream_t st = (cudaStream_t)stream;
+    if (m->shadow) {  // precision form: coordinates in chunks, then the tensor-core forward
+        const int64_t total = d[0] * d[1] * d[2], chunk = 1 << 23;
+        FH_TRY(grow(m, m->s_misc, (size_t)chunk * 16));
+        for (int64_t i0 = 0; i0 < total; i0 += chunk) {
+            const int64_t cnt = std::min(chunk, total - i0);
+            k_grid_coords<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>((int)d[0], (int)d[1], (int)d[2], t_norm, i0, cnt,
+                                                                         (float4*)m->s_misc.p);
+            FH_CUDA(cudaGetLastError());
+            FH_TRY(launch_forward(m, (const float*)m->s_misc.p, cnt, out + i0, st));
+        }
+        return FHASH_OK;
+    }
     cudaError_t e;
     switch (m->lv.F) {
         case 1: e = run_decode<1>(m, (int)d[0], (int)d[1], (int)d[2], t_norm, out, st); break;
@@ -307,11 +329,8 @@ fhash_status fhash_render(fhash_model* m, const fhash_camera* cam, float t_norm,
         int ns = (int)std::max<int64_t>(1, std::min<int64_t>(NR / na, max_pace));
         k_arm_generate<<<(na + 127) / 128, 128, 0, st>>>(g, rs, al[cur], na, ns, co, cnt, stats ? acc : nullptr);
         FH_CUDA(cudaGetLastError());
-        FusedArgs a{};
-        a.lv = &m->lv; a.sh = &m->mlp; a.T = m->param; a.G = m->grad; a.Pm = m->param + m->n_table;
-        a.coords = (const float*)co; a.n = (int64_t)na * ns; a.out = val; a.st = st;
-        a.grid = (int)std::max<int64_t>(1, std::min<int64_t>((a.n + TB - 1) / TB, (int64_t)num_sms() * 16));
-        FH_CUDA(run_fused_any(m->lv.F, 0, a));
+        const int64_t nslots = (int64_t)na * ns;
+        FH_TRY(launch_forward(m, (const float*)co, nslots, val, st));
         FH_CUDA(cudaMemsetAsync(ctr + 1 - cur, 0, 4, st));
         k_arm_composite<<<(na + 127) / 128, 128, 0, st>>>(g, rs, al[cur], na, ns, cnt, val, (const float4*)tf,
                                                           al[1 - cur], ctr + 1 - cur, (float4*)rgba, counts,
@@ -321,7 +340,7 @@ fhash_status fhash_render(fhash_model* m, const fhash_camera* cam, float t_norm,
         FH_CUDA(cudaStreamSynchronize(st));
         cur = 1 - cur;
         ++rounds;
-        slots += a.n;
+        slots += nslots;
     }
     if (stats) {
         unsigned long long h2[2];
