@@ -68,6 +68,18 @@ class fhash_render_stats(ctypes.Structure):
                 ("samples_composited", ctypes.c_int64), ("steps_marched", ctypes.c_int64)]
 
 
+class fhash_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("model", ctypes.c_int32), ("t_norm", ctypes.c_float), ("cam", fhash_camera),
+                ("w", ctypes.c_int32), ("h", ctypes.c_int32), ("max_pace", ctypes.c_int32), ("tf", ctypes.c_void_p),
+                ("upsample", ctypes.c_int32), ("out", ctypes.c_void_p), ("counts", ctypes.c_void_p)]
+
+
+class fhash_server_stats(ctypes.Structure):
+    _fields_ = [("ticks", ctypes.c_int64), ("samples", ctypes.c_int64), ("model_launches", ctypes.c_int64),
+                ("live", ctypes.c_int64), ("queued", ctypes.c_int64), ("pool_bytes", ctypes.c_uint64),
+                ("pool_used", ctypes.c_uint64)]
+
+
 _vp, _i64, _u64, _i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32
 _SIGS = {
     "fhash_build": [ctypes.POINTER(fhash_build_desc), _vp, ctypes.POINTER(_vp)],
@@ -88,11 +100,18 @@ _SIGS = {
                      ctypes.POINTER(fhash_render_stats), _vp],
     "fhash_decode_dims": [_vp, _i32, ctypes.POINTER(ctypes.c_int64 * 3)],
     "fhash_decode": [_vp, ctypes.c_float, _i32, _vp, _vp],
+    "fhash_server_create": [ctypes.POINTER(_vp), _i32, _u64, _i32, _i64, _vp, ctypes.POINTER(_vp)],
+    "fhash_server_submit": [_vp, ctypes.POINTER(fhash_request), ctypes.POINTER(_u64)],
+    "fhash_server_tick": [_vp, _vp, ctypes.POINTER(_i32)],
+    "fhash_server_poll": [_vp, _u64, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double)],
+    "fhash_server_cancel": [_vp, _u64],
+    "fhash_server_get_stats": [_vp, ctypes.POINTER(fhash_server_stats)],
+    "fhash_server_destroy": [_vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
-    _f.restype = None if _name == "fhash_destroy" else ctypes.c_int
+    _f.restype = None if _name in ("fhash_destroy", "fhash_server_destroy") else ctypes.c_int
 _lib.fhash_last_error.restype = ctypes.c_char_p
 _lib.fhash_last_error.argtypes = []
 
@@ -278,3 +297,66 @@ def fhash_decode(model, t_norm, upsample, out, stream=None):
 
 def fhash_check(model, stream=None):
     _ok(_lib.fhash_check(model.handle, _stream(stream)))
+
+
+REQ_RENDER, REQ_DECODE = 0, 1
+REQ_QUEUED, REQ_LIVE, REQ_DONE, REQ_CANCELLED = 0, 1, 2, 3
+
+
+class Server:
+    """Owning handle of an fhash_server*; keeps its models alive."""
+
+    def __init__(self, handle, models):
+        self.handle, self.models = handle, list(models)
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            _lib.fhash_server_destroy(self.handle)
+            self.handle = None
+
+
+def fhash_server_create(models, budget_bytes, max_live=64, tick_samples=1 << 22, stream=None):
+    arr = (_vp * len(models))(*[m.handle for m in models])
+    h = _vp()
+    _ok(_lib.fhash_server_create(arr, len(models), int(budget_bytes), int(max_live), int(tick_samples),
+                                 _stream(stream), ctypes.byref(h)))
+    return Server(h.value, models)
+
+
+def make_request(kind, model=0, t_norm=0.0, cam=None, w=0, h=0, max_pace=64, tf=None, upsample=1, out=None,
+                 counts=None):
+    r = fhash_request()
+    r.kind, r.model, r.t_norm = int(kind), int(model), float(t_norm)
+    if cam is not None:
+        r.cam = cam if isinstance(cam, fhash_camera) else make_camera(*cam)
+    r.w, r.h, r.max_pace = int(w), int(h), int(max_pace)
+    r.tf, r.upsample, r.out, r.counts = _ptr(tf), int(upsample), _ptr(out), _ptr(counts)
+    return r
+
+
+def fhash_server_submit(server, req):
+    i = _u64()
+    _ok(_lib.fhash_server_submit(server.handle, ctypes.byref(req), ctypes.byref(i)))
+    return int(i.value)
+
+
+def fhash_server_tick(server, stream=None):
+    n = _i32()
+    _ok(_lib.fhash_server_tick(server.handle, _stream(stream), ctypes.byref(n)))
+    return int(n.value)
+
+
+def fhash_server_poll(server, rid):
+    st, lat = _i32(), ctypes.c_double()
+    _ok(_lib.fhash_server_poll(server.handle, int(rid), ctypes.byref(st), ctypes.byref(lat)))
+    return int(st.value), float(lat.value)
+
+
+def fhash_server_cancel(server, rid):
+    _ok(_lib.fhash_server_cancel(server.handle, int(rid)))
+
+
+def fhash_server_get_stats(server):
+    st = fhash_server_stats()
+    _ok(_lib.fhash_server_get_stats(server.handle, ctypes.byref(st)))
+    return {k: int(getattr(st, k)) for k, _ in fhash_server_stats._fields_}

@@ -158,6 +158,8 @@ inline int num_sms() {
 fhash_status launch_lookup(fhash_model* m, const float* coords, int64_t n, uint64_t* rows, float* w, cudaStream_t st);
 fhash_status launch_encode(fhash_model* m, const float* coords, int64_t n, float* enc, cudaStream_t st);
 fhash_status launch_forward(fhash_model* m, const float* coords, int64_t n, float* out, cudaStream_t st);
+fhash_status launch_forward_seg(fhash_model* m, const float* coords, float* out, const int64_t* seg, int64_t max_n,
+                                cudaStream_t st);
 fhash_status launch_grads(fhash_model* m, const float* coords, const float* target, int64_t n, double* loss_dev,
                           cudaStream_t st);
 fhash_status launch_adam(fhash_model* m, const fhash_adam* a, cudaStream_t st);

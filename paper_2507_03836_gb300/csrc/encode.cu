@@ -190,6 +190,26 @@ fhash_status launch_forward(fhash_model* m, const float* coords, int64_t n, floa
     return FHASH_OK;
 }
 
+// Persistent forward over the segment {offset, count} held in device memory at `seg`: the grid does
+// not depend on the count, so the launch can be captured once and replayed with new segments.
+fhash_status launch_forward_seg(fhash_model* m, const float* coords, float* out, const int64_t* seg, int64_t max_n,
+                                cudaStream_t st) {
+    FusedArgs a{};
+    a.coords = coords;
+    a.n = 0;
+    a.out = out;
+    a.st = st;
+    a.seg = seg;
+    if (m->shadow) {
+        a.grid = tc_grid(max_n);
+        FH_CUDA(run_tc_any(m, false, a));
+    } else {
+        a.n = max_n;  // sizes the persistent grid only
+        FH_CUDA(dispatch_fused(m, 0, a));
+    }
+    return FHASH_OK;
+}
+
 fhash_status launch_grads(fhash_model* m, const float* coords, const float* target, int64_t n, double* loss_dev,
                           cudaStream_t st) {
     const MlpShape& sh = m->mlp;

@@ -198,10 +198,18 @@ __device__ __forceinline__ float mlp_fwd_col(const MlpShape& sh, const MlpSmemLa
 }
 
 // ------------------------------------------------------------------ forward (inference)
+// seg (optional, device): {offset, count} read at run time, so that one captured launch can serve
+// batches of any size placed anywhere in a packed buffer (the serving loop replays it every tick).
 template <int F>
 __global__ void __launch_bounds__(TB) k_forward(const __grid_constant__ Levels lv, const __grid_constant__ MlpShape sh,
                                                 const float* __restrict__ T, const float* __restrict__ Pm,
-                                                const float* __restrict__ coords, int64_t n, float* __restrict__ out) {
+                                                const float* __restrict__ coords, int64_t n, float* __restrict__ out,
+                                                const int64_t* __restrict__ seg) {
+    if (seg) {
+        coords += 4 * seg[0];
+        out += seg[0];
+        n = seg[1];
+    }
     extern __shared__ float4 smem4[];
     float* s = reinterpret_cast<float*>(smem4);
     const MlpSmemLayout L = mlp_layout(sh, false, sh.in + 2 * sh.width);
@@ -365,6 +373,7 @@ struct FusedArgs {
     double* partial;
     int grid;
     cudaStream_t st;
+    const int64_t* seg;  // optional device {offset, count} for the forward kernels
 };
 
 template <int F>
@@ -377,7 +386,7 @@ cudaError_t run_fused(int which, const FusedArgs& a) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     if (which == 0)
-        k_forward<F><<<a.grid, TB, smem, a.st>>>(*a.lv, sh, a.T, a.Pm, a.coords, a.n, a.out);
+        k_forward<F><<<a.grid, TB, smem, a.st>>>(*a.lv, sh, a.T, a.Pm, a.coords, a.n, a.out, a.seg);
     else if (which == 1)
         k_train_fwd<F><<<a.grid, TB, smem, a.st>>>(*a.lv, sh, a.T, a.Pm, a.coords, a.target, a.n, 2.0f / (float)a.n,
                                                    a.acts, a.gy, a.partial);

@@ -126,7 +126,12 @@ __global__ void __launch_bounds__(128) k_forward_tc(const __grid_constant__ Leve
                                                     const float* __restrict__ coords, const float* __restrict__ target,
                                                     int64_t n, float* __restrict__ out, float* __restrict__ acts,
                                                     float* __restrict__ gy, double* __restrict__ partial, float two_over_n,
-                                                    int* __restrict__ err) {
+                                                    int* __restrict__ err, const int64_t* __restrict__ seg) {
+    if (!TRAIN && seg) {  // packed serving buffers: {offset, count} read at run time
+        coords += 4 * seg[0];
+        out += seg[0];
+        n = seg[1];
+    }
     extern __shared__ uint8_t smraw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
     const int nh = sh.nh, Wd = sh.width;
@@ -267,10 +272,10 @@ static cudaError_t run_tc(fhash_model* m, bool train, const FusedArgs& a) {
     const float* Pm = m->param + m->n_table;
     if (train)
         k_forward_tc<F, true><<<a.grid, 128, smem, a.st>>>(m->lv, m->mlp, Tb, Pmb, Pm, a.coords, a.target, a.n, nullptr,
-                                                           a.acts, a.gy, a.partial, 2.0f / (float)a.n, m->err_word);
+                                                           a.acts, a.gy, a.partial, 2.0f / (float)a.n, m->err_word, nullptr);
     else
         k_forward_tc<F, false><<<a.grid, 128, smem, a.st>>>(m->lv, m->mlp, Tb, Pmb, Pm, a.coords, nullptr, a.n, a.out,
-                                                            nullptr, nullptr, nullptr, 0.0f, m->err_word);
+                                                            nullptr, nullptr, nullptr, 0.0f, m->err_word, a.seg);
     return cudaGetLastError();
 }
 

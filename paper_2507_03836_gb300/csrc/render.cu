@@ -14,34 +14,11 @@
 
 #include <algorithm>
 
-#include "kernels.cuh"
+#include "render.cuh"
 
 namespace fh {
 
 cudaError_t run_fused_any(int F, int which, const FusedArgs& a);
-
-struct RenderGeo {
-    float eye[3], right[3], up[3], fwd[3];
-    float delta;      // sample spacing in world units
-    float t_norm;
-    int W, H;
-    int S[3];         // FBB vertices per axis
-    int nt;
-    int tp, tn;       // time steps whose occupancy is used
-    int use_tn;       // 1 when t lies strictly between key frames
-    int64_t nbx, nby, nbrick;
-    const uint32_t* occ;
-    const uint8_t* occ_any;
-};
-
-struct RayState {
-    float d[3];
-    float tmin, tmax;
-    int k;       // next sample index
-    int flags;   // 1 = exited
-    float C[3], T;
-    int count;   // composited samples
-};
 
 __device__ __forceinline__ bool occ_bit(const RenderGeo& g, int t, int x, int y, int z) {
     int64_t b = ((int64_t)(z >> 3) * g.nby + (y >> 3)) * g.nbx + (x >> 3);
@@ -175,6 +152,31 @@ __global__ void k_arm_composite(const __grid_constant__ RenderGeo g, RayState* _
     rs[pix].count = s.count;
 }
 
+RenderGeo make_geo(const fhash_model* m, const fhash_camera* cam, float t_norm, int w, int h) {
+    RenderGeo g{};
+    for (int a = 0; a < 3; ++a) {
+        g.eye[a] = cam->eye[a]; g.right[a] = cam->right[a]; g.up[a] = cam->up[a]; g.fwd[a] = cam->fwd[a];
+        g.S[a] = (int)m->fbb_size[a];
+    }
+    int64_t smax = std::max(m->fbb_size[0], std::max(m->fbb_size[1], m->fbb_size[2]));
+    g.delta = (float)(1.0 / (double)(smax - 1));
+    g.t_norm = t_norm;
+    g.W = w; g.H = h;
+    g.nt = (int)m->nt;
+    // time steps of the occupancy used at t_norm (same float32 steps as the sample test)
+    const float tq = t_norm * (float)(g.nt - 1);  // host code is built without FP contraction
+    int tp = (int)floorf(tq);
+    tp = std::min(std::max(tp, 0), g.nt - 1);
+    const float wt = tq - (float)tp;
+    g.tp = tp;
+    g.tn = std::min(tp + 1, g.nt - 1);
+    g.use_tn = wt > 0.0f ? 1 : 0;
+    g.nbx = m->nbx; g.nby = m->nby; g.nbrick = m->nbx * m->nby * m->nbz;
+    g.occ = m->occ; g.occ_any = m->occ_any;
+
+    return g;
+}
+
 // Decode: the model on a regular grid over the FBB at fractional t (n'_d = up*(S_d-1)+1 points per
 // axis, u_d = j/(n'_d - 1)), out[z][y][x].
 template <int F>
@@ -211,7 +213,7 @@ static cudaError_t run_decode(fhash_model* m, int nx, int ny, int nz, float t, f
     return cudaGetLastError();
 }
 
-static int64_t decode_n(int64_t S, int up) { return (int64_t)up * (S - 1) + 1; }
+int64_t decode_points(int64_t S, int up) { return (int64_t)up * (S - 1) + 1; }
 
 // Grid coordinates of points [i0, i0 + cnt) of the decode grid (same float32 steps as k_decode).
 __global__ void k_grid_coords(int nx, int ny, int nz, float t_norm, int64_t i0, int64_t cnt, float4* __restrict__ co) {
@@ -231,7 +233,7 @@ extern "C" {
 
 fhash_status fhash_decode_dims(const fhash_model* m, int32_t upsample, int64_t dims[3]) {
     if (!m || !dims || upsample < 1 || upsample > 8) return set_error(FHASH_EINVAL, "fhash_decode_dims: bad arguments");
-    for (int a = 0; a < 3; ++a) dims[a] = decode_n(m->fbb_size[a], upsample);
+    for (int a = 0; a < 3; ++a) dims[a] = decode_points(m->fbb_size[a], upsample);
     return FHASH_OK;
 }
 
@@ -240,7 +242,7 @@ fhash_status fhash_decode(fhash_model* m, float t_norm, int32_t upsample, float*
         return set_error(FHASH_EINVAL, "fhash_decode: bad arguments (upsample 1..8, t_norm in [0,1])");
     if (!is_device_ptr(out)) return set_error(FHASH_EINVAL, "fhash_decode: out must be device memory");
     int64_t d[3];
-    for (int a = 0; a < 3; ++a) d[a] = decode_n(m->fbb_size[a], upsample);
+    for (int a = 0; a < 3; ++a) d[a] = decode_points(m->fbb_size[a], upsample);
     if (d[0] * d[1] * d[2] >= (1ll << 40)) return set_error(FHASH_EINVAL, "fhash_decode: grid too large");
     cudaStream_t st = (cudaStream_t)stream;
     if (m->shadow) {  // precision form: coordinates in chunks, then the tensor-core forward
@@ -276,27 +278,7 @@ fhash_status fhash_render(fhash_model* m, const fhash_camera* cam, float t_norm,
     if (!is_device_ptr(tf) || !is_device_ptr(rgba) || (counts && !is_device_ptr(counts)))
         return set_error(FHASH_EINVAL, "fhash_render: tf, rgba and counts must be device memory");
     cudaStream_t st = (cudaStream_t)stream;
-    RenderGeo g{};
-    for (int a = 0; a < 3; ++a) {
-        g.eye[a] = cam->eye[a]; g.right[a] = cam->right[a]; g.up[a] = cam->up[a]; g.fwd[a] = cam->fwd[a];
-        g.S[a] = (int)m->fbb_size[a];
-    }
-    int64_t smax = std::max(m->fbb_size[0], std::max(m->fbb_size[1], m->fbb_size[2]));
-    g.delta = (float)(1.0 / (double)(smax - 1));
-    g.t_norm = t_norm;
-    g.W = w; g.H = h;
-    g.nt = (int)m->nt;
-    // time steps of the occupancy used at t_norm (same float32 steps as the sample test)
-    const float tq = t_norm * (float)(g.nt - 1);  // host code is built without FP contraction
-    int tp = (int)floorf(tq);
-    tp = std::min(std::max(tp, 0), g.nt - 1);
-    const float wt = tq - (float)tp;
-    g.tp = tp;
-    g.tn = std::min(tp + 1, g.nt - 1);
-    g.use_tn = wt > 0.0f ? 1 : 0;
-    g.nbx = m->nbx; g.nby = m->nby; g.nbrick = m->nbx * m->nby * m->nbz;
-    g.occ = m->occ; g.occ_any = m->occ_any;
-
+    const RenderGeo g = make_geo(m, cam, t_norm, w, h);
     const int64_t NR = (int64_t)w * h;
     // scratch: ray states, two alive lists, sample coords and values, per-ray counts, counters
     const size_t o_rs = 0;

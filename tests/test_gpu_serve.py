@@ -1,0 +1,131 @@
+"""GPU tests of the continuous-batching serving loop (include/fhash_serve.h).
+
+Each request's result in a mix - renders of different sizes, cameras and fractional times, and
+decodes at different upsampling and times, over an FP32 and a bf16 model, interleaved across many
+ticks of a small packed buffer - must be bit-identical to the same request run alone through
+fhash_render / fhash_decode (per-sample arithmetic does not depend on batch position, and the image
+does not depend on the ARM pace).  Admission follows the memory budget; cancellation releases memory.
+"""
+import numpy as np
+import pytest
+
+import synth
+from synth import workloads
+
+from _util import build, fh, set_params, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+W1 = workloads.SMALL
+
+
+@pytest.fixture(scope="module")
+def models():
+    f, m = workloads.make_field_and_mask(W1)
+    out = []
+    for dt in (fh().FP32, fh().BF16):
+        model = build(W1, mask=m, dtype=dt, seed=17)
+        info = fh().fhash_get_info(model)
+        table = synth.uniform(51, 50, info["n_table_params"], -0.6, 0.6)
+        p = synth.init_mlp(51, info["mlp_dims"])
+        p[-1] = 0.45
+        set_params(model, table, p)
+        out.append(model)
+    return out
+
+
+def _alone_render(model, cam, t, w, h, tf):
+    rgba = torch().empty((h, w, 4), dtype=torch().float32, device="cuda")
+    cnt = torch().empty((h, w), dtype=torch().int32, device="cuda")
+    fh().fhash_render(model, cam, t, tf, w, h, rgba, cnt)
+    return rgba.cpu().numpy(), cnt.cpu().numpy()
+
+
+def _alone_decode(model, t, up):
+    d = fh().fhash_decode_dims(model, up)
+    out = torch().empty((d[2], d[1], d[0]), dtype=torch().float32, device="cuda")
+    fh().fhash_decode(model, t, up, out)
+    return out.cpu().numpy()
+
+
+def _run(srv, ids, max_ticks=10000):
+    for _ in range(max_ticks):
+        if all(fh().fhash_server_poll(srv, i)[0] in (fh().REQ_DONE, fh().REQ_CANCELLED) for i in ids):
+            return
+        fh().fhash_server_tick(srv)
+    raise AssertionError("requests did not finish")
+
+
+def test_mix_equals_alone(models):
+    tf = to_dev(synth.transfer_function(0.5))
+    srv = fh().fhash_server_create(models, budget_bytes=1 << 30, max_live=8, tick_samples=8192)
+    specs = [("r", 0, 0.0, 40, 30, 0), ("d", 1, 0.37, 2), ("r", 1, 0.55, 64, 48, 1), ("d", 0, 1.0, 1),
+             ("r", 0, 0.9, 24, 24, 2), ("r", 1, 0.2, 72, 40, 3), ("d", 0, 0.5, 2)]
+    subs = []
+    for sp in specs:
+        if sp[0] == "r":
+            _, mi, t, w, h, v = sp
+            cam = synth.camera(synth.sphere_eye(3, v), w, h)
+            out = torch().empty((h, w, 4), dtype=torch().float32, device="cuda")
+            cnt = torch().empty((h, w), dtype=torch().int32, device="cuda")
+            rid = fh().fhash_server_submit(srv, fh().make_request(fh().REQ_RENDER, mi, t, cam, w, h, 64, tf, out=out,
+                                                                  counts=cnt))
+            subs.append((sp, rid, out, cnt, cam))
+        else:
+            _, mi, t, up = sp
+            d = fh().fhash_decode_dims(models[mi], up)
+            out = torch().empty((d[2], d[1], d[0]), dtype=torch().float32, device="cuda")
+            rid = fh().fhash_server_submit(srv, fh().make_request(fh().REQ_DECODE, mi, t, upsample=up, out=out))
+            subs.append((sp, rid, out, None, None))
+        fh().fhash_server_tick(srv)  # requests arrive while others are on the GPU
+    _run(srv, [s[1] for s in subs])
+    st = fh().fhash_server_get_stats(srv)
+    assert st["ticks"] > len(specs) and st["pool_used"] == 0 and st["live"] == 0
+    for sp, rid, out, cnt, cam in subs:
+        state, lat = fh().fhash_server_poll(srv, rid)
+        assert state == fh().REQ_DONE and lat >= 0
+        if sp[0] == "r":
+            a, c = _alone_render(models[sp[1]], cam, sp[2], sp[3], sp[4], tf)
+            assert np.array_equal(out.cpu().numpy(), a) and np.array_equal(cnt.cpu().numpy(), c), sp
+        else:
+            assert np.array_equal(out.cpu().numpy(), _alone_decode(models[sp[1]], sp[2], sp[3])), sp
+
+
+def test_budget_admission_and_cancel(models):
+    tf = to_dev(synth.transfer_function(0.5))
+    w, h = 64, 64
+    probe = fh().fhash_server_create([models[0]], budget_bytes=1 << 28, max_live=8, tick_samples=4096)
+    fixed = (1 << 28) - fh().fhash_server_get_stats(probe)["pool_bytes"]  # models + packed buffers
+    need = 4096 * 48 + 3 * 4096 * 4  # one 64x64 render: ray states + two alive lists + counts
+    del probe
+    srv = fh().fhash_server_create([models[0]], budget_bytes=fixed + need * 3 // 2, max_live=8, tick_samples=4096)
+    outs, ids = [], []
+    for v in range(3):
+        out = torch().empty((h, w, 4), dtype=torch().float32, device="cuda")
+        cam = synth.camera(synth.sphere_eye(4, v), w, h)
+        ids.append(fh().fhash_server_submit(srv, fh().make_request(fh().REQ_RENDER, 0, 0.3, cam, w, h, 64, tf, out=out)))
+        outs.append((out, cam))
+    fh().fhash_server_tick(srv)
+    states = [fh().fhash_server_poll(srv, i)[0] for i in ids]
+    assert states.count(fh().REQ_LIVE) + states.count(fh().REQ_DONE) == 1 and states.count(fh().REQ_QUEUED) == 2
+    fh().fhash_server_cancel(srv, ids[2])
+    _run(srv, ids)
+    assert fh().fhash_server_poll(srv, ids[2])[0] == fh().REQ_CANCELLED
+    for i, (out, cam) in zip(ids[:2], outs[:2]):
+        assert fh().fhash_server_poll(srv, i)[0] == fh().REQ_DONE
+        a, _ = _alone_render(models[0], cam, 0.3, w, h, tf)
+        assert np.array_equal(out.cpu().numpy(), a)
+    assert fh().fhash_server_get_stats(srv)["pool_used"] == 0
+
+
+def test_invalid_requests(models):
+    srv = fh().fhash_server_create([models[0]], budget_bytes=1 << 28, max_live=2, tick_samples=1024)
+    out = torch().empty(16, device="cuda")
+    tf = to_dev(synth.transfer_function(0.5))
+    bad = [fh().make_request(fh().REQ_RENDER, 5, 0.1, synth.camera([2, 0, 0], 4, 4), 4, 4, 64, tf, out=out),
+           fh().make_request(fh().REQ_RENDER, 0, 1.5, synth.camera([2, 0, 0], 4, 4), 4, 4, 64, tf, out=out),
+           fh().make_request(fh().REQ_RENDER, 0, 0.1, synth.camera([2, 0, 0], 64, 64), 64, 64, 64, tf, out=out),
+           fh().make_request(fh().REQ_DECODE, 0, 0.1, upsample=9, out=out), fh().make_request(7, 0, 0.1, out=out)]
+    for r in bad:
+        with pytest.raises(fh().FHashError) as e:
+            fh().fhash_server_submit(srv, r)
+        assert e.value.status == 1
