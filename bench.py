@@ -27,6 +27,10 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "train samples/s (enc+MLP fwd+bwd); render p50/p99 ms; BF16 vs FP32 @PSNR"
+# DRAM bytes per parameter of k_adam from one ncu capture of the same kernel on advect-128^3x32
+# (profiles/ncu_k_adam_advect-128^3x32.md): 8.147 GB / 256,431,192 parameters.  The traffic of this
+# streaming kernel grows in proportion to the parameter count, so it scales to the full launch.
+ADAM_DRAM_BYTES_PER_PARAM = 8.147e9 / 256431192
 
 
 def _peaks():
@@ -144,6 +148,101 @@ def run_reference(args):
         "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def _copy_params(src, dst, n, chunk=1 << 28):
+    """Trained float32 parameters of one model into another of the same shape, through the C ABI."""
+    import torch
+    import paper_2507_03836_gb300 as fh
+    buf = torch.empty(min(n, chunk), dtype=torch.float32, device="cuda")
+    for o in range(0, n, chunk):
+        k = min(chunk, n - o)
+        fh.fhash_read_state(src, fh.STATE_PARAM, o, buf[:k])
+        fh.fhash_write_state(dst, fh.STATE_PARAM, o, buf[:k])
+    torch.cuda.synchronize()
+
+
+def serving_leg(args, w, model, info, field, mask, rank):
+    """Render serving of the trained model in FP32 and in the precision form (bf16 + tensor cores):
+    a Poisson stream of renders (sizes uniform in {256^2, 512^2, 1024^2}, cameras uniform on the
+    radius-2 sphere, t uniform in [0,1], 256-entry transfer function) through the continuous-batching
+    server; latency from arrival to completion.  Also PSNR / max error of both forms on 1M held-out
+    points against the field."""
+    import torch
+    import synth
+    import paper_2507_03836_gb300 as fh
+    nx, ny, nz, nt = w["dims"]
+    m16 = fh.fhash_build(nx, ny, nz, nt, mask=mask, schedule=fh.make_schedule(**w["schedule"]), F=w["F"],
+                         dtype=fh.BF16, mlp_hidden_layers=w["hidden"], mlp_width=w["width"], seed=1 + rank,
+                         init_range=w["init_range"])
+    n_all = info["n_table_params"] + info["n_mlp_params"]
+    _copy_params(model, m16, n_all)
+
+    # precision: the same trained weights served in both forms, on 1M held-out points
+    held = synth.coords(777, 1 << 20)
+    truth = synth.sample(field, info["fbb_lo"], info["fbb_size"], held).astype(np.float64)
+    hd = torch.from_numpy(held).cuda()
+    prec = {"held_out_points": int(held.shape[0]), "reference": "field sampled at the held-out points"}
+    rngv = truth.max() - truth.min()
+    for name, mm in (("fp32", model), ("bf16", m16)):
+        o = torch.empty(held.shape[0], dtype=torch.float32, device="cuda")
+        fh.fhash_forward(mm, hd, o)
+        pred = o.cpu().numpy().astype(np.float64)
+        mse = np.mean((pred - truth) ** 2)
+        prec["psnr_" + name] = float(10 * np.log10(rngv ** 2 / mse))
+        prec["max_abs_err_" + name] = float(np.abs(pred - truth).max())
+    prec["psnr_drop_db"] = prec["psnr_fp32"] - prec["psnr_bf16"]
+
+    tf = torch.from_numpy(synth.transfer_function(0.5)).cuda()
+    rng = np.random.default_rng(1234)
+    n_req = args.serve_requests
+    arrivals = np.cumsum(rng.exponential(1.0 / args.serve_rate, n_req))
+    sizes = rng.choice([256, 512, 1024], n_req)
+    times = rng.random(n_req)
+    render = {"requests": n_req, "rate_req_s": args.serve_rate, "sizes": [256, 512, 1024],
+              "model": w["name"] + " after the timed training steps"}
+    outs = [torch.empty((int(s), int(s), 4), dtype=torch.float32, device="cuda") for s in sizes]
+    for name, mi in (("fp32", 0), ("bf16", 1)):
+        srv = fh.fhash_server_create([model, m16], budget_bytes=64 << 30, max_live=64, tick_samples=1 << 22)
+        # warm-up request (graph replays and kernels loaded)
+        cam = synth.camera(synth.sphere_eye(99, 0), 256, 256)
+        wid = fh.fhash_server_submit(srv, fh.make_request(fh.REQ_RENDER, mi, 0.5, cam, 256, 256, 64, tf, out=outs[0]))
+        while fh.fhash_server_poll(srv, wid)[0] != fh.REQ_DONE:
+            fh.fhash_server_tick(srv)
+        st0 = fh.fhash_server_get_stats(srv)
+        torch.cuda.synchronize()
+        lat = np.zeros(n_req)
+        done = np.zeros(n_req, bool)
+        ids = {}
+        nxt = 0
+        t0 = time.perf_counter()
+        while not done.all():
+            now = time.perf_counter() - t0
+            while nxt < n_req and arrivals[nxt] <= now:
+                s_ = int(sizes[nxt])
+                cam = synth.camera(synth.sphere_eye(7, nxt), s_, s_)
+                ids[nxt] = fh.fhash_server_submit(srv, fh.make_request(fh.REQ_RENDER, mi, float(times[nxt]), cam, s_, s_,
+                                                                       64, tf, out=outs[nxt]))
+                nxt += 1
+            if not ids or all(done[k] for k in ids):
+                time.sleep(max(0.0, min(arrivals[nxt] - (time.perf_counter() - t0), 0.01)) if nxt < n_req else 0)
+                continue
+            fh.fhash_server_tick(srv)
+            tnow = time.perf_counter() - t0
+            for k, rid in ids.items():
+                if not done[k] and fh.fhash_server_poll(srv, rid)[0] == fh.REQ_DONE:
+                    done[k] = True
+                    lat[k] = (tnow - arrivals[k]) * 1e3
+        elapsed = time.perf_counter() - t0
+        st = fh.fhash_server_get_stats(srv)
+        samples = st["samples"] - st0["samples"]
+        render[name] = {"p50_ms": float(np.percentile(lat, 50)), "p95_ms": float(np.percentile(lat, 95)),
+                        "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                        "throughput_samples_s": samples / elapsed, "requests_s": n_req / elapsed,
+                        "ticks": st["ticks"] - st0["ticks"], "graph_launches": st["model_launches"] - st0["model_launches"]}
+        del srv
+    del m16
+    return {"render": render, "precision": prec}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -152,6 +251,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=["large", "medium", "small"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving and precision legs")
+    ap.add_argument("--serve-requests", type=int, default=60)
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, requests/s")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -177,6 +279,7 @@ def main():
     model = fh.fhash_build(nx, ny, nz, nt, mask=mask, schedule=fh.make_schedule(**w["schedule"]), F=w["F"],
                            mlp_hidden_layers=w["hidden"], mlp_width=w["width"], seed=1 + rank,
                            init_range=w["init_range"])
+    mask_for_bf16 = mask if not args.no_serve else None
     del mask
     info = fh.fhash_get_info(model)
     setup_s = time.time() - t0
@@ -246,6 +349,11 @@ def main():
         e2e_s = float(t.item())
     fh.fhash_check(model)
 
+    serve = None
+    if not args.no_serve:
+        serve = serving_leg(args, w, model, info, field, mask_for_bf16, rank)
+    del mask_for_bf16
+
     n_params = info["n_table_params"] + info["n_mlp_params"]
     peaks, peak_kind = _peaks()
     adam_bytes = 32.0 * n_params  # read p, g, m, v; write p, m, v and the cleared g
@@ -263,7 +371,9 @@ def main():
         "phases_ms": {"encode_mlp_fwd_bwd_scatter": grads_ms, "adam": adam_ms},
         "gpu_launches": K * (4 + 2 * (w["hidden"] + 1)),
         "roofline": {"kernel": "k_adam", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                     "traffic": ADAM_DRAM_BYTES_PER_PARAM * n_params,
+                     "traffic_note": "ncu dram__bytes_read+write of k_adam on advect-128^3x32, scaled by parameters",
                      "peak_source": peak_kind, "bytes_per_launch": adam_bytes},
         "clocks": clk,
         "e2e": {"value": world * B * K / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": B * 20,
@@ -271,6 +381,9 @@ def main():
         "loss_first_last": [float(losses[0]), float(losses[-1])],
         "setup_s": setup_s,
     }
+    if serve:
+        out["render"] = serve["render"]
+        out["precision"] = serve["precision"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t, desc = oracle_step_sample(w, 32768, adam_slice=1 << 25)
         out["cpu_baseline"] = {"value": B / t, "unit": "samples/s", "cores": 1, "kind": "oracle", "sample": desc}
