@@ -103,7 +103,10 @@ def encode_backward(levels, level_bases, coords, d_enc, F):
         all_vals.append((wts[:, :, None] * g[:, None, :]).reshape(-1, F))
     rows = np.concatenate(all_rows)
     vals = np.concatenate(all_vals)
-    uniq, inv = np.unique(rows, return_inverse=True)
-    grad = np.zeros((uniq.size, F), np.float64)
-    np.add.at(grad, inv, vals)
+    # per-row sums of the contributions: sort by row, then sum each run of equal rows
+    order = np.argsort(rows, kind="stable")
+    rs = rows[order]
+    starts = np.flatnonzero(np.concatenate([[True], rs[1:] != rs[:-1]]))
+    uniq = rs[starts]
+    grad = np.stack([np.add.reduceat(vals[order, f], starts) for f in range(F)], 1)
     return uniq, grad

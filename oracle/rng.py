@@ -45,3 +45,15 @@ class InitTable:
         rows = np.asarray(rows, np.int64)
         idx = (rows[..., None] * self.F + np.arange(self.F)).astype(np.uint64)
         return uniform_range(self.seed, 200, idx, -self.r, self.r)
+
+
+def init_mlp(seed, dims):
+    """Initial MLP parameters as the library draws them: layer k's W[out][in] from stream 300 + 2k and
+    b[out] from stream 301 + 2k, U(-1/sqrt(fan_in), 1/sqrt(fan_in)); flat layer by layer."""
+    parts = []
+    for k in range(len(dims) - 1):
+        fi, fo = dims[k], dims[k + 1]
+        b = 1.0 / np.sqrt(fi)
+        parts.append(uniform_range(seed, 300 + 2 * k, np.arange(fo * fi, dtype=np.uint64), -b, b))
+        parts.append(uniform_range(seed, 301 + 2 * k, np.arange(fo, dtype=np.uint64), -b, b))
+    return np.concatenate(parts)

@@ -160,8 +160,9 @@ fhash_status launch_encode(fhash_model* m, const float* coords, int64_t n, float
 fhash_status launch_forward(fhash_model* m, const float* coords, int64_t n, float* out, cudaStream_t st);
 fhash_status launch_forward_seg(fhash_model* m, const float* coords, float* out, const int64_t* seg, int64_t max_n,
                                 cudaStream_t st);
-fhash_status launch_grads(fhash_model* m, const float* coords, const float* target, int64_t n, double* loss_dev,
-                          cudaStream_t st);
+// Forward + loss + backward into the gradient buffer (csrc/train.cu).
+fhash_status launch_grads2(fhash_model* m, const float* coords, const float* target, int64_t n, double* loss_dev,
+                           cudaStream_t st);
 fhash_status launch_adam(fhash_model* m, const fhash_adam* a, cudaStream_t st);
 fhash_status refresh_shadow(fhash_model* m, uint64_t off, uint64_t n, cudaStream_t st);
 

@@ -210,65 +210,6 @@ fhash_status launch_forward_seg(fhash_model* m, const float* coords, float* out,
     return FHASH_OK;
 }
 
-fhash_status launch_grads(fhash_model* m, const float* coords, const float* target, int64_t n, double* loss_dev,
-                          cudaStream_t st) {
-    const MlpShape& sh = m->mlp;
-    const int W = sh.width;
-    const int64_t A = sh.in + (int64_t)sh.nh * W;  // activation rows
-    const int64_t D = (int64_t)sh.nh * W + 1;       // delta rows
-    FH_TRY(grow(m, m->s_acts, (size_t)(A * n * 4)));
-    FH_TRY(grow(m, m->s_gacts, (size_t)((D + 1) * n * 4)));
-    const int nb_loss = m->shadow ? tc_grid(n)
-                                  : (int)std::max<int64_t>(1, std::min<int64_t>((n + TB - 1) / TB, (int64_t)num_sms() * 16));
-    const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 2));
-    const int64_t chunk = ((n + nchunk - 1) / nchunk + 31) / 32 * 32;
-    int ne_max = 0;
-    for (int j = 0; j <= sh.nh; ++j) {
-        int fi = j == 0 ? sh.in : W, fo = j == sh.nh ? 1 : W;
-        ne_max = std::max(ne_max, fo * fi + fo);
-    }
-    FH_TRY(grow(m, m->s_partial, (size_t)nchunk * ne_max * 4 + (size_t)nb_loss * 8 + 64));
-    FH_TRY(grow(m, m->s_loss, 64));
-    float* acts = (float*)m->s_acts.p;
-    float* gy = (float*)m->s_gacts.p;
-    float* dl = gy + n;
-    double* lpart = (double*)m->s_partial.p;
-    float* wpart = (float*)((char*)m->s_partial.p + ((size_t)nb_loss * 8 + 63) / 64 * 64);
-
-    FusedArgs a{};
-    a.coords = coords;
-    a.target = target;
-    a.n = n;
-    a.acts = acts;
-    a.gy = gy;
-    a.dl = dl;
-    a.partial = lpart;
-    a.st = st;
-    if (m->shadow) {  // precision form: bf16 forward on the tensor cores, float32 backward
-        a.grid = nb_loss;
-        FH_CUDA(run_tc_any(m, true, a));
-    } else {
-        FH_CUDA(dispatch_fused(m, 1, a));
-    }
-    if (a.grid != nb_loss) return set_error(FHASH_ECUDA, "internal: loss grid mismatch");
-    k_loss<<<1, 256, 0, st>>>(lpart, nb_loss, n, loss_dev ? loss_dev : (double*)m->s_loss.p);
-    FH_CUDA(cudaGetLastError());
-    a.grid = 0;
-    FH_CUDA(dispatch_fused(m, 2, a));
-    // weight gradients, layer by layer
-    float* gm = m->grad + m->n_table;
-    for (int j = 0; j <= sh.nh; ++j) {
-        int fi = j == 0 ? sh.in : W, fo = j == sh.nh ? 1 : W;
-        const float* aj = (j == 0) ? acts : acts + (int64_t)(sh.in + (j - 1) * W) * n;
-        const float* dj = dl + (int64_t)j * W * n;
-        k_dw_partial<<<nchunk, 256, 0, st>>>(aj, dj, fi, fo, n, chunk, wpart);
-        int ne = fo * fi + fo;
-        k_dw_reduce<<<(ne + 255) / 256, 256, 0, st>>>(wpart, nchunk, ne, gm + sh.w_off[j]);
-    }
-    FH_CUDA(cudaGetLastError());
-    return FHASH_OK;
-}
-
 fhash_status launch_adam(fhash_model* m, const fhash_adam* ad, cudaStream_t st) {
     m->step += 1;
     const double k = (double)m->step;
@@ -344,7 +285,7 @@ fhash_status fhash_compute_grads(fhash_model* m, const float* coords, const floa
     FH_TRY(stage_in(m, m->s_target, target, (size_t)n * 4, st, &dt));
     FH_TRY(grow(m, m->s_loss, 64));
     bool dev_loss = loss && is_device_ptr(loss);
-    FH_TRY(launch_grads(m, (const float*)dc, (const float*)dt, n, dev_loss ? loss : (double*)m->s_loss.p, st));
+    FH_TRY(launch_grads2(m, (const float*)dc, (const float*)dt, n, dev_loss ? loss : (double*)m->s_loss.p, st));
     if (loss && !dev_loss) {
         FH_CUDA(cudaMemcpyAsync(loss, m->s_loss.p, 8, cudaMemcpyDeviceToHost, st));
         FH_CUDA(cudaStreamSynchronize(st));
@@ -371,7 +312,7 @@ fhash_status fhash_train_step(fhash_model* m, const float* coords, const float* 
     FH_TRY(stage_in(m, m->s_target, target, (size_t)n * 4, st, &dt));
     FH_TRY(grow(m, m->s_loss, 64));
     bool dev_loss = loss && is_device_ptr(loss);
-    FH_TRY(launch_grads(m, (const float*)dc, (const float*)dt, n, dev_loss ? loss : (double*)m->s_loss.p, st));
+    FH_TRY(launch_grads2(m, (const float*)dc, (const float*)dt, n, dev_loss ? loss : (double*)m->s_loss.p, st));
     FH_TRY(fhash_apply_adam(m, a, stream));
     if (loss && !dev_loss) {
         FH_CUDA(cudaMemcpyAsync(loss, m->s_loss.p, 8, cudaMemcpyDeviceToHost, st));

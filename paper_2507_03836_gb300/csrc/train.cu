@@ -1,0 +1,433 @@
+// Training pass split by access pattern (float32 and the backward of the bf16 form):
+//   k_encode_cols   level-major gathers (thread per level and sample), encoding to global columns;
+//   k_mlp_fwd_g     MLP forward + MSE from those columns (weights in shared memory, activations in
+//                   registers and global columns), dL/dy and float64 loss partials;
+//   k_mlp_bwd_g     MLP backward data path: deltas per layer and d(loss)/d(encoding) to global columns;
+//   k_scatter_cols  backward of Eqs. 10-12: level-major vector reductions into the table gradient, with
+//                   coarse levels accumulated in shared memory first (privatised) to avoid thousands of
+//                   same-address atomics per row;
+//   k_dw_tiles      weight gradients over the batch, 4 x 4 register tiles per thread.
+// The gather and scatter kernels carry no MLP state, so they run at full occupancy.
+#include <math.h>
+
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace fh {
+
+// ------------------------------------------------------------------ gathers / scatters (level-major)
+template <int F>
+__global__ void __launch_bounds__(256) k_encode_cols(const __grid_constant__ Levels lv, const float* __restrict__ T,
+                                                     const float* __restrict__ coords, int64_t n, float* __restrict__ enc) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * lv.L) return;
+    const int l = (int)(idx / n);
+    const int64_t s = idx - (int64_t)l * n;
+    Corners k = corners(lv.lv[l], load_coord(coords, s));
+    float o[F];
+    interp_level<F>(T, k, o);
+#pragma unroll
+    for (int f = 0; f < F; ++f) enc[(int64_t)(l * F + f) * n + s] = o[f];
+}
+
+template <int F>
+__device__ __forceinline__ void red_row(float* dst, float w, const float (&g)[F]) {
+    if constexpr (F == 2) {
+        red_add2(dst, w * g[0], w * g[1]);
+    } else if constexpr (F == 4) {
+        red_add4(dst, w * g[0], w * g[1], w * g[2], w * g[3]);
+    } else if constexpr (F == 8) {
+        red_add4(dst, w * g[0], w * g[1], w * g[2], w * g[3]);
+        red_add4(dst + 4, w * g[4], w * g[5], w * g[6], w * g[7]);
+    } else {
+#pragma unroll
+        for (int f = 0; f < F; ++f) red_add(dst + f, w * g[f]);
+    }
+}
+
+// Blocks [first[l], first[l+1]) serve level l, `per[l]` samples each; priv[l] = 1 when the whole level
+// table (rows*F floats) is accumulated in shared memory by each block before one flush.
+struct ScatterPlan {
+    int32_t first[FHASH_MAX_LEVELS + 1];
+    int64_t per[FHASH_MAX_LEVELS];
+    int32_t priv[FHASH_MAX_LEVELS];
+};
+
+template <int F>
+__global__ void __launch_bounds__(256) k_scatter_cols(const __grid_constant__ Levels lv, const __grid_constant__ ScatterPlan P,
+                                                      float* __restrict__ G, const float* __restrict__ coords, int64_t n,
+                                                      const float* __restrict__ denc) {
+    extern __shared__ float acc[];
+    int l = 0;
+    while (l + 1 < lv.L && (int)blockIdx.x >= P.first[l + 1]) ++l;
+    const int64_t s0 = (int64_t)(blockIdx.x - P.first[l]) * P.per[l];
+    const int64_t s1 = min(n, s0 + P.per[l]);
+    const Level& L = lv.lv[l];
+    if (P.priv[l]) {
+        const int64_t nrow = (int64_t)L.st * L.R[3];
+        for (int64_t e = threadIdx.x; e < nrow * F; e += blockDim.x) acc[e] = 0.0f;
+        __syncthreads();
+        for (int64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+            Corners k = corners(L, load_coord(coords, s));
+            float g[F];
+#pragma unroll
+            for (int f = 0; f < F; ++f) g[f] = denc[(int64_t)(l * F + f) * n + s];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const float w = corner_weight(k, c);
+                float* dst = acc + (corner_row(k, c) - L.base) * F;
+#pragma unroll
+                for (int f = 0; f < F; ++f) atomicAdd(dst + f, w * g[f]);
+            }
+        }
+        __syncthreads();
+        float* Gl = G + L.base * F;
+        for (int64_t e = threadIdx.x; e < nrow * F; e += blockDim.x)
+            if (acc[e] != 0.0f) red_add(Gl + e, acc[e]);
+    } else {
+        const int64_t s = s0 + threadIdx.x;
+        if (s >= s1) return;
+        Corners k = corners(L, load_coord(coords, s));
+        float g[F];
+#pragma unroll
+        for (int f = 0; f < F; ++f) g[f] = denc[(int64_t)(l * F + f) * n + s];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) red_row<F>(G + corner_row(k, c) * F, corner_weight(k, c), g);
+    }
+}
+
+// ------------------------------------------------------------------ MLP, activations in registers
+// Forward weights transposed (Wt[in][out]) and backward weights row-major (W[out][in]) in shared memory.
+struct GLayout {
+    int wt[FHASH_MAX_HIDDEN + 1], wr[FHASH_MAX_HIDDEN + 1], b[FHASH_MAX_HIDDEN + 1], floats;
+};
+
+__host__ __device__ inline GLayout g_layout(const MlpShape& sh) {
+    GLayout L{};
+    int off = 0;
+    for (int k = 0; k <= sh.nh; ++k) {
+        const int fi = k == 0 ? sh.in : sh.width, fo = k == sh.nh ? 1 : sh.width;
+        const int n4 = (fi * fo + 3) / 4 * 4;
+        L.wt[k] = off; off += n4;
+        L.wr[k] = off; off += fo * ((fi + 3) / 4 * 4);  // rows padded to a multiple of 4
+        L.b[k] = off; off += (fo + 3) / 4 * 4;
+    }
+    L.floats = off;
+    return L;
+}
+
+__device__ inline void g_load(const float* __restrict__ g, const MlpShape& sh, const GLayout& L, float* s) {
+    for (int k = 0; k <= sh.nh; ++k) {
+        const int fi = k == 0 ? sh.in : sh.width, fo = k == sh.nh ? 1 : sh.width;
+        const int fi4 = (fi + 3) / 4 * 4;
+        for (int e = threadIdx.x; e < fi4 * fo; e += blockDim.x) {
+            const int o = e / fi4, i = e % fi4;
+            const float w = (i < fi) ? g[sh.w_off[k] + o * fi + i] : 0.0f;
+            if (i < fi) s[L.wt[k] + i * fo + o] = w;
+            s[L.wr[k] + e] = w;
+        }
+        for (int e = threadIdx.x; e < fo; e += blockDim.x) s[L.b[k] + e] = g[sh.b_off[k] + e];
+    }
+}
+
+// acc[o] = b[o] + sum_i Wt[i][o] x[i * xs], o < fo (fo a multiple of 4, at most 64): one load of each
+// input, 16 float4 weight broadcasts per input.
+__device__ __forceinline__ void dense_g(const float* __restrict__ Wt, const float* __restrict__ b, int fi, int fo,
+                                        const float* __restrict__ x, int64_t xs, float (&acc)[64]) {
+#pragma unroll
+    for (int o = 0; o < 64; ++o) acc[o] = (o < fo) ? b[o] : 0.0f;
+#pragma unroll 2
+    for (int i = 0; i < fi; ++i) {
+        const float xv = x[i * xs];
+        const float4* w4 = reinterpret_cast<const float4*>(Wt + i * fo);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            if (4 * q < fo) {
+                const float4 w = w4[q];
+                acc[4 * q + 0] = fmaf(w.x, xv, acc[4 * q + 0]);
+                acc[4 * q + 1] = fmaf(w.y, xv, acc[4 * q + 1]);
+                acc[4 * q + 2] = fmaf(w.z, xv, acc[4 * q + 2]);
+                acc[4 * q + 3] = fmaf(w.w, xv, acc[4 * q + 3]);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) k_mlp_fwd_g(const __grid_constant__ MlpShape sh, const float* __restrict__ Pm,
+                                                   const float* __restrict__ target, int64_t n, float two_over_n,
+                                                   float* __restrict__ acts, float* __restrict__ gy,
+                                                   double* __restrict__ partial) {
+    extern __shared__ float4 sm4[];
+    float* s = reinterpret_cast<float*>(sm4);
+    const GLayout L = g_layout(sh);
+    g_load(Pm, sh, L, s);
+    __syncthreads();
+    const int W = sh.width;
+    double lsum = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float acc[64];
+        const float* x = acts + i;
+        for (int k = 0; k < sh.nh; ++k) {
+            const int fi = k == 0 ? sh.in : W;
+            dense_g(s + L.wt[k], s + L.b[k], fi, W, x, n, acc);
+            float* y = acts + (int64_t)(sh.in + k * W) * n + i;
+#pragma unroll
+            for (int o = 0; o < 64; ++o)
+                if (o < W) y[(int64_t)o * n] = fmaxf(acc[o], 0.0f);
+            x = y;
+        }
+        // output layer from the last hidden activations (still in registers)
+        const float* wo = s + L.wt[sh.nh];
+        float yv = s[L.b[sh.nh]];
+#pragma unroll
+        for (int o = 0; o < 64; ++o)
+            if (o < W) yv = fmaf(wo[o], fmaxf(acc[o], 0.0f), yv);
+        const float r = yv - __ldg(target + i);
+        gy[i] = two_over_n * r;
+        lsum += (double)r * (double)r;
+    }
+    const double t = block_sum(lsum);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+// dl[(j*W + o) * n + i] = delta of layer j's output (the output layer's at row nh*W); denc[c * n + i] =
+// d(loss)/d(encoding c).
+__global__ void __launch_bounds__(128) k_mlp_bwd_g(const __grid_constant__ MlpShape sh, const float* __restrict__ Pm,
+                                                   int64_t n, const float* __restrict__ acts, const float* __restrict__ gy,
+                                                   float* __restrict__ dl, float* __restrict__ denc) {
+    extern __shared__ float4 sm4[];
+    float* s = reinterpret_cast<float*>(sm4);
+    const GLayout L = g_layout(sh);
+    g_load(Pm, sh, L, s);
+    __syncthreads();
+    const int W = sh.width;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float g = gy[i];
+        dl[(int64_t)(sh.nh * W) * n + i] = g;
+        const float* wo = s + L.wt[sh.nh];  // output layer: W[0][o], same in both layouts
+        const float* a = acts + (int64_t)(sh.in + (sh.nh - 1) * W) * n + i;
+        float* d = dl + (int64_t)((sh.nh - 1) * W) * n + i;
+        for (int o = 0; o < W; ++o) d[(int64_t)o * n] = (a[(int64_t)o * n] > 0.0f) ? wo[o] * g : 0.0f;
+        for (int j = sh.nh - 1; j >= 0; --j) {
+            // p[c] = sum_o W_j[o][c] delta_j[o], outer-product order: one load of each delta
+            const int fi = j == 0 ? sh.in : W, fi4 = (fi + 3) / 4 * 4;
+            const float* Wr = s + L.wr[j];
+            const float* dj = dl + (int64_t)(j * W) * n + i;
+            float p[64];
+#pragma unroll
+            for (int c = 0; c < 64; ++c) p[c] = 0.0f;
+#pragma unroll 2
+            for (int o = 0; o < W; ++o) {
+                const float dv = dj[(int64_t)o * n];
+                const float4* row = reinterpret_cast<const float4*>(Wr + o * fi4);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    if (4 * q < fi4) {
+                        const float4 w = row[q];
+                        p[4 * q + 0] = fmaf(w.x, dv, p[4 * q + 0]);
+                        p[4 * q + 1] = fmaf(w.y, dv, p[4 * q + 1]);
+                        p[4 * q + 2] = fmaf(w.z, dv, p[4 * q + 2]);
+                        p[4 * q + 3] = fmaf(w.w, dv, p[4 * q + 3]);
+                    }
+                }
+            }
+            if (j > 0) {
+                const float* aj = acts + (int64_t)(sh.in + (j - 1) * W) * n + i;
+                float* dn = dl + (int64_t)((j - 1) * W) * n + i;
+#pragma unroll
+                for (int c = 0; c < 64; ++c)
+                    if (c < W) dn[(int64_t)c * n] = (aj[(int64_t)c * n] > 0.0f) ? p[c] : 0.0f;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 64; ++c)
+                    if (c < fi) denc[(int64_t)c * n + i] = p[c];
+            }
+        }
+    }
+}
+
+// Weight gradient partials of one layer over a chunk of samples: thread (ob, ib) owns the 4 x 4 tile
+// dW[4ob..4ob+3][4ib..4ib+3] (and db of its rows when ib == 0).  partial[chunk][e] as k_dw_partial.
+__global__ void __launch_bounds__(256) k_dw_tiles(const float* __restrict__ a, const float* __restrict__ d, int fi, int fo,
+                                                  int64_t n, int64_t chunk, float* __restrict__ partial) {
+    constexpr int TS = 32;
+    __shared__ float sa[64][TS + 1];
+    __shared__ float sd[64][TS + 1];
+    const int nig = (fi + 3) / 4, nob = (fo + 3) / 4;
+    const int ob = threadIdx.x / nig, ib = threadIdx.x % nig;
+    const bool active = threadIdx.x < nob * nig;
+    const int64_t n0 = blockIdx.x * chunk, n1 = min(n, n0 + chunk);
+    float acc[4][4] = {}, bacc[4] = {};
+    for (int64_t t0 = n0; t0 < n1; t0 += TS) {
+        __syncthreads();
+        for (int q = threadIdx.x; q < (fi + fo) * TS; q += blockDim.x) {
+            const int r = q / TS, c = q % TS;
+            const int64_t smp = t0 + c;
+            float v = 0.0f;
+            if (smp < n1) v = (r < fi) ? a[(int64_t)r * n + smp] : d[(int64_t)(r - fi) * n + smp];
+            if (r < fi) sa[r][c] = v; else sd[r - fi][c] = v;
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll 4
+            for (int c = 0; c < TS; ++c) {
+                float dv[4], av[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    dv[u] = (4 * ob + u < fo) ? sd[4 * ob + u][c] : 0.0f;
+                    av[u] = (4 * ib + u < fi) ? sa[4 * ib + u][c] : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(dv[u], av[v], acc[u][v]);
+                    bacc[u] += dv[u];
+                }
+            }
+        }
+    }
+    if (!active) return;
+    const int ne = fo * fi + fo;
+    float* out = partial + (int64_t)blockIdx.x * ne;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int o = 4 * ob + u;
+        if (o >= fo) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int i = 4 * ib + v;
+            if (i < fi) out[o * fi + i] = acc[u][v];
+        }
+        if (ib == 0) out[fo * fi + o] = bacc[u];
+    }
+}
+
+__global__ void k_dw_reduce2(const float* __restrict__ partial, int nchunk, int ne, float* __restrict__ grad) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    float s = 0.0f;
+    for (int c = 0; c < nchunk; ++c) s += partial[(int64_t)c * ne + e];
+    grad[e] += s;
+}
+
+__global__ void k_loss2(const double* __restrict__ partial, int nb, int64_t n, double* __restrict__ loss) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partial[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = red[0] / (double)n;
+}
+
+cudaError_t run_tc_any(fhash_model* m, bool train, const FusedArgs& a);
+int tc_grid(int64_t n);
+
+template <int F>
+static cudaError_t scatter_launch(fhash_model* m, const float* coords, int64_t n, const float* denc, cudaStream_t st) {
+    constexpr int64_t kPrivMax = 16384;  // floats of a level accumulated in shared memory (64 KB)
+    ScatterPlan P{};
+    int blocks = 0;
+    int64_t priv_floats = 0;
+    for (int l = 0; l < m->lv.L; ++l) {
+        const Level& L = m->lv.lv[l];
+        const int64_t fl = (int64_t)L.st * L.R[3] * F;
+        P.first[l] = blocks;
+        if (fl <= kPrivMax) {
+            P.priv[l] = 1;
+            P.per[l] = std::max<int64_t>(2048, (n + 63) / 64);  // at most 64 flushes of the level
+            priv_floats = std::max(priv_floats, fl);
+        } else {
+            P.priv[l] = 0;
+            P.per[l] = 256;
+        }
+        blocks += (int)((n + P.per[l] - 1) / P.per[l]);
+    }
+    P.first[m->lv.L] = blocks;
+    const int smem = (int)(priv_floats * 4);
+    cudaError_t e = cudaFuncSetAttribute((const void*)k_scatter_cols<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         std::max(smem, 1));
+    if (e != cudaSuccess) return e;
+    k_scatter_cols<F><<<blocks, 256, smem, st>>>(m->lv, P, m->grad, coords, n, denc);
+    return cudaGetLastError();
+}
+
+fhash_status launch_grads2(fhash_model* m, const float* coords, const float* target, int64_t n, double* loss_dev,
+                           cudaStream_t st) {
+    const MlpShape& sh = m->mlp;
+    const int W = sh.width, F = m->lv.F;
+    const int64_t A = sh.in + (int64_t)sh.nh * W;  // activation rows
+    const int64_t D = (int64_t)sh.nh * W + 1;       // delta rows
+    FH_TRY(grow(m, m->s_acts, (size_t)(A * n * 4)));
+    FH_TRY(grow(m, m->s_gacts, (size_t)((D + 1 + sh.in) * n * 4)));
+    const int nb = m->shadow ? tc_grid(n)
+                             : (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, (int64_t)num_sms() * 8));
+    const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, (int64_t)num_sms() * 2));
+    const int64_t chunk = ((n + nchunk - 1) / nchunk + 31) / 32 * 32;
+    int ne_max = 0;
+    for (int j = 0; j <= sh.nh; ++j) {
+        const int fi = j == 0 ? sh.in : W, fo = j == sh.nh ? 1 : W;
+        ne_max = std::max(ne_max, fo * fi + fo);
+    }
+    FH_TRY(grow(m, m->s_partial, (size_t)nchunk * ne_max * 4 + (size_t)nb * 8 + 64));
+    float* acts = (float*)m->s_acts.p;
+    float* gy = (float*)m->s_gacts.p;
+    float* dl = gy + n;
+    float* denc = dl + D * n;
+    double* lpart = (double*)m->s_partial.p;
+    float* wpart = (float*)((char*)m->s_partial.p + ((size_t)nb * 8 + 63) / 64 * 64);
+    const float* Pm = m->param + m->n_table;
+    const GLayout GL = g_layout(sh);
+    const int gsmem = GL.floats * 4;
+
+    // forward: encoding + MLP (bf16 form: one tensor-core kernel writes the same activations)
+    if (m->shadow) {
+        FusedArgs a{};
+        a.coords = coords; a.target = target; a.n = n; a.acts = acts; a.gy = gy; a.partial = lpart; a.st = st;
+        a.grid = nb;
+        FH_CUDA(run_tc_any(m, true, a));
+    } else {
+        const unsigned eg = (unsigned)((n * m->lv.L + 255) / 256);
+        switch (F) {
+            case 1: k_encode_cols<1><<<eg, 256, 0, st>>>(m->lv, m->param, coords, n, acts); break;
+            case 2: k_encode_cols<2><<<eg, 256, 0, st>>>(m->lv, m->param, coords, n, acts); break;
+            case 4: k_encode_cols<4><<<eg, 256, 0, st>>>(m->lv, m->param, coords, n, acts); break;
+            case 8: k_encode_cols<8><<<eg, 256, 0, st>>>(m->lv, m->param, coords, n, acts); break;
+            default: return set_error(FHASH_EINVAL, "F=%d unsupported", F);
+        }
+        FH_CUDA(cudaGetLastError());
+        FH_CUDA(cudaFuncSetAttribute((const void*)k_mlp_fwd_g, cudaFuncAttributeMaxDynamicSharedMemorySize, gsmem));
+        k_mlp_fwd_g<<<nb, 128, gsmem, st>>>(sh, Pm, target, n, 2.0f / (float)n, acts, gy, lpart);
+        FH_CUDA(cudaGetLastError());
+    }
+    k_loss2<<<1, 256, 0, st>>>(lpart, nb, n, loss_dev);
+    FH_CUDA(cudaGetLastError());
+    // backward: MLP data path, table scatter, weight gradients
+    const int bb = (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, (int64_t)num_sms() * 8));
+    FH_CUDA(cudaFuncSetAttribute((const void*)k_mlp_bwd_g, cudaFuncAttributeMaxDynamicSharedMemorySize, gsmem));
+    k_mlp_bwd_g<<<bb, 128, gsmem, st>>>(sh, Pm, n, acts, gy, dl, denc);
+    FH_CUDA(cudaGetLastError());
+    switch (F) {
+        case 1: FH_CUDA(scatter_launch<1>(m, coords, n, denc, st)); break;
+        case 2: FH_CUDA(scatter_launch<2>(m, coords, n, denc, st)); break;
+        case 4: FH_CUDA(scatter_launch<4>(m, coords, n, denc, st)); break;
+        case 8: FH_CUDA(scatter_launch<8>(m, coords, n, denc, st)); break;
+    }
+    float* gm = m->grad + m->n_table;
+    for (int j = 0; j <= sh.nh; ++j) {
+        const int fi = j == 0 ? sh.in : W, fo = j == sh.nh ? 1 : W;
+        const float* aj = (j == 0) ? acts : acts + (int64_t)(sh.in + (j - 1) * W) * n;
+        const float* dj = dl + (int64_t)j * W * n;
+        k_dw_tiles<<<nchunk, 256, 0, st>>>(aj, dj, fi, fo, n, chunk, wpart);
+        const int ne = fo * fi + fo;
+        k_dw_reduce2<<<(ne + 255) / 256, 256, 0, st>>>(wpart, nchunk, ne, gm + sh.w_off[j]);
+    }
+    FH_CUDA(cudaGetLastError());
+    return FHASH_OK;
+}
+
+}  // namespace fh

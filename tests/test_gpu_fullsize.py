@@ -1,0 +1,111 @@
+"""Parity at the full size of the bench workload (advect-256^3x64: 16 levels up to 256^3 x 64, F=2,
+3.56e9 parameters, batch 2^18), in the launch configuration bench.py times.
+
+The oracle computes only what it can afford, from its own inputs: initial tables and MLP from its own
+SplitMix64 (the library's documented initialisation), the seeded field and mask from synth.  Checked:
+- the Feature Bounding Box and two time steps of the occupancy grid, bit-exact;
+- forward outputs on 4096 sampled points, within 1e-4 x max(|o|, RMS(o));
+- the full-batch loss of one training step, within 1e-5 relative;
+- MLP gradients and the table gradient on 20000 sampled touched rows, within 1e-4 x the sum of
+  the magnitudes of their terms; 2000 sampled untouched rows exactly zero;
+- the Adam update of the same rows, fed the same gradient, within 1e-6 x lr + 3e-7 x |p|.
+"""
+import numpy as np
+import pytest
+
+import synth
+from synth import workloads
+from oracle import adam, encode, index, mlp, rng, schedule, train
+
+from _util import fh, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+W = workloads.LARGE
+SEED = 3
+HP32 = tuple(float(np.float32(x)) for x in W["adam"])
+R32 = float(np.float32(W["init_range"]))
+
+
+@pytest.fixture(scope="module")
+def large():
+    f, m = workloads.make_field_and_mask(W)
+    nx, ny, nz, nt = W["dims"]
+    model = fh().fhash_build(nx, ny, nz, nt, mask=m, schedule=fh().make_schedule(**W["schedule"]), F=W["F"],
+                             mlp_hidden_layers=W["hidden"], mlp_width=W["width"], seed=SEED, init_range=W["init_range"])
+    return dict(field=f, mask=m, model=model, info=fh().fhash_get_info(model))
+
+
+def test_fullsize_build(large):
+    info = large["info"]
+    lv = schedule.geometric_schedule(W["schedule"]["r0"], W["schedule"]["r1"], W["schedule"]["n_levels"])
+    b, total = schedule.bases(lv)
+    assert info["res"] == lv and info["base"] == b and info["total_rows"] == total == 1778559385
+    d = index.dilate(large["mask"])
+    lo, size = index.fbb(d)
+    assert info["fbb_lo"] == lo and info["fbb_size"] == size
+    occ = index.occupancy(d, lo, size)
+    for t in (0, 37):
+        got = np.empty((size[2], size[1], size[0]), np.uint8)
+        fh().fhash_read_occupancy(large["model"], t, got)
+        assert np.array_equal(got.astype(bool), occ[t]), t
+
+
+def test_fullsize_forward_train_step(large):
+    info, model = large["info"], large["model"]
+    lv, b, F, dims = info["res"], info["base"], info["F"], info["mlp_dims"]
+    table = rng.InitTable(SEED, F, R32)
+    p = rng.init_mlp(SEED, dims)
+    n_t = info["n_table_params"]
+
+    # forward on sampled points
+    c = synth.coords(31, 4096)
+    out = torch().empty(c.shape[0], dtype=torch().float32, device="cuda")
+    fh().fhash_forward(model, to_dev(c), out)
+    ref = mlp.forward(p, dims, encode.encode(lv, b, c, table))[0]
+    tol = 1e-4 * np.maximum(np.abs(ref), np.sqrt(np.mean(ref ** 2)))
+    assert (np.abs(out.cpu().numpy() - ref) <= tol).all()
+
+    # one full training step at the bench's batch
+    B = W["batch"]
+    c = synth.coords(10_000, B)
+    tgt = synth.sample(large["field"], info["fbb_lo"], info["fbb_size"], c)
+    loss = np.zeros(1, np.float64)
+    fh().fhash_compute_grads(model, to_dev(c), to_dev(tgt), loss)
+    L, _, g_mlp, (rows, g_rows) = train.loss_and_grads(lv, b, F, dims, table, p, c, tgt)
+    assert abs(loss[0] - L) <= 1e-5 * L, (loss[0], L)
+
+    g_dev = np.empty(info["n_mlp_params"], np.float32)
+    fh().fhash_read_state(model, fh().STATE_GRAD, n_t, g_dev)
+    enc = encode.encode(lv, b, c, table)
+    y, a, z = mlp.forward(p, dims, enc)
+    _, gy = mlp.mse(y, tgt)
+    abs_mlp, abs_denc = mlp.backward(np.abs(p), dims, [np.abs(x) for x in a], [np.where(x > 0, 1.0, -1.0) for x in z],
+                                     np.abs(gy))
+    assert (np.abs(g_dev - g_mlp) <= 1e-4 * abs_mlp + 1e-12).all()
+
+    r_abs, g_abs = encode.encode_backward(lv, b, c, abs_denc, F)
+    assert np.array_equal(r_abs, rows)
+    pick = np.random.default_rng(0).choice(rows.size, 20000, replace=False)
+    touched = rows[pick]
+    gt = np.empty((touched.size, F), np.float32)
+    one = np.empty(F, np.float32)
+    for k, r in enumerate(touched):
+        fh().fhash_read_state(model, fh().STATE_GRAD, int(r) * F, one)
+        gt[k] = one
+    assert (np.abs(gt - g_rows[pick]) <= 1e-4 * g_abs[pick] + 1e-12).all()
+    cand = np.random.default_rng(1).integers(0, info["total_rows"], 40000)
+    untouched = cand[~np.isin(cand, rows)][:2000]
+    for r in untouched:
+        fh().fhash_read_state(model, fh().STATE_GRAD, int(r) * F, one)
+        assert (one == 0).all()
+
+    # Adam on the same rows, same gradient
+    fh().fhash_apply_adam(model, HP32)
+    p0 = table[touched].astype(np.float64)
+    p1, _, _ = adam.step(p0, gt.astype(np.float64), np.zeros_like(p0), np.zeros_like(p0), 1, *HP32)
+    got = np.empty_like(gt)
+    for k, r in enumerate(touched):
+        fh().fhash_read_state(model, fh().STATE_PARAM, int(r) * F, one)
+        got[k] = one
+    assert (np.abs(got - p1) <= 1e-6 * HP32[0] + 3e-7 * np.abs(p1)).all()
+    fh().fhash_check(model)

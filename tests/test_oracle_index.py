@@ -54,3 +54,8 @@ def test_init_table_matches_input_generator():
     rows = np.array([0, 1, 7, 1000])
     ref = synth.init_tables(5, 2002).reshape(-1, 2)[rows]
     assert np.array_equal(t[rows], ref)
+
+
+def test_init_mlp_matches_input_generator():
+    for dims in ([8, 32, 32, 1], [32, 64, 64, 1], [64, 64, 64, 64, 1]):
+        assert np.array_equal(rng.init_mlp(9, dims), synth.init_mlp(9, dims))
