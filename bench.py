@@ -251,6 +251,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=["large", "medium", "small"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"],
+                    help="training form: float32, or the bf16 precision form (tensor-core MLP)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving and precision legs")
     ap.add_argument("--serve-requests", type=int, default=60)
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, requests/s")
@@ -277,6 +279,7 @@ def main():
     field, mask = workloads.make_field_and_mask(w)
     nx, ny, nz, nt = w["dims"]
     model = fh.fhash_build(nx, ny, nz, nt, mask=mask, schedule=fh.make_schedule(**w["schedule"]), F=w["F"],
+                           dtype=fh.BF16 if args.dtype == "bf16" else fh.FP32,
                            mlp_hidden_layers=w["hidden"], mlp_width=w["width"], seed=1 + rank,
                            init_range=w["init_range"])
     mask_for_bf16 = mask if not args.no_serve else None
@@ -356,14 +359,15 @@ def main():
 
     n_params = info["n_table_params"] + info["n_mlp_params"]
     peaks, peak_kind = _peaks()
-    adam_bytes = 32.0 * n_params  # read p, g, m, v; write p, m, v and the cleared g
+    # read p, g, m, v; write p, m, v and the cleared g (+ the bf16 shadow of p in the precision form)
+    adam_bytes = (34.0 if args.dtype == "bf16" else 32.0) * n_params
     achieved = adam_bytes / (adam_ms / 1e3) / 1e9
     value = world * B * K / elapsed
 
     out = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": elapsed / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
+        "dtype": args.dtype, "data": "synthetic",
         "config": {"workload": w["name"], "global_batch": B * world, "levels": len(info["res"]), "F": info["F"],
                    "mlp": info["mlp_dims"], "table_params": info["n_table_params"],
                    "parallelism": "replicas" if world > 1 else "single",
@@ -372,7 +376,7 @@ def main():
         "gpu_launches": K * (4 + 2 * (w["hidden"] + 1)),
         "roofline": {"kernel": "k_adam", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                     "traffic": ADAM_DRAM_BYTES_PER_PARAM * n_params,
+                     "traffic": ADAM_DRAM_BYTES_PER_PARAM * n_params if args.dtype == "f32" else None,
                      "traffic_note": "ncu dram__bytes_read+write of k_adam on advect-128^3x32, scaled by parameters",
                      "peak_source": peak_kind, "bytes_per_launch": adam_bytes},
         "clocks": clk,

@@ -31,3 +31,26 @@ def forward_bf16(levels, level_bases, table, params, dims, coords):
         x = np.maximum(bf16_round(x) @ bf16_round(W).T + b, 0.0)
     Wo, bo = layers[-1]
     return (x @ Wo.T + bo)[:, 0]
+
+
+def grads_bf16(levels, level_bases, table, params, dims, coords, targets):
+    """Loss and MLP gradient of one training step in the precision form: the forward of forward_bf16
+    (activations kept as computed), the MSE, and the backward in float64 with the float32 master
+    weights (the GPU's backward reads those, and forms the weight gradients from the stored
+    activations and deltas).  Also returns the sum of |terms| of each gradient entry."""
+    enc = encode.encode(levels, level_bases, coords, bf16_round(np.asarray(table, np.float32)))
+    layers = mlp.unpack(params, dims)
+    acts, pre = [enc], []
+    x = enc
+    for W, b in layers[:-1]:
+        z = bf16_round(x) @ bf16_round(W).T + b
+        pre.append(z)
+        x = np.maximum(z, 0.0)
+        acts.append(x)
+    Wo, bo = layers[-1]
+    y = (x @ Wo.T + bo)[:, 0]
+    L, gy = mlp.mse(y, targets)
+    g, _ = mlp.backward(params, dims, acts, pre + [None], gy)
+    gabs, _ = mlp.backward(np.abs(params), dims, [np.abs(a) for a in acts],
+                           [np.where(z > 0, 1.0, -1.0) for z in pre] + [None], np.abs(gy))
+    return L, g, gabs

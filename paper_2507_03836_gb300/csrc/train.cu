@@ -326,6 +326,8 @@ __global__ void k_loss2(const double* __restrict__ partial, int nb, int64_t n, d
 
 cudaError_t run_tc_any(fhash_model* m, bool train, const FusedArgs& a);
 int tc_grid(int64_t n);
+bool launch_dw_tc(fhash_model* m, const float* acts, const float* dl, int64_t n, float* wpart, size_t wpart_bytes,
+                  cudaStream_t st, cudaError_t* err);
 
 template <int F>
 static cudaError_t scatter_launch(fhash_model* m, const float* coords, int64_t n, const float* denc, cudaStream_t st) {
@@ -373,7 +375,8 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
         const int fi = j == 0 ? sh.in : W, fo = j == sh.nh ? 1 : W;
         ne_max = std::max(ne_max, fo * fi + fo);
     }
-    FH_TRY(grow(m, m->s_partial, (size_t)nchunk * ne_max * 4 + (size_t)nb * 8 + 64));
+    const size_t tc_part = m->shadow ? ((size_t)num_sms() * (sh.nh + 1) * 4096 + 64 * 64) * 4 : 0;
+    FH_TRY(grow(m, m->s_partial, std::max((size_t)nchunk * ne_max * 4, tc_part) + (size_t)nb * 8 + 64));
     float* acts = (float*)m->s_acts.p;
     float* gy = (float*)m->s_gacts.p;
     float* dl = gy + n;
@@ -416,6 +419,15 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
         case 2: FH_CUDA(scatter_launch<2>(m, coords, n, denc, st)); break;
         case 4: FH_CUDA(scatter_launch<4>(m, coords, n, denc, st)); break;
         case 8: FH_CUDA(scatter_launch<8>(m, coords, n, denc, st)); break;
+    }
+    // weight gradients: tensor cores (TMA + tcgen05 kind::tf32) for the bf16 form, float32 SIMT tiles
+    // otherwise (the float32 form keeps full float32 products)
+    if (m->shadow) {
+        cudaError_t e = cudaSuccess;
+        if (launch_dw_tc(m, acts, dl, n, wpart, m->s_partial.bytes - ((size_t)nb * 8 + 63) / 64 * 64, st, &e)) {
+            FH_CUDA(e);
+            return FHASH_OK;
+        }
     }
     float* gm = m->grad + m->n_table;
     for (int j = 0; j <= sh.nh; ++j) {

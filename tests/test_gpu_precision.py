@@ -134,3 +134,26 @@ def test_bf16_render_pace_invariance_and_close_to_fp32(mask):
         imgs[name] = outs[0][0]
     mse = np.mean((imgs["fp32"] - imgs["bf16"]) ** 2)
     assert mse == 0 or 10 * np.log10(1.0 / mse) >= 35
+
+
+@pytest.mark.parametrize("n", [4096, 3001])
+def test_bf16_gradients_parity(mask, n):
+    # n a multiple of 4: weight gradients on the tensor cores (TMA + tcgen05 kind::tf32, inputs
+    # rounded to tf32: 2^-11 relative per product); otherwise the float32 tiles.  Bound: 3e-3 x the
+    # sum of |terms| of each entry.
+    f, m = mask
+    model = build(W1, mask=m, dtype=fh().BF16, seed=23)
+    info = fh().fhash_get_info(model)
+    table = synth.uniform(61, 50, info["n_table_params"], -0.6, 0.6)
+    p = synth.init_mlp(61, info["mlp_dims"])
+    set_params(model, table, p)
+    c = synth.coords(71, n)
+    tgt = synth.sample(f, info["fbb_lo"], info["fbb_size"], c)
+    loss = np.zeros(1, np.float64)
+    fh().fhash_compute_grads(model, to_dev(c), to_dev(tgt), loss)
+    L, g_ref, g_abs = precision.grads_bf16(info["res"], info["base"], table.reshape(-1, info["F"]),
+                                           p.astype(np.float64), info["mlp_dims"], c, tgt.astype(np.float64))
+    assert abs(loss[0] - L) <= 2e-3 * L
+    g = read(model, fh().STATE_GRAD, info["n_table_params"], info["n_mlp_params"]).astype(np.float64)
+    assert (np.abs(g - g_ref) <= 3e-3 * g_abs + 1e-9).all(), np.max(np.abs(g - g_ref) / (g_abs + 1e-9))
+    fh().fhash_check(model)
