@@ -91,9 +91,72 @@ __device__ __forceinline__ void encode64_bf16(const Levels& lv, const __nv_bfloa
     }
 }
 
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b);
+
+// Encodes one sample straight into its bf16 row t of the A tile (column l*F + f for level l, zeros
+// beyond L*F), without holding the whole encoding in registers; in training also stores the float32
+// encoding to the activation columns.
+// Shared-memory stores as explicit st.shared without a memory clobber: the compiler knows they cannot
+// alias the global gathers and keeps issuing the next level's loads ahead of them.
+__device__ __forceinline__ void sts32(uint32_t a, uint32_t v) { asm volatile("st.shared.b32 [%0], %1;" ::"r"(a), "r"(v)); }
+__device__ __forceinline__ void sts16(uint32_t a, unsigned short v) { asm volatile("st.shared.b16 [%0], %1;" ::"r"(a), "h"(v)); }
+__device__ __forceinline__ void sts64(uint32_t a, uint32_t x, uint32_t y) {
+    asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a), "r"(x), "r"(y));
+}
+__device__ __forceinline__ void sts128(uint32_t a, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w));
+}
+
+// Encodes one sample straight into its bf16 row t of the A tile (column l*F + f for level l, zeros
+// beyond L*F), without holding the whole encoding in registers; in training also stores the float32
+// encoding to the activation columns.
+template <int F, bool TRAIN>
+__device__ __forceinline__ void encode_row_bf16(const Levels& lv, const __nv_bfloat16* __restrict__ T, float4 u,
+                                                uint8_t* tile, int t, float* acts, int64_t n) {
+    const uint32_t rowa = tc::smem_addr(tile) + (t >> 3) * 1024 + (t & 7) * 128;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) sts128(rowa + ((c ^ (t & 7)) << 4), 0u, 0u, 0u, 0u);
+#pragma unroll
+    for (int l = 0; l < 64 / F; ++l) {
+        if (l < lv.L) {
+            Corners k = corners(lv.lv[l], u);
+            float o[F];
+            interp_level_bf16<F>(T, k, o);
+            if (TRAIN && acts) {
+#pragma unroll
+                for (int f = 0; f < F; ++f) acts[(int64_t)(l * F + f) * n] = o[f];
+            }
+            const int byte = l * F * 2;  // column l*F
+            const uint32_t dst = rowa + (((byte >> 4) ^ (t & 7)) << 4) + (byte & 15);
+            if constexpr (F == 1) {
+                __nv_bfloat16 h = __float2bfloat16_rn(o[0]);
+                sts16(dst, *reinterpret_cast<unsigned short*>(&h));
+            } else if constexpr (F == 2) {
+                sts32(dst, pack_bf16x2(o[0], o[1]));
+            } else if constexpr (F == 4) {
+                sts64(dst, pack_bf16x2(o[0], o[1]), pack_bf16x2(o[2], o[3]));
+            } else {
+                sts128(dst, pack_bf16x2(o[0], o[1]), pack_bf16x2(o[2], o[3]), pack_bf16x2(o[4], o[5]),
+                       pack_bf16x2(o[6], o[7]));
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// Columns 32h .. 32h+31 of row r of a 128 x 64 bf16 A tile (128-byte swizzle) from 32 floats.
+__device__ __forceinline__ void write_half_row(uint8_t* tile, int r, int h, const float (&x)[32]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int c = 4 * h + q;
+        uint4 w = make_uint4(pack_bf16x2(x[8 * q + 0], x[8 * q + 1]), pack_bf16x2(x[8 * q + 2], x[8 * q + 3]),
+                             pack_bf16x2(x[8 * q + 4], x[8 * q + 5]), pack_bf16x2(x[8 * q + 6], x[8 * q + 7]));
+        *reinterpret_cast<uint4*>(tile + tc::sw128_off(r, c)) = w;
+    }
 }
 
 // Row r of a 128 x 64 bf16 A tile (128-byte swizzle) from 64 floats.
@@ -185,20 +248,14 @@ __global__ void __launch_bounds__(128) k_forward_tc(const __grid_constant__ Leve
     for (int64_t tile = blockIdx.x; tile * 128 < n && !bad; tile += gridDim.x) {
         const int64_t i = tile * 128 + t;
         const bool valid = i < n;
-        float x[64];
         {
             float4 u = valid ? load_coord(coords, i) : make_float4(0.f, 0.f, 0.f, 0.f);
-            encode64_bf16<F>(lv, Tb, u, x);
+            encode_row_bf16<F, TRAIN>(lv, Tb, u, At, t, valid ? acts + i : nullptr, n);
         }
-        if (TRAIN && valid) {
-#pragma unroll
-            for (int c = 0; c < 64; ++c)
-                if (c < sh.in) acts[(int64_t)c * n + i] = x[c];
-        }
-        write_row(At, t, x);
         tc::fence_async_smem();
         tc::fence_before_sync();
         __syncthreads();
+        float y = bout[0];
         for (int j = 0; j < nh; ++j) {
             if (t == 0) {
                 tc::fence_after_sync();
@@ -212,32 +269,32 @@ __global__ void __launch_bounds__(128) k_forward_tc(const __grid_constant__ Leve
             phase ^= 1;
             if (__syncthreads_or(!ok)) { bad = true; break; }
             tc::fence_after_sync();
-            float v[32];
-            tc::tmem_ld32(lane_base + 0, v);
-            tc::tmem_ld_wait();
+            const bool last = j + 1 == nh;
 #pragma unroll
-            for (int q = 0; q < 32; ++q) x[q] = fmaxf(v[q] + bias[j * 64 + q], 0.0f);
-            tc::tmem_ld32(lane_base + 32, v);
-            tc::tmem_ld_wait();
+            for (int h = 0; h < 2; ++h) {  // 32 accumulator columns at a time
+                float v[32];
+                tc::tmem_ld32(lane_base + 32 * h, v);
+                tc::tmem_ld_wait();
 #pragma unroll
-            for (int q = 0; q < 32; ++q) x[32 + q] = fmaxf(v[q] + bias[j * 64 + 32 + q], 0.0f);
-            if (TRAIN && valid) {
-                float* a = acts + (int64_t)(sh.in + j * Wd) * n + i;
+                for (int q = 0; q < 32; ++q) v[q] = fmaxf(v[q] + bias[j * 64 + 32 * h + q], 0.0f);
+                if (TRAIN && valid) {
+                    float* a = acts + (int64_t)(sh.in + j * Wd) * n + i;
 #pragma unroll
-                for (int o = 0; o < 64; ++o)
-                    if (o < Wd) a[(int64_t)o * n] = x[o];
+                    for (int q = 0; q < 32; ++q)
+                        if (32 * h + q < Wd) a[(int64_t)(32 * h + q) * n] = v[q];
+                }
+                if (!last) {
+                    write_half_row(At, t, h, v);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) y = fmaf(wout[32 * h + q], v[q], y);  // scalar output layer
+                }
             }
-            if (j + 1 < nh) {
-                write_row(At, t, x);
-                tc::fence_async_smem();
-            }
+            if (!last) tc::fence_async_smem();
             tc::fence_before_sync();
             __syncthreads();
         }
         if (bad) break;
-        float y = bout[0];
-#pragma unroll
-        for (int o = 0; o < 64; ++o) y = fmaf(wout[o], x[o], y);
         if (valid) {
             if (TRAIN) {
                 const float r = y - __ldg(target + i);
@@ -279,9 +336,18 @@ static cudaError_t run_tc(fhash_model* m, bool train, const FusedArgs& a) {
     return cudaGetLastError();
 }
 
-// Grid for the tensor-core kernels: persistent, at most 4 CTAs per SM (4 x 64 TMEM columns).
-int tc_grid(int64_t n) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, (int64_t)num_sms() * 4));
+// Grid for the tensor-core kernels: persistent, as many CTAs per SM as shared memory lets reside.
+// Every configuration takes at least 26 KB of shared memory per CTA, so at most 8 CTAs share an SM:
+// 8 x 64 = 512 TMEM columns, never more than the SM has (allocation can never wait on a CTA that waits).
+int tc_grid(int64_t n, int nh) {
+    static int smem_sm = 0;
+    if (!smem_sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    }
+    const int per_sm = std::max(1, std::min(8, smem_sm / (TcSmem::bytes(nh) + 1024)));
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, (int64_t)num_sms() * per_sm));
 }
 
 cudaError_t run_tc_any(fhash_model* m, bool train, const FusedArgs& a) {

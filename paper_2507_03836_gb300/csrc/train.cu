@@ -325,7 +325,7 @@ __global__ void k_loss2(const double* __restrict__ partial, int nb, int64_t n, d
 }
 
 cudaError_t run_tc_any(fhash_model* m, bool train, const FusedArgs& a);
-int tc_grid(int64_t n);
+int tc_grid(int64_t n, int nh);
 bool launch_dw_tc(fhash_model* m, const float* acts, const float* dl, int64_t n, float* wpart, size_t wpart_bytes,
                   cudaStream_t st, cudaError_t* err);
 
@@ -366,7 +366,7 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
     const int64_t D = (int64_t)sh.nh * W + 1;       // delta rows
     FH_TRY(grow(m, m->s_acts, (size_t)(A * n * 4)));
     FH_TRY(grow(m, m->s_gacts, (size_t)((D + 1 + sh.in) * n * 4)));
-    const int nb = m->shadow ? tc_grid(n)
+    const int nb = m->shadow ? tc_grid(n, m->mlp.nh)
                              : (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, (int64_t)num_sms() * 8));
     const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, (int64_t)num_sms() * 2));
     const int64_t chunk = ((n + nchunk - 1) / nchunk + 31) / 32 * 32;
