@@ -243,6 +243,194 @@ def serving_leg(args, w, model, info, field, mask, rank):
     return {"render": render, "precision": prec}
 
 
+# ------------------------------------------------------------------ suites beyond the default line
+def _build(w, dtype, seed, mask):
+    import paper_2507_03836_gb300 as fh
+    nx, ny, nz, nt = w["dims"]
+    m = fh.fhash_build(nx, ny, nz, nt, mask=mask, schedule=fh.make_schedule(**w["schedule"]), F=w["F"], dtype=dtype,
+                       mlp_hidden_layers=w["hidden"], mlp_width=w["width"], seed=seed, init_range=w["init_range"])
+    return m, fh.fhash_get_info(m)
+
+
+def _batches(w, info, field, k, seed):
+    import torch
+    import synth
+    out = []
+    for i in range(k):
+        c = synth.coords(seed + i, w["batch"])
+        out.append((torch.from_numpy(c).cuda(), torch.from_numpy(synth.sample(field, info["fbb_lo"], info["fbb_size"], c)).cuda()))
+    return out
+
+
+def _train(model, batches, hp, warmup=3):
+    """Trains on the batches; returns ms per step over all but the first `warmup` (CUDA events)."""
+    import torch
+    import paper_2507_03836_gb300 as fh
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for i, (c, t) in enumerate(batches):
+        if i == warmup:
+            torch.cuda.synchronize()
+            e0.record(st)
+        fh.fhash_train_step(model, c, t, hp)
+    e1.record(st)
+    torch.cuda.synchronize()
+    fh.fhash_check(model)
+    return e0.elapsed_time(e1) / max(1, len(batches) - warmup)
+
+
+def _psnr(model, info, field, n=1 << 20, seed=777):
+    import torch
+    import synth
+    import paper_2507_03836_gb300 as fh
+    held = synth.coords(seed, n)
+    truth = synth.sample(field, info["fbb_lo"], info["fbb_size"], held).astype(np.float64)
+    o = torch.empty(n, dtype=torch.float32, device="cuda")
+    fh.fhash_forward(model, torch.from_numpy(held).cuda(), o)
+    pred = o.cpu().numpy().astype(np.float64)
+    rng = truth.max() - truth.min()
+    return float(10 * np.log10(rng ** 2 / np.mean((pred - truth) ** 2))), float(np.abs(pred - truth).max())
+
+
+def suite_precision(args):
+    """Precision form against float32 on the Combustion-shaped front: both trained from the same start on the
+    same batches; samples/s of each, and PSNR / max abs error on 1M held-out points against the field."""
+    import paper_2507_03836_gb300 as fh
+    from synth import workloads
+    w = workloads.FRONT
+    t0 = time.time()
+    field, mask = workloads.make_field_and_mask(w)
+    res = {"suite": "precision", "workload": w["name"], "steps": args.steps, "batch": w["batch"]}
+    for name, dt in (("fp32", fh.FP32), ("bf16", fh.BF16)):
+        model, info = _build(w, dt, 5, mask)
+        batches = _batches(w, info, field, args.steps + 3, 50_000)
+        ms = _train(model, batches, w["adam"])
+        p, e = _psnr(model, info, field)
+        res[name] = {"ms_per_step": ms, "samples_s": w["batch"] / ms * 1e3, "psnr_db": p, "max_abs_err": e,
+                     "params": info["n_table_params"] + info["n_mlp_params"]}
+        del model, batches
+    res["psnr_drop_db"] = res["fp32"]["psnr_db"] - res["bf16"]["psnr_db"]
+    res["setup_s"] = time.time() - t0
+    print(json.dumps(res))
+
+
+def _serve(models, kinds, n_req, rate, budget, tf, seed=1234, decode_every=0):
+    """Poisson stream through one server; kinds[i] = model index of request i; every `decode_every`-th
+    request (0: none) is a time-slice decode (upsample 1 or 2), the rest renders of 256^2/512^2/1024^2."""
+    import torch
+    import synth
+    import paper_2507_03836_gb300 as fh
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    sizes = rng.choice([256, 512, 1024], n_req)
+    times = rng.random(n_req)
+    ups = rng.choice([1, 2], n_req)
+    srv = fh.fhash_server_create(models, budget_bytes=budget, max_live=64, tick_samples=1 << 22)
+    reqs, outs = [], []
+    for i in range(n_req):
+        mi = kinds[i]
+        if decode_every and i % decode_every == decode_every - 1:
+            d = fh.fhash_decode_dims(models[mi], int(ups[i]))
+            out = torch.empty((d[2], d[1], d[0]), dtype=torch.float32, device="cuda")
+            reqs.append(fh.make_request(fh.REQ_DECODE, mi, float(times[i]), upsample=int(ups[i]), out=out))
+        else:
+            s_ = int(sizes[i])
+            out = torch.empty((s_, s_, 4), dtype=torch.float32, device="cuda")
+            cam = synth.camera(synth.sphere_eye(7, i), s_, s_)
+            reqs.append(fh.make_request(fh.REQ_RENDER, mi, float(times[i]), cam, s_, s_, 64, tf, out=out))
+        outs.append(out)
+    # warm-up (kernels, graphs)
+    wid = fh.fhash_server_submit(srv, reqs[0])
+    while fh.fhash_server_poll(srv, wid)[0] != fh.REQ_DONE:
+        fh.fhash_server_tick(srv)
+    st0 = fh.fhash_server_get_stats(srv)
+    torch.cuda.synchronize()
+    lat = np.zeros(n_req)
+    done = np.zeros(n_req, bool)
+    ids = {}
+    nxt = 0
+    t0 = time.perf_counter()
+    while not done.all():
+        now = time.perf_counter() - t0
+        while nxt < n_req and arrivals[nxt] <= now:
+            ids[nxt] = fh.fhash_server_submit(srv, reqs[nxt])
+            nxt += 1
+        if not ids or all(done[k] for k in ids):
+            time.sleep(max(0.0, min(arrivals[nxt] - (time.perf_counter() - t0), 0.01)) if nxt < n_req else 0)
+            continue
+        fh.fhash_server_tick(srv)
+        tnow = time.perf_counter() - t0
+        for k, rid in ids.items():
+            if not done[k] and fh.fhash_server_poll(srv, rid)[0] == fh.REQ_DONE:
+                done[k] = True
+                lat[k] = (tnow - arrivals[k]) * 1e3
+    elapsed = time.perf_counter() - t0
+    st = fh.fhash_server_get_stats(srv)
+    samples = st["samples"] - st0["samples"]
+    is_dec = np.array([bool(decode_every and i % decode_every == decode_every - 1) for i in range(n_req)])
+    out = {"p50_ms": float(np.percentile(lat, 50)), "p95_ms": float(np.percentile(lat, 95)),
+           "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+           "throughput_samples_s": samples / elapsed, "requests_s": n_req / elapsed,
+           "ticks": st["ticks"] - st0["ticks"], "graph_launches": st["model_launches"] - st0["model_launches"]}
+    if is_dec.any():
+        out["render_p50_ms"] = float(np.percentile(lat[~is_dec], 50))
+        out["render_p99_ms"] = float(np.percentile(lat[~is_dec], 99))
+        out["decode_p50_ms"] = float(np.percentile(lat[is_dec], 50))
+        out["decode_p99_ms"] = float(np.percentile(lat[is_dec], 99))
+    del srv
+    return out
+
+
+def suite_serve(args):
+    """Render serving on the Supernova-shaped shell model (trained as the default workload): Poisson stream,
+    FP32 form and the precision form (same weights), p50/p95/p99 and samples/s; PSNR of both forms."""
+    import torch
+    import synth
+    import paper_2507_03836_gb300 as fh
+    from synth import workloads
+    w = workloads.SHELL
+    t0 = time.time()
+    field, mask = workloads.make_field_and_mask(w)
+    m32, info = _build(w, fh.FP32, 6, mask)
+    ms = _train(m32, _batches(w, info, field, args.steps + 3, 60_000), w["adam"])
+    m16, _ = _build(w, fh.BF16, 6, mask)
+    _copy_params(m32, m16, info["n_table_params"] + info["n_mlp_params"])
+    tf = torch.from_numpy(synth.transfer_function(0.5)).cuda()
+    res = {"suite": "serve", "workload": w["name"], "train_steps": args.steps + 3, "train_ms_per_step": ms,
+           "requests": args.serve_requests, "rate_req_s": args.serve_rate}
+    for name, mi in (("fp32", 0), ("bf16", 1)):
+        res[name] = _serve([m32, m16], [mi] * args.serve_requests, args.serve_requests, args.serve_rate, 96 << 30, tf)
+        res[name]["psnr_db"], res[name]["max_abs_err"] = _psnr(m32 if mi == 0 else m16, info, field)
+    res["setup_s"] = time.time() - t0
+    print(json.dumps(res))
+
+
+def suite_mixed(args):
+    """Mixed stream over three resident models (the advect-256^3x64 model in FP32, the front model and a second
+    256^3x64 model in the precision form) under a 64 GB budget; decode:render 1:3."""
+    import torch
+    import synth
+    import paper_2507_03836_gb300 as fh
+    from synth import workloads
+    t0 = time.time()
+    models, infos = [], []
+    for w, dt, seed in ((workloads.LARGE, fh.FP32, 7), (workloads.FRONT, fh.BF16, 8),
+                        (dict(workloads.LARGE, seed=4, name="advect2-256^3x64"), fh.BF16, 9)):
+        field, mask = workloads.make_field_and_mask(w)
+        m, info = _build(w, dt, seed, mask)
+        _train(m, _batches(w, info, field, args.steps + 3, 70_000 + seed * 1000), w["adam"])
+        models.append(m)
+        infos.append((w["name"], info))
+        del field, mask
+    tf = torch.from_numpy(synth.transfer_function(0.5)).cuda()
+    kinds = list(np.random.default_rng(5).integers(0, 3, args.serve_requests))
+    res = {"suite": "mixed", "models": [n for n, _ in infos], "budget_bytes": 64 << 30,
+           "requests": args.serve_requests, "rate_req_s": args.serve_rate, "decode_to_render": "1:3"}
+    res.update(_serve(models, kinds, args.serve_requests, args.serve_rate, 64 << 30, tf, decode_every=4))
+    res["setup_s"] = time.time() - t0
+    print(json.dumps(res))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -256,9 +444,15 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving and precision legs")
     ap.add_argument("--serve-requests", type=int, default=60)
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--suite", default="train", choices=["train", "precision", "serve", "mixed"],
+                    help="train: the default line; precision / serve / mixed: the other workloads")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.suite != "train":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        return {"precision": suite_precision, "serve": suite_serve, "mixed": suite_mixed}[args.suite](args)
 
     import torch
     import synth

@@ -202,6 +202,17 @@ fhash_status fhash_write_state(fhash_model* model, int32_t which, uint64_t offse
  * out: host or device [Sz][Sy][Sx]. */
 fhash_status fhash_read_occupancy(fhash_model* model, int64_t t, uint8_t* out, fhash_stream stream);
 
+/*
+ * Checkpoints (the paper pretrains the INR before visualisation, Section 3.3).  fhash_save writes the
+ * model description, level schedule, Feature Bounding Box, Adam step count, every state vector
+ * (parameters, gradients, both Adam moments) and the occupancy grid to `path`; fhash_load rebuilds an
+ * identical model on the current device (bf16 shadows recomputed).  Both are synchronous; the file is
+ * specific to this library version and byte order.  Errors: FHASH_EIO for unreadable, truncated or
+ * foreign files; FHASH_ENOMEM.
+ */
+fhash_status fhash_save(const fhash_model* model, const char* path);
+fhash_status fhash_load(const char* path, fhash_stream stream, fhash_model** out);
+
 /* Synchronise `stream` and report FHASH_EDEVICE if a kernel of this model raised the device
  * error word since the last check (the word is then cleared). */
 fhash_status fhash_check(fhash_model* model, fhash_stream stream);

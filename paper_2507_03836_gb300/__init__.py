@@ -95,6 +95,8 @@ _SIGS = {
     "fhash_write_state": [_vp, _i32, _u64, _u64, _vp, _vp],
     "fhash_read_occupancy": [_vp, _i64, _vp, _vp],
     "fhash_check": [_vp, _vp],
+    "fhash_save": [_vp, ctypes.c_char_p],
+    "fhash_load": [ctypes.c_char_p, _vp, ctypes.POINTER(_vp)],
     "fhash_compute_grads_noalloc": [_vp, _vp, _vp, _i64, _vp, _vp],
     "fhash_render": [_vp, ctypes.POINTER(fhash_camera), ctypes.c_float, _vp, _i32, _i32, _i32, _vp, _vp,
                      ctypes.POINTER(fhash_render_stats), _vp],
@@ -293,6 +295,16 @@ def fhash_decode_dims(model, upsample):
 
 def fhash_decode(model, t_norm, upsample, out, stream=None):
     _ok(_lib.fhash_decode(model.handle, float(t_norm), int(upsample), _ptr(out), _stream(stream)))
+
+
+def fhash_save(model, path):
+    _ok(_lib.fhash_save(model.handle, str(path).encode()))
+
+
+def fhash_load(path, stream=None):
+    h = _vp()
+    _ok(_lib.fhash_load(str(path).encode(), _stream(stream), ctypes.byref(h)))
+    return Model(h.value)
 
 
 def fhash_check(model, stream=None):

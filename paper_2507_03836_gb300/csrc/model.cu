@@ -4,6 +4,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -494,6 +495,125 @@ fhash_status fhash_check(fhash_model* m, fhash_stream stream) {
         FH_CUDA(cudaMemset(m->err_word, 0, sizeof(int)));
         return set_error(FHASH_EDEVICE, "device error word %d", w);
     }
+    return FHASH_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ checkpoints
+namespace fh {
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version, header_bytes;
+    fhash_build_desc desc;
+    Levels lv;
+    MlpShape mlp;
+    uint64_t total_rows, n_table, n_params;
+    int64_t fbb_lo[3], fbb_size[3], nt, step, nbx, nby, nbz;
+};
+static const char kMagic[8] = {'F', 'H', 'A', 'S', 'H', 'C', 'K', '1'};
+
+// Streams `bytes` between a device buffer and a file through a pinned host buffer.
+static fhash_status stream_file(FILE* f, void* dev, uint64_t bytes, bool write, void* pin, size_t pin_bytes) {
+    char* d = (char*)dev;
+    for (uint64_t o = 0; o < bytes; o += pin_bytes) {
+        const size_t k = (size_t)std::min<uint64_t>(pin_bytes, bytes - o);
+        if (write) {
+            FH_CUDA(cudaMemcpy(pin, d + o, k, cudaMemcpyDeviceToHost));
+            if (fwrite(pin, 1, k, f) != k) return set_error(FHASH_EIO, "checkpoint write failed");
+        } else {
+            if (fread(pin, 1, k, f) != k) return set_error(FHASH_EIO, "checkpoint truncated");
+            FH_CUDA(cudaMemcpy(d + o, pin, k, cudaMemcpyHostToDevice));
+        }
+    }
+    return FHASH_OK;
+}
+
+}  // namespace fh
+
+extern "C" {
+
+fhash_status fhash_save(const fhash_model* mc, const char* path) {
+    fhash_model* m = const_cast<fhash_model*>(mc);
+    if (!m || !path) return set_error(FHASH_EINVAL, "fhash_save: null argument");
+    FH_CUDA(cudaDeviceSynchronize());
+    FILE* f = fopen(path, "wb");
+    if (!f) return set_error(FHASH_EIO, "fhash_save: cannot open %s", path);
+    CkptHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, kMagic, 8);
+    h.version = 1;
+    h.header_bytes = sizeof h;
+    h.desc = m->desc;
+    h.desc.mask = nullptr;
+    h.lv = m->lv;
+    h.mlp = m->mlp;
+    h.total_rows = m->total_rows; h.n_table = m->n_table; h.n_params = m->n_params;
+    for (int a = 0; a < 3; ++a) { h.fbb_lo[a] = m->fbb_lo[a]; h.fbb_size[a] = m->fbb_size[a]; }
+    h.nt = m->nt; h.step = m->step; h.nbx = m->nbx; h.nby = m->nby; h.nbz = m->nbz;
+    fhash_status rc = FHASH_OK;
+    if (fwrite(&h, sizeof h, 1, f) != 1) rc = set_error(FHASH_EIO, "fhash_save: write failed");
+    const size_t pin_bytes = 64u << 20;
+    void* pin = nullptr;
+    if (rc == FHASH_OK && cudaMallocHost(&pin, pin_bytes) != cudaSuccess) rc = set_error(FHASH_ENOMEM, "fhash_save: pinned buffer");
+    const uint64_t nb = (uint64_t)(m->nbx * m->nby * m->nbz * m->nt);
+    void* arrays[] = {m->param, m->grad, m->adam_m, m->adam_v, m->occ, m->occ_any};
+    const uint64_t sizes[] = {m->n_params * 4, m->n_params * 4, m->n_params * 4, m->n_params * 4, nb * 64, nb};
+    for (int i = 0; i < 6 && rc == FHASH_OK; ++i) rc = stream_file(f, arrays[i], sizes[i], true, pin, pin_bytes);
+    if (pin) cudaFreeHost(pin);
+    if (fclose(f) != 0 && rc == FHASH_OK) rc = set_error(FHASH_EIO, "fhash_save: close failed");
+    return rc;
+}
+
+fhash_status fhash_load(const char* path, fhash_stream stream, fhash_model** out) {
+    if (!path || !out) return set_error(FHASH_EINVAL, "fhash_load: null argument");
+    *out = nullptr;
+    FILE* f = fopen(path, "rb");
+    if (!f) return set_error(FHASH_EIO, "fhash_load: cannot open %s", path);
+    CkptHeader h;
+    if (fread(&h, sizeof h, 1, f) != 1 || memcmp(h.magic, kMagic, 8) != 0 || h.version != 1 ||
+        h.header_bytes != sizeof h || h.lv.L < 1 || h.lv.L > FHASH_MAX_LEVELS || h.n_params < h.n_table) {
+        fclose(f);
+        return set_error(FHASH_EIO, "fhash_load: %s is not an F-Hash checkpoint of this version", path);
+    }
+    fhash_model* m = new fhash_model();
+    struct Guard {
+        fhash_model*& m;
+        FILE* f;
+        ~Guard() { if (m) destroy_model(m); if (f) fclose(f); }
+    } guard{m, f};
+    cudaGetDevice(&m->device);
+    m->desc = h.desc;
+    m->lv = h.lv;
+    m->mlp = h.mlp;
+    m->total_rows = h.total_rows; m->n_table = h.n_table; m->n_params = h.n_params;
+    for (int a = 0; a < 3; ++a) { m->fbb_lo[a] = h.fbb_lo[a]; m->fbb_size[a] = h.fbb_size[a]; }
+    m->nt = h.nt; m->step = h.step; m->nbx = h.nbx; m->nby = h.nby; m->nbz = h.nbz;
+    const uint64_t nb = (uint64_t)(m->nbx * m->nby * m->nbz * m->nt);
+    const size_t bytes = (size_t)m->n_params * 4;
+    FH_TRY(dev_alloc(m, (void**)&m->err_word, sizeof(int)));
+    FH_CUDA(cudaMemset(m->err_word, 0, sizeof(int)));
+    FH_TRY(dev_alloc(m, (void**)&m->param, bytes));
+    FH_TRY(dev_alloc(m, (void**)&m->grad, bytes));
+    FH_TRY(dev_alloc(m, (void**)&m->adam_m, bytes));
+    FH_TRY(dev_alloc(m, (void**)&m->adam_v, bytes));
+    if (m->desc.dtype == FHASH_BF16) FH_TRY(dev_alloc(m, (void**)&m->shadow, (size_t)m->n_params * 2));
+    FH_TRY(dev_alloc(m, (void**)&m->occ, (size_t)nb * 64));
+    FH_TRY(dev_alloc(m, (void**)&m->occ_any, (size_t)nb));
+    const size_t pin_bytes = 64u << 20;
+    void* pin = nullptr;
+    if (cudaMallocHost(&pin, pin_bytes) != cudaSuccess) return set_error(FHASH_ENOMEM, "fhash_load: pinned buffer");
+    void* arrays[] = {m->param, m->grad, m->adam_m, m->adam_v, m->occ, m->occ_any};
+    const uint64_t sizes[] = {bytes, bytes, bytes, bytes, nb * 64, nb};
+    fhash_status rc = FHASH_OK;
+    for (int i = 0; i < 6 && rc == FHASH_OK; ++i) rc = stream_file(f, arrays[i], sizes[i], false, pin, pin_bytes);
+    cudaFreeHost(pin);
+    if (rc != FHASH_OK) return rc;
+    FH_TRY(refresh_shadow(m, 0, m->n_params, (cudaStream_t)stream));
+    FH_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    *out = m;
+    m = nullptr;
     return FHASH_OK;
 }
 

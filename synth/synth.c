@@ -133,20 +133,27 @@ static void add_blobs(const blob* b, int nb, int64_t nx, int64_t ny, int64_t nz,
     }
 }
 
-static void add_noise(uint64_t seed, int octaves, double sp0, double st0, double amp0, int64_t nx, int64_t ny,
-                      int64_t nz, int64_t nt, int64_t t, float* vol) {
+static void add_noise(const noise_lattice* lat, int octaves, double amp0, int64_t nx, int64_t ny, int64_t nz,
+                      int64_t t, float* vol) {
     for (int o = 0; o < octaves; ++o) {
-        noise_lattice L;
-        double s = sp0 / (double)(1 << o), st = st0 / (double)(1 << o);
-        if (st < 1.0) st = 1.0;
-        lattice_init(&L, seed, 10 + (uint64_t)o, nx, ny, nz, nt, s, st);
-        float* sl = lattice_slice(&L, t);
+        const noise_lattice* L = &lat[o];
+        float* sl = lattice_slice(L, t);
         double a = amp0 * pow(0.5, o);
 #pragma omp parallel for schedule(static)
         for (int64_t z = 0; z < nz; ++z)
             for (int64_t y = 0; y < ny; ++y)
-                for (int64_t x = 0; x < nx; ++x) vol[(z * ny + y) * nx + x] += (float)(a * slice_eval(&L, sl, x, y, z));
-        free(sl); free(L.v);
+                for (int64_t x = 0; x < nx; ++x) vol[(z * ny + y) * nx + x] += (float)(a * slice_eval(L, sl, x, y, z));
+        free(sl);
+    }
+}
+
+/* Octave o: spacing sp0/2^o voxels and st0/2^o steps (at least 1), values from stream 10 + o. */
+static void make_lattices(uint64_t seed, int octaves, double sp0, double st0, int64_t nx, int64_t ny, int64_t nz,
+                          int64_t nt, noise_lattice* lat) {
+    for (int o = 0; o < octaves; ++o) {
+        double s = sp0 / (double)(1 << o), st = st0 / (double)(1 << o);
+        if (st < 1.0) st = 1.0;
+        lattice_init(&lat[o], seed, 10 + (uint64_t)o, nx, ny, nz, nt, s, st);
     }
 }
 
@@ -154,6 +161,9 @@ int synth_field(int kind, uint64_t seed, int64_t nx, int64_t ny, int64_t nz, int
                 float* out) {
     if (t0 < 0 || t1 > nt || t0 >= t1 || nx < 2 || ny < 2 || nz < 2) return 1;
     int64_t n3 = nx * ny * nz;
+    noise_lattice lat[4];
+    const int octaves = kind == 2 ? 3 : (kind == 3 || kind == 4) ? 4 : 0;
+    make_lattices(seed, octaves, 32.0, 16.0, nx, ny, nz, nt, lat);
     double mx = (double)(nx > ny ? (nx > nz ? nx : nz) : (ny > nz ? ny : nz));
     for (int64_t t = t0; t < t1; ++t) {
         float* vol = out + (t - t0) * n3;
@@ -172,7 +182,7 @@ int synth_field(int kind, uint64_t seed, int64_t nx, int64_t ny, int64_t nz, int
             double lo[3] = {0.15 * nx, 0.15 * ny, 0.15 * nz}, hi[3] = {0.85 * nx, 0.85 * ny, 0.85 * nz};
             make_blobs(seed, 64, 0.03 * mx, lo, hi, b);
             add_blobs(b, 64, nx, ny, nz, t, vol);
-            add_noise(seed, 3, 32.0, 16.0, 0.3, nx, ny, nz, nt, t, vol);
+            add_noise(lat, 3, 0.3, nx, ny, nz, t, vol);
         } else if (kind == 3) {
             noise_lattice H;   /* 2D height noise over (y, z), reusing a 3D lattice slice at x = 0 */
             lattice_init(&H, seed, 5, 1, ny, nz, 1, 64.0, 1.0);
@@ -185,7 +195,7 @@ int synth_field(int kind, uint64_t seed, int64_t nx, int64_t ny, int64_t nz, int
                         vol[(z * ny + y) * nx + x] = (float)(0.5 * (1.0 + tanh((xf - x) / 4.0)));
                 }
             free(hs); free(H.v);
-            add_noise(seed, 4, 32.0, 16.0, 0.05, nx, ny, nz, nt, t, vol);
+            add_noise(lat, 4, 0.05, nx, ny, nz, t, vol);
         } else if (kind == 4) {
             double cx = 0.5 * (nx - 1), cy = 0.5 * (ny - 1), cz = 0.5 * (nz - 1), r0 = 20.0 + 2.0 * t;
 #pragma omp parallel for schedule(static)
@@ -196,11 +206,13 @@ int synth_field(int kind, uint64_t seed, int64_t nx, int64_t ny, int64_t nz, int
                         double q = (r - r0) / 3.0;
                         vol[(z * ny + y) * nx + x] = (float)exp(-q * q);
                     }
-            add_noise(seed, 4, 32.0, 16.0, 0.1, nx, ny, nz, nt, t, vol);
+            add_noise(lat, 4, 0.1, nx, ny, nz, t, vol);
         } else {
+            for (int o = 0; o < octaves; ++o) free(lat[o].v);
             return 2;
         }
     }
+    for (int o = 0; o < octaves; ++o) free(lat[o].v);
     return 0;
 }
 
