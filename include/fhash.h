@@ -93,7 +93,7 @@ typedef struct {
  *    by the 26-neighbourhood per time step (feature dilation, Section 3.1), takes the union of
  *    the per-frame boxes as the Feature Bounding Box and keeps the dilated mask as the bit
  *    occupancy grid used by the renderer.  An all-zero mask is FHASH_EINVAL.
- *  F: embedding size, 1..8.  dtype: FHASH_FP32, or FHASH_BF16 (tables and MLP read as bf16
+ *  F: embedding size, 1, 2, 4 or 8 (L*F at most 64).  dtype: FHASH_FP32, or FHASH_BF16 (tables and MLP read as bf16
  *    shadows of float32 master weights; MLP on the tensor cores with float32 accumulation).
  *  mlp_hidden_layers (1..FHASH_MAX_HIDDEN) hidden layers of mlp_width (16, 32 or 64) with ReLU,
  *    then a linear scalar output; every layer has a bias.
@@ -213,6 +213,12 @@ fhash_status fhash_read_occupancy(fhash_model* model, int64_t t, uint8_t* out, f
 fhash_status fhash_save(const fhash_model* model, const char* path);
 fhash_status fhash_load(const char* path, fhash_stream stream, fhash_model** out);
 
+/* Diagnostic of the failure path: launches one CTA that waits, with the bounded wait every
+ * tensor-core kernel uses, on an mbarrier that nothing arrives on.  After limit_ns (at most 10 s) the
+ * wait gives up, the kernel records the timeout in the model's device error word and returns; the
+ * next fhash_check reports FHASH_EDEVICE.  Nothing traps or hangs.  Asynchronous. */
+fhash_status fhash_diag_wait_timeout(fhash_model* model, uint64_t limit_ns, fhash_stream stream);
+
 /* Synchronise `stream` and report FHASH_EDEVICE if a kernel of this model raised the device
  * error word since the last check (the word is then cleared). */
 fhash_status fhash_check(fhash_model* model, fhash_stream stream);
@@ -276,6 +282,8 @@ fhash_status fhash_decode(fhash_model* model, float t_norm, int32_t upsample, fl
  * cudaMalloc, cudaFree or other allocating call.
  *  - coords [n][4] and target [n] must be DEVICE memory (they are not staged); loss is host or
  *    device double* or NULL.
+ *  - It evaluates the float32 form (float32 master tables and MLP on the CUDA cores), also for
+ *    FHASH_BF16 models.
  *  - n must be in 1..FHASH_NOALLOC_MAX_SAMPLES; a model/n combination whose working set exceeds the
  *    array is rejected with FHASH_EINVAL before anything is launched.
  *  - The first call on a device, made with that device current, looks up the array's device address

@@ -96,6 +96,7 @@ _SIGS = {
     "fhash_read_occupancy": [_vp, _i64, _vp, _vp],
     "fhash_check": [_vp, _vp],
     "fhash_save": [_vp, ctypes.c_char_p],
+    "fhash_diag_wait_timeout": [_vp, _u64, _vp],
     "fhash_load": [ctypes.c_char_p, _vp, ctypes.POINTER(_vp)],
     "fhash_compute_grads_noalloc": [_vp, _vp, _vp, _i64, _vp, _vp],
     "fhash_render": [_vp, ctypes.POINTER(fhash_camera), ctypes.c_float, _vp, _i32, _i32, _i32, _vp, _vp,
@@ -305,6 +306,10 @@ def fhash_load(path, stream=None):
     h = _vp()
     _ok(_lib.fhash_load(str(path).encode(), _stream(stream), ctypes.byref(h)))
     return Model(h.value)
+
+
+def fhash_diag_wait_timeout(model, limit_ns, stream=None):
+    _ok(_lib.fhash_diag_wait_timeout(model.handle, int(limit_ns), _stream(stream)))
 
 
 def fhash_check(model, stream=None):

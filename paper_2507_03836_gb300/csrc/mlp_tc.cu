@@ -361,3 +361,25 @@ cudaError_t run_tc_any(fhash_model* m, bool train, const FusedArgs& a) {
 }
 
 }  // namespace fh
+
+namespace fh {
+// One CTA waits on an mbarrier that nothing arrives on, with the same bounded wait the tensor-core
+// kernels use; when the limit runs out it reports through the model's error word and returns.
+__global__ void k_diag_wait(uint64_t limit_ns, int* __restrict__ err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !tc::mbar_wait(&bar, 0, limit_ns)) raise_error(err, 0x7C07);
+}
+}  // namespace fh
+
+extern "C" fhash_status fhash_diag_wait_timeout(fhash_model* m, uint64_t limit_ns, fhash_stream stream) {
+    if (!m || limit_ns == 0 || limit_ns > 10000000000ull)
+        return fh::set_error(FHASH_EINVAL, "fhash_diag_wait_timeout: limit must be in (0, 10 s]");
+    fh::k_diag_wait<<<1, 32, 0, (cudaStream_t)stream>>>(limit_ns, m->err_word);
+    FH_CUDA(cudaGetLastError());
+    return FHASH_OK;
+}

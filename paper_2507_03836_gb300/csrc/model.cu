@@ -266,7 +266,7 @@ fhash_status fhash_build(const fhash_build_desc* d, fhash_stream stream, fhash_m
     cudaStream_t st = (cudaStream_t)stream;
     if (d->nx < 2 || d->ny < 2 || d->nz < 2 || d->nt < 1 || d->nx > (1 << 20) || d->ny > (1 << 20) || d->nz > (1 << 20))
         return set_error(FHASH_EINVAL, "volume dims must be >= 2 (space) and >= 1 (time)");
-    if (d->F < 1 || d->F > 8) return set_error(FHASH_EINVAL, "F must be in 1..8");
+    if (d->F != 1 && d->F != 2 && d->F != 4 && d->F != 8) return set_error(FHASH_EINVAL, "F must be 1, 2, 4 or 8");
     if (d->dtype != FHASH_FP32 && d->dtype != FHASH_BF16) return set_error(FHASH_EINVAL, "dtype");
     if (d->mlp_hidden_layers < 1 || d->mlp_hidden_layers > FHASH_MAX_HIDDEN)
         return set_error(FHASH_EINVAL, "mlp_hidden_layers must be in 1..%d", FHASH_MAX_HIDDEN);
