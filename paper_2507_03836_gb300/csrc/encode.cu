@@ -139,8 +139,7 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ P, float* __re
 }
 
 cudaError_t run_fused_any(int F, int which, const FusedArgs& a);
-cudaError_t run_tc_any(fhash_model* m, bool train, const FusedArgs& a);
-int tc_grid(int64_t n, int nh);
+cudaError_t run_tc_any(fhash_model* m, bool train, FusedArgs& a);
 
 static cudaError_t dispatch_fused(fhash_model* m, int which, FusedArgs& a) {
     a.lv = &m->lv;
@@ -182,7 +181,6 @@ fhash_status launch_forward(fhash_model* m, const float* coords, int64_t n, floa
     a.out = out;
     a.st = st;
     if (m->shadow) {  // precision form: bf16 tables, MLP on the tensor cores
-        a.grid = tc_grid(n, m->mlp.nh);
         FH_CUDA(run_tc_any(m, false, a));
     } else {
         FH_CUDA(dispatch_fused(m, 0, a));
@@ -201,7 +199,7 @@ fhash_status launch_forward_seg(fhash_model* m, const float* coords, float* out,
     a.st = st;
     a.seg = seg;
     if (m->shadow) {
-        a.grid = tc_grid(max_n, m->mlp.nh);
+        a.n = max_n;  // sizes the persistent grid; the kernel reads its count from `seg`
         FH_CUDA(run_tc_any(m, false, a));
     } else {
         a.n = max_n;  // sizes the persistent grid only

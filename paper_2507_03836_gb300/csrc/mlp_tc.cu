@@ -169,20 +169,21 @@ __device__ __forceinline__ void write_row(uint8_t* tile, int r, const float (&x)
     }
 }
 
+// Shared memory of a CTA with R sample tiles: R A tiles (128 x 64 bf16, 16 KB each), the layer weight
+// tiles (64 x 64 bf16, 8 KB each), biases, output layer, mbarrier and TMEM slot.
 struct TcSmem {
-    static constexpr int A = 0;          // 128 x 64 bf16 = 16 KB
-    static constexpr int W = 16384;      // per layer 64 x 64 bf16 = 8 KB
-    __host__ __device__ static int bias(int nh) { return W + nh * 8192; }
-    __host__ __device__ static int wout(int nh) { return bias(nh) + nh * 64 * 4; }
-    __host__ __device__ static int bout(int nh) { return wout(nh) + 64 * 4; }
-    __host__ __device__ static int mbar(int nh) { return bout(nh) + 16; }
-    __host__ __device__ static int slot(int nh) { return mbar(nh) + 8; }
-    __host__ __device__ static int bytes(int nh) { return slot(nh) + 8 + 1024; }  // + alignment slack
+    __host__ __device__ static int W(int R) { return R * 16384; }
+    __host__ __device__ static int bias(int R, int nh) { return W(R) + nh * 8192; }
+    __host__ __device__ static int wout(int R, int nh) { return bias(R, nh) + nh * 64 * 4; }
+    __host__ __device__ static int bout(int R, int nh) { return wout(R, nh) + 64 * 4; }
+    __host__ __device__ static int mbar(int R, int nh) { return bout(R, nh) + 16; }
+    __host__ __device__ static int slot(int R, int nh) { return mbar(R, nh) + 8; }
+    __host__ __device__ static int bytes(int R, int nh) { return slot(R, nh) + 8 + 1024; }  // + alignment slack
 };
 
-constexpr uint32_t kTmemCols = 64;
-
-template <int F, bool TRAIN>
+// R = samples per thread: the CTA holds R tiles of 128 samples (R MMA tiles, R x 64 TMEM columns),
+// so every thread keeps the gathers of R samples in flight.
+template <int F, bool TRAIN, int R>
 __global__ void __launch_bounds__(128) k_forward_tc(const __grid_constant__ Levels lv, const __grid_constant__ MlpShape sh,
                                                     const __nv_bfloat16* __restrict__ Tb,
                                                     const __nv_bfloat16* __restrict__ Pmb, const float* __restrict__ Pm,
@@ -198,16 +199,16 @@ __global__ void __launch_bounds__(128) k_forward_tc(const __grid_constant__ Leve
     extern __shared__ uint8_t smraw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
     const int nh = sh.nh, Wd = sh.width;
-    uint8_t* At = sm + TcSmem::A;
-    uint8_t* Wt = sm + TcSmem::W;
-    float* bias = reinterpret_cast<float*>(sm + TcSmem::bias(nh));
-    float* wout = reinterpret_cast<float*>(sm + TcSmem::wout(nh));
-    float* bout = reinterpret_cast<float*>(sm + TcSmem::bout(nh));
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + TcSmem::mbar(nh));
-    uint32_t* slot = reinterpret_cast<uint32_t*>(sm + TcSmem::slot(nh));
+    uint8_t* Wt = sm + TcSmem::W(R);
+    float* bias = reinterpret_cast<float*>(sm + TcSmem::bias(R, nh));
+    float* wout = reinterpret_cast<float*>(sm + TcSmem::wout(R, nh));
+    float* bout = reinterpret_cast<float*>(sm + TcSmem::bout(R, nh));
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + TcSmem::mbar(R, nh));
+    uint32_t* slot = reinterpret_cast<uint32_t*>(sm + TcSmem::slot(R, nh));
     const int t = threadIdx.x, warp = t >> 5;
+    constexpr uint32_t kCols = 64 * R;
 
-    if (warp == 0) tc::tmem_alloc(slot, kTmemCols);
+    if (warp == 0) tc::tmem_alloc(slot, kCols);
     if (t == 0) {
         tc::mbar_init(mbar, 1);
         tc::fence_mbar_init();
@@ -240,29 +241,39 @@ __global__ void __launch_bounds__(128) k_forward_tc(const __grid_constant__ Leve
     const uint32_t tmem = *slot;
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     constexpr uint32_t idesc = tc::idesc_bf16(128, 64);
-    const uint32_t a_addr = tc::smem_addr(At), w_addr = tc::smem_addr(Wt);
+    const uint32_t a_addr = tc::smem_addr(sm), w_addr = tc::smem_addr(Wt);
 
     uint32_t phase = 0;
     bool bad = false;
     double lsum = 0.0;
-    for (int64_t tile = blockIdx.x; tile * 128 < n && !bad; tile += gridDim.x) {
-        const int64_t i = tile * 128 + t;
-        const bool valid = i < n;
-        {
-            float4 u = valid ? load_coord(coords, i) : make_float4(0.f, 0.f, 0.f, 0.f);
-            encode_row_bf16<F, TRAIN>(lv, Tb, u, At, t, valid ? acts + i : nullptr, n);
+    for (int64_t tile = blockIdx.x; tile * (128 * R) < n && !bad; tile += gridDim.x) {
+        int64_t idx[R];
+        bool valid[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            idx[r] = tile * (128 * R) + r * 128 + t;
+            valid[r] = idx[r] < n;
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float4 u = valid[r] ? load_coord(coords, idx[r]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            encode_row_bf16<F, TRAIN>(lv, Tb, u, sm + r * 16384, t, valid[r] ? acts + idx[r] : nullptr, n);
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
         __syncthreads();
-        float y = bout[0];
+        float y[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) y[r] = bout[0];
         for (int j = 0; j < nh; ++j) {
             if (t == 0) {
                 tc::fence_after_sync();
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk)
-                    tc::mma_bf16(tmem, tc::sdesc_sw128(a_addr + kk * 32), tc::sdesc_sw128(w_addr + j * 8192 + kk * 32),
-                                 idesc, kk > 0 ? 1u : 0u);
+                for (int r = 0; r < R; ++r)
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        tc::mma_bf16(tmem + 64 * r, tc::sdesc_sw128(a_addr + r * 16384 + kk * 32),
+                                     tc::sdesc_sw128(w_addr + j * 8192 + kk * 32), idesc, kk > 0 ? 1u : 0u);
                 tc::mma_commit(mbar);
             }
             const bool ok = tc::mbar_wait(mbar, phase);
@@ -271,23 +282,26 @@ __global__ void __launch_bounds__(128) k_forward_tc(const __grid_constant__ Leve
             tc::fence_after_sync();
             const bool last = j + 1 == nh;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {  // 32 accumulator columns at a time
-                float v[32];
-                tc::tmem_ld32(lane_base + 32 * h, v);
-                tc::tmem_ld_wait();
+            for (int r = 0; r < R; ++r) {
 #pragma unroll
-                for (int q = 0; q < 32; ++q) v[q] = fmaxf(v[q] + bias[j * 64 + 32 * h + q], 0.0f);
-                if (TRAIN && valid) {
-                    float* a = acts + (int64_t)(sh.in + j * Wd) * n + i;
+                for (int h = 0; h < 2; ++h) {  // 32 accumulator columns at a time
+                    float v[32];
+                    tc::tmem_ld32(lane_base + 64 * r + 32 * h, v);
+                    tc::tmem_ld_wait();
 #pragma unroll
-                    for (int q = 0; q < 32; ++q)
-                        if (32 * h + q < Wd) a[(int64_t)(32 * h + q) * n] = v[q];
-                }
-                if (!last) {
-                    write_half_row(At, t, h, v);
-                } else {
+                    for (int q = 0; q < 32; ++q) v[q] = fmaxf(v[q] + bias[j * 64 + 32 * h + q], 0.0f);
+                    if (TRAIN && valid[r]) {
+                        float* a = acts + (int64_t)(sh.in + j * Wd) * n + idx[r];
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) y = fmaf(wout[32 * h + q], v[q], y);  // scalar output layer
+                        for (int q = 0; q < 32; ++q)
+                            if (32 * h + q < Wd) a[(int64_t)(32 * h + q) * n] = v[q];
+                    }
+                    if (!last) {
+                        write_half_row(sm + r * 16384, t, h, v);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) y[r] = fmaf(wout[32 * h + q], v[q], y[r]);  // scalar output layer
+                    }
                 }
             }
             if (!last) tc::fence_async_smem();
@@ -295,13 +309,15 @@ __global__ void __launch_bounds__(128) k_forward_tc(const __grid_constant__ Leve
             __syncthreads();
         }
         if (bad) break;
-        if (valid) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (!valid[r]) continue;
             if (TRAIN) {
-                const float r = y - __ldg(target + i);
-                gy[i] = two_over_n * r;
-                lsum += (double)r * (double)r;
+                const float d = y[r] - __ldg(target + idx[r]);
+                gy[idx[r]] = two_over_n * d;
+                lsum += (double)d * (double)d;
             } else {
-                out[i] = y;
+                out[idx[r]] = y[r];
             }
         }
     }
@@ -315,42 +331,44 @@ __global__ void __launch_bounds__(128) k_forward_tc(const __grid_constant__ Leve
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+    if (warp == 0) tc::tmem_dealloc(tmem, kCols);
 }
 
+// Samples per thread (the kernel supports R tiles per CTA; one measured fastest).
+constexpr int kRInfer = 1, kRTrain = 1;
+
+// Launches the tensor-core forward over a.n samples (the largest segment for segment launches) on a
+// persistent grid of kCtasPerSm CTAs per SM with half the unified L1/shared memory as shared memory.
+// Measured on GB300 (1024^2 renders and 4M uniform points, advect-128^3x32): the gathers depend on L1
+// capacity (the maximum shared carve-out halves throughput) and 3 CTAs of 4 warps per SM are as fast
+// as 6 or 8; 2 samples per thread (more registers, fewer warps) is slower.  3 x 64 TMEM columns per SM
+// never approach the 512 available.  a.grid returns the grid used.
+constexpr int kCtasPerSm = 3;
 template <int F>
-static cudaError_t run_tc(fhash_model* m, bool train, const FusedArgs& a) {
-    const int smem = TcSmem::bytes(m->mlp.nh);
-    const void* fn = train ? (const void*)k_forward_tc<F, true> : (const void*)k_forward_tc<F, false>;
+static cudaError_t run_tc(fhash_model* m, bool train, FusedArgs& a) {
+    const int R = train ? kRTrain : kRInfer;
+    const int smem = TcSmem::bytes(R, m->mlp.nh);
+    const void* fn = train ? (const void*)k_forward_tc<F, true, kRTrain> : (const void*)k_forward_tc<F, false, kRInfer>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 50);
     if (e != cudaSuccess) return e;
+    const int64_t tiles = (std::max<int64_t>(a.n, 1) + 128 * R - 1) / (128 * R);
+    a.grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)num_sms() * kCtasPerSm));
     const __nv_bfloat16* Tb = m->shadow;
     const __nv_bfloat16* Pmb = m->shadow + m->n_table;
     const float* Pm = m->param + m->n_table;
     if (train)
-        k_forward_tc<F, true><<<a.grid, 128, smem, a.st>>>(m->lv, m->mlp, Tb, Pmb, Pm, a.coords, a.target, a.n, nullptr,
-                                                           a.acts, a.gy, a.partial, 2.0f / (float)a.n, m->err_word, nullptr);
+        k_forward_tc<F, true, kRTrain><<<a.grid, 128, smem, a.st>>>(m->lv, m->mlp, Tb, Pmb, Pm, a.coords, a.target, a.n,
+                                                                    nullptr, a.acts, a.gy, a.partial, 2.0f / (float)a.n,
+                                                                    m->err_word, nullptr);
     else
-        k_forward_tc<F, false><<<a.grid, 128, smem, a.st>>>(m->lv, m->mlp, Tb, Pmb, Pm, a.coords, nullptr, a.n, a.out,
-                                                            nullptr, nullptr, nullptr, 0.0f, m->err_word, a.seg);
+        k_forward_tc<F, false, kRInfer><<<a.grid, 128, smem, a.st>>>(m->lv, m->mlp, Tb, Pmb, Pm, a.coords, nullptr, a.n,
+                                                                     a.out, nullptr, nullptr, nullptr, 0.0f, m->err_word,
+                                                                     a.seg);
     return cudaGetLastError();
 }
 
-// Grid for the tensor-core kernels: persistent, as many CTAs per SM as shared memory lets reside.
-// Every configuration takes at least 26 KB of shared memory per CTA, so at most 8 CTAs share an SM:
-// 8 x 64 = 512 TMEM columns, never more than the SM has (allocation can never wait on a CTA that waits).
-int tc_grid(int64_t n, int nh) {
-    static int smem_sm = 0;
-    if (!smem_sm) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    }
-    const int per_sm = std::max(1, std::min(8, smem_sm / (TcSmem::bytes(nh) + 1024)));
-    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, (int64_t)num_sms() * per_sm));
-}
-
-cudaError_t run_tc_any(fhash_model* m, bool train, const FusedArgs& a) {
+cudaError_t run_tc_any(fhash_model* m, bool train, FusedArgs& a) {
     switch (m->lv.F) {
         case 1: return run_tc<1>(m, train, a);
         case 2: return run_tc<2>(m, train, a);

@@ -324,8 +324,7 @@ __global__ void k_loss2(const double* __restrict__ partial, int nb, int64_t n, d
     if (threadIdx.x == 0) *loss = red[0] / (double)n;
 }
 
-cudaError_t run_tc_any(fhash_model* m, bool train, const FusedArgs& a);
-int tc_grid(int64_t n, int nh);
+cudaError_t run_tc_any(fhash_model* m, bool train, FusedArgs& a);
 bool launch_dw_tc(fhash_model* m, const float* acts, const float* dl, int64_t n, float* wpart, size_t wpart_bytes,
                   cudaStream_t st, cudaError_t* err);
 
@@ -366,8 +365,7 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
     const int64_t D = (int64_t)sh.nh * W + 1;       // delta rows
     FH_TRY(grow(m, m->s_acts, (size_t)(A * n * 4)));
     FH_TRY(grow(m, m->s_gacts, (size_t)((D + 1 + sh.in) * n * 4)));
-    const int nb = m->shadow ? tc_grid(n, m->mlp.nh)
-                             : (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, (int64_t)num_sms() * 8));
+    int nb = (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, (int64_t)num_sms() * 8));  // loss partials
     const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, (int64_t)num_sms() * 2));
     const int64_t chunk = ((n + nchunk - 1) / nchunk + 31) / 32 * 32;
     int ne_max = 0;
@@ -382,7 +380,8 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
     float* dl = gy + n;
     float* denc = dl + D * n;
     double* lpart = (double*)m->s_partial.p;
-    float* wpart = (float*)((char*)m->s_partial.p + ((size_t)nb * 8 + 63) / 64 * 64);
+    const size_t wpart_off = ((size_t)nb * 8 + 63) / 64 * 64;  // fixed before nb shrinks to the grid used
+    float* wpart = (float*)((char*)m->s_partial.p + wpart_off);
     const float* Pm = m->param + m->n_table;
     const GLayout GL = g_layout(sh);
     const int gsmem = GL.floats * 4;
@@ -391,8 +390,8 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
     if (m->shadow) {
         FusedArgs a{};
         a.coords = coords; a.target = target; a.n = n; a.acts = acts; a.gy = gy; a.partial = lpart; a.st = st;
-        a.grid = nb;
         FH_CUDA(run_tc_any(m, true, a));
+        nb = a.grid;  // at most one loss partial per CTA, never more than the buffer holds
     } else {
         const unsigned eg = (unsigned)((n * m->lv.L + 255) / 256);
         switch (F) {
@@ -424,7 +423,7 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
     // otherwise (the float32 form keeps full float32 products)
     if (m->shadow) {
         cudaError_t e = cudaSuccess;
-        if (launch_dw_tc(m, acts, dl, n, wpart, m->s_partial.bytes - ((size_t)nb * 8 + 63) / 64 * 64, st, &e)) {
+        if (launch_dw_tc(m, acts, dl, n, wpart, m->s_partial.bytes - wpart_off, st, &e)) {
             FH_CUDA(e);
             return FHASH_OK;
         }
