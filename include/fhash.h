@@ -168,6 +168,20 @@ fhash_status fhash_lookup(fhash_model* model, const float* coords, int64_t n, ui
  * (coarsest) first.  coords: device [n][4]; enc: device.  n = 0 is a no-op. */
 fhash_status fhash_encode(fhash_model* model, const float* coords, int64_t n, float* enc, fhash_stream stream);
 
+/*
+ * Backward of fhash_encode.  Eqs. 10-12 are linear in the table, so for every sample n, level l,
+ * corner c (Eq. 9 row r) and feature f it adds w_c(n) * d_enc[n][l*F + f] to the gradient of
+ * table element [r][f].  The sums ACCUMULATE in the model's gradient buffer (the table part of
+ * FHASH_STATE_GRAD), which fhash_apply_adam consumes and clears; the MLP part is not touched.
+ * Weights are recomputed from the coordinates, not stored.
+ *  coords: device [n][4], the coordinates given to fhash_encode; d_enc: device [n][L*F] float32,
+ *  row-major like fhash_encode's output.  Both stay owned by the caller.  n = 0 is a no-op; host
+ *  pointers are FHASH_EINVAL.  Additions are float32 atomics: their order, and so the last bits
+ *  of the sums, is not deterministic.
+ */
+fhash_status fhash_encode_backward(fhash_model* model, const float* coords, const float* d_enc, int64_t n,
+                                   fhash_stream stream);
+
 /* Encoding fused with the MLP decoder (Section 3.2.4): out[n] float32.
  * coords: host or device [n][4]; out: host or device [n]. */
 fhash_status fhash_forward(fhash_model* model, const float* coords, int64_t n, float* out, fhash_stream stream);

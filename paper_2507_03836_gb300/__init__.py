@@ -87,6 +87,7 @@ _SIGS = {
     "fhash_get_info": [_vp, ctypes.POINTER(fhash_info)],
     "fhash_lookup": [_vp, _vp, _i64, _vp, _vp, _vp],
     "fhash_encode": [_vp, _vp, _i64, _vp, _vp],
+    "fhash_encode_backward": [_vp, _vp, _vp, _i64, _vp],
     "fhash_forward": [_vp, _vp, _i64, _vp, _vp],
     "fhash_compute_grads": [_vp, _vp, _vp, _i64, _vp, _vp],
     "fhash_apply_adam": [_vp, ctypes.POINTER(fhash_adam), _vp],
@@ -220,6 +221,10 @@ def fhash_lookup(model, coords, rows, weights=None, stream=None):
 
 def fhash_encode(model, coords, enc, stream=None):
     _ok(_lib.fhash_encode(model.handle, _ptr(coords), coords.shape[0], _ptr(enc), _stream(stream)))
+
+
+def fhash_encode_backward(model, coords, d_enc, stream=None):
+    _ok(_lib.fhash_encode_backward(model.handle, _ptr(coords), _ptr(d_enc), coords.shape[0], _stream(stream)))
 
 
 def fhash_forward(model, coords, out, stream=None):

@@ -163,6 +163,8 @@ fhash_status launch_forward_seg(fhash_model* m, const float* coords, float* out,
 // Forward + loss + backward into the gradient buffer (csrc/train.cu).
 fhash_status launch_grads2(fhash_model* m, const float* coords, const float* target, int64_t n, double* loss_dev,
                            cudaStream_t st);
+// Table-gradient scatter of the encoding alone, d(encoding) row-major [n][L*F] (csrc/train.cu).
+fhash_status launch_encode_backward(fhash_model* m, const float* coords, int64_t n, const float* denc, cudaStream_t st);
 fhash_status launch_adam(fhash_model* m, const fhash_adam* a, cudaStream_t st);
 fhash_status refresh_shadow(fhash_model* m, uint64_t off, uint64_t n, cudaStream_t st);
 

@@ -255,6 +255,16 @@ fhash_status fhash_encode(fhash_model* m, const float* coords, int64_t n, float*
     return launch_encode(m, coords, n, enc, (cudaStream_t)stream);
 }
 
+fhash_status fhash_encode_backward(fhash_model* m, const float* coords, const float* d_enc, int64_t n,
+                                   fhash_stream stream) {
+    FH_TRY(check_model(m, "fhash_encode_backward"));
+    if (n < 0 || (n && (!coords || !d_enc))) return set_error(FHASH_EINVAL, "fhash_encode_backward: bad arguments");
+    if (n == 0) return FHASH_OK;
+    if (!is_device_ptr(coords) || !is_device_ptr(d_enc))
+        return set_error(FHASH_EINVAL, "fhash_encode_backward: buffers must be device memory");
+    return launch_encode_backward(m, coords, n, d_enc, (cudaStream_t)stream);
+}
+
 fhash_status fhash_forward(fhash_model* m, const float* coords, int64_t n, float* out, fhash_stream stream) {
     FH_TRY(check_model(m, "fhash_forward"));
     if (n < 0 || (n && (!coords || !out))) return set_error(FHASH_EINVAL, "fhash_forward: bad arguments");

@@ -57,7 +57,7 @@ struct ScatterPlan {
 template <int F>
 __global__ void __launch_bounds__(256) k_scatter_cols(const __grid_constant__ Levels lv, const __grid_constant__ ScatterPlan P,
                                                       float* __restrict__ G, const float* __restrict__ coords, int64_t n,
-                                                      const float* __restrict__ denc) {
+                                                      const float* __restrict__ denc, int64_t dsf, int64_t dss) {
     extern __shared__ float acc[];
     int l = 0;
     while (l + 1 < lv.L && (int)blockIdx.x >= P.first[l + 1]) ++l;
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256) k_scatter_cols(const __grid_constant__ Le
             Corners k = corners(L, load_coord(coords, s));
             float g[F];
 #pragma unroll
-            for (int f = 0; f < F; ++f) g[f] = denc[(int64_t)(l * F + f) * n + s];
+            for (int f = 0; f < F; ++f) g[f] = denc[(int64_t)(l * F + f) * dsf + s * dss];
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
                 const float w = corner_weight(k, c);
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256) k_scatter_cols(const __grid_constant__ Le
         Corners k = corners(L, load_coord(coords, s));
         float g[F];
 #pragma unroll
-        for (int f = 0; f < F; ++f) g[f] = denc[(int64_t)(l * F + f) * n + s];
+        for (int f = 0; f < F; ++f) g[f] = denc[(int64_t)(l * F + f) * dsf + s * dss];
 #pragma unroll
         for (int c = 0; c < 16; ++c) red_row<F>(G + corner_row(k, c) * F, corner_weight(k, c), g);
     }
@@ -329,7 +329,8 @@ bool launch_dw_tc(fhash_model* m, const float* acts, const float* dl, int64_t n,
                   cudaStream_t st, cudaError_t* err);
 
 template <int F>
-static cudaError_t scatter_launch(fhash_model* m, const float* coords, int64_t n, const float* denc, cudaStream_t st) {
+static cudaError_t scatter_launch(fhash_model* m, const float* coords, int64_t n, const float* denc, int64_t dsf,
+                                  int64_t dss, cudaStream_t st) {
     constexpr int64_t kPrivMax = 16384;  // floats of a level accumulated in shared memory (64 KB)
     ScatterPlan P{};
     int blocks = 0;
@@ -353,8 +354,21 @@ static cudaError_t scatter_launch(fhash_model* m, const float* coords, int64_t n
     cudaError_t e = cudaFuncSetAttribute((const void*)k_scatter_cols<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          std::max(smem, 1));
     if (e != cudaSuccess) return e;
-    k_scatter_cols<F><<<blocks, 256, smem, st>>>(m->lv, P, m->grad, coords, n, denc);
+    k_scatter_cols<F><<<blocks, 256, smem, st>>>(m->lv, P, m->grad, coords, n, denc, dsf, dss);
     return cudaGetLastError();
+}
+
+// Backward of the encoding alone: d(encoding) given row-major [n][L*F] (the layout of fhash_encode).
+fhash_status launch_encode_backward(fhash_model* m, const float* coords, int64_t n, const float* denc, cudaStream_t st) {
+    const int64_t LF = (int64_t)m->lv.L * m->lv.F;
+    switch (m->lv.F) {
+        case 1: FH_CUDA(scatter_launch<1>(m, coords, n, denc, 1, LF, st)); break;
+        case 2: FH_CUDA(scatter_launch<2>(m, coords, n, denc, 1, LF, st)); break;
+        case 4: FH_CUDA(scatter_launch<4>(m, coords, n, denc, 1, LF, st)); break;
+        case 8: FH_CUDA(scatter_launch<8>(m, coords, n, denc, 1, LF, st)); break;
+        default: return set_error(FHASH_EINVAL, "F=%d unsupported", m->lv.F);
+    }
+    return FHASH_OK;
 }
 
 fhash_status launch_grads2(fhash_model* m, const float* coords, const float* target, int64_t n, double* loss_dev,
@@ -414,10 +428,10 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
     k_mlp_bwd_g<<<bb, 128, gsmem, st>>>(sh, Pm, n, acts, gy, dl, denc);
     FH_CUDA(cudaGetLastError());
     switch (F) {
-        case 1: FH_CUDA(scatter_launch<1>(m, coords, n, denc, st)); break;
-        case 2: FH_CUDA(scatter_launch<2>(m, coords, n, denc, st)); break;
-        case 4: FH_CUDA(scatter_launch<4>(m, coords, n, denc, st)); break;
-        case 8: FH_CUDA(scatter_launch<8>(m, coords, n, denc, st)); break;
+        case 1: FH_CUDA(scatter_launch<1>(m, coords, n, denc, n, 1, st)); break;
+        case 2: FH_CUDA(scatter_launch<2>(m, coords, n, denc, n, 1, st)); break;
+        case 4: FH_CUDA(scatter_launch<4>(m, coords, n, denc, n, 1, st)); break;
+        case 8: FH_CUDA(scatter_launch<8>(m, coords, n, denc, n, 1, st)); break;
     }
     // weight gradients: tensor cores (TMA + tcgen05 kind::tf32) for the bf16 form, float32 SIMT tiles
     // otherwise (the float32 form keeps full float32 products)
