@@ -27,10 +27,26 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "train samples/s (enc+MLP fwd+bwd); render p50/p99 ms; BF16 vs FP32 @PSNR"
-# DRAM bytes per parameter of k_adam from one ncu capture of the same kernel on advect-128^3x32
-# (profiles/ncu_k_adam_advect-128^3x32.md): 8.147 GB / 256,431,192 parameters.  The traffic of this
-# streaming kernel grows in proportion to the parameter count, so it scales to the full launch.
-ADAM_DRAM_BYTES_PER_PARAM = 8.147e9 / 256431192
+# DRAM bytes per parameter of k_adam from an ncu capture of the current kernel (None: not yet taken
+# since the kernel last changed, and the bench then reports no traffic).
+ADAM_DRAM_BYTES_PER_PARAM = None
+
+
+def _touched_fraction(fh, model, info, coords, tgt, hp, chunk=1 << 28):
+    """One more training step, untimed: the fraction of 4-parameter gradient groups that are non-zero
+    before its Adam update."""
+    import torch
+    n = info["n_table_params"] + info["n_mlp_params"]
+    fh.fhash_compute_grads(model, coords, tgt)
+    buf = torch.empty(min(chunk, n), dtype=torch.float32, device="cuda")
+    hit = 0
+    for off in range(0, n - n % 4, chunk):
+        k = min(chunk, n - n % 4 - off)
+        fh.fhash_read_state(model, fh.STATE_GRAD, off, buf[:k])
+        hit += int(buf[:k].view(-1, 4).ne(0).any(1).sum())
+    fh.fhash_apply_adam(model, hp)
+    torch.cuda.synchronize()
+    return hit / max(1, n // 4)
 
 
 def _peaks():
@@ -526,6 +542,10 @@ def main():
     adam_ms = float(np.mean([ev[k][1].elapsed_time(ev[k][2]) for k in range(K)]))
     losses = loss_d.cpu().numpy()
 
+    # fraction of 4-parameter groups with a non-zero gradient after one step (untimed): k_adam writes the
+    # cleared gradient back only there, so its algorithmic bytes are 28 B/param + 4 B x that fraction
+    touched = _touched_fraction(fh, model, info, coords_d[args.warmup], tgt_d[args.warmup], hp)
+
     # end to end through the public API: host (pinned) inputs copied in, loss read back, every step
     pin_c = [torch.from_numpy(c).pin_memory() for c in coords_h[:K]]
     pin_t = [torch.from_numpy(t).pin_memory() for t in tgt_h[:K]]
@@ -553,8 +573,10 @@ def main():
 
     n_params = info["n_table_params"] + info["n_mlp_params"]
     peaks, peak_kind = _peaks()
-    # read p, g, m, v; write p, m, v and the cleared g (+ the bf16 shadow of p in the precision form)
-    adam_bytes = (34.0 if args.dtype == "bf16" else 32.0) * n_params
+    # read p, g, m, v; write p, m, v, the cleared g where it was not zero (+ the bf16 shadow of p in the
+    # precision form)
+    adam_bpp = (30.0 if args.dtype == "bf16" else 28.0) + 4.0 * touched
+    adam_bytes = adam_bpp * n_params
     achieved = adam_bytes / (adam_ms / 1e3) / 1e9
     value = world * B * K / elapsed
 
@@ -570,9 +592,10 @@ def main():
         "gpu_launches": K * (4 + 2 * (w["hidden"] + 1)),
         "roofline": {"kernel": "k_adam", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                     "traffic": ADAM_DRAM_BYTES_PER_PARAM * n_params if args.dtype == "f32" else None,
+                     "traffic": ADAM_DRAM_BYTES_PER_PARAM * n_params if ADAM_DRAM_BYTES_PER_PARAM and args.dtype == "f32" else None,
                      "traffic_note": "ncu dram__bytes_read+write of k_adam on advect-128^3x32, scaled by parameters",
-                     "peak_source": peak_kind, "bytes_per_launch": adam_bytes},
+                     "peak_source": peak_kind, "bytes_per_launch": adam_bytes, "bytes_per_param": adam_bpp,
+                     "grad_groups_touched": touched},
         "clocks": clk,
         "e2e": {"value": world * B * K / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": B * 20,
                 "d2h_bytes_per_step": 8},

@@ -182,6 +182,18 @@ fhash_status fhash_encode(fhash_model* model, const float* coords, int64_t n, fl
 fhash_status fhash_encode_backward(fhash_model* model, const float* coords, const float* d_enc, int64_t n,
                                    fhash_stream stream);
 
+/*
+ * How fhash_forward, fhash_render and fhash_decode evaluate FHASH_BF16 models (float32 models have
+ * one path).  FUSED: one kernel encodes each 128-sample tile into shared memory and runs the MLP on
+ * it.  SPLIT: per chunk of up to 2^20 samples, one kernel writes the bf16 encoding rows and a second
+ * one runs the MLP on the tensor cores, fed by TMA from those rows.  Both give bit-identical outputs;
+ * they differ only in speed.  AUTO (the default) takes FUSED, the faster of the two on GB300 at every
+ * batch size measured.  The serving loop always uses the fused kernel.  Unknown values are
+ * FHASH_EINVAL.
+ */
+enum { FHASH_FORWARD_AUTO = 0, FHASH_FORWARD_FUSED = 1, FHASH_FORWARD_SPLIT = 2 };
+fhash_status fhash_set_forward_path(fhash_model* model, int32_t path);
+
 /* Encoding fused with the MLP decoder (Section 3.2.4): out[n] float32.
  * coords: host or device [n][4]; out: host or device [n]. */
 fhash_status fhash_forward(fhash_model* model, const float* coords, int64_t n, float* out, fhash_stream stream);

@@ -1,11 +1,11 @@
 """bf16 precision form of the forward pass (oracle; test infrastructure only).
 
 The precision form stores embeddings and MLP weights in bf16 (rounded to nearest, ties to even,
-from the float32 master values) and feeds bf16 inputs to each hidden layer's matrix product, with
-accumulation in float32 on the GPU.  This module rounds exactly the same quantities to bf16 and then
-computes in float64, so the remaining difference to the GPU is its float32 accumulation (and, rarely,
-a value on a bf16 rounding boundary that float32 and float64 round to neighbouring bf16 values).
-Biases and the scalar output layer stay float32, as on the GPU.
+from the float32 master values) and feeds bf16 inputs to every layer's matrix product, the scalar
+output layer included, with accumulation in float32 on the GPU.  This module rounds exactly the same
+quantities to bf16 and then computes in float64, so the remaining difference to the GPU is its
+float32 accumulation (and, rarely, a value on a bf16 rounding boundary that float32 and float64
+round to neighbouring bf16 values).  Biases stay float32, as on the GPU.
 """
 import numpy as np
 
@@ -22,15 +22,15 @@ def bf16_round(x):
 
 
 def forward_bf16(levels, level_bases, table, params, dims, coords):
-    """y [N] of the precision form: bf16 table values, quadrilinear interpolation (float64), then each
-    hidden layer on bf16 inputs and bf16 weights, float32 biases; output layer on unrounded inputs."""
+    """y [N] of the precision form: bf16 table values, quadrilinear interpolation (float64), then every
+    layer on bf16 inputs and bf16 weights with float32 biases (ReLU after the hidden layers)."""
     enc = encode.encode(levels, level_bases, coords, bf16_round(np.asarray(table, np.float32)))
     layers = mlp.unpack(params, dims)
     x = enc
     for k, (W, b) in enumerate(layers[:-1]):
         x = np.maximum(bf16_round(x) @ bf16_round(W).T + b, 0.0)
     Wo, bo = layers[-1]
-    return (x @ Wo.T + bo)[:, 0]
+    return (bf16_round(x) @ bf16_round(Wo).T + bo)[:, 0]
 
 
 def grads_bf16(levels, level_bases, table, params, dims, coords, targets):
@@ -48,7 +48,7 @@ def grads_bf16(levels, level_bases, table, params, dims, coords, targets):
         x = np.maximum(z, 0.0)
         acts.append(x)
     Wo, bo = layers[-1]
-    y = (x @ Wo.T + bo)[:, 0]
+    y = (bf16_round(x) @ bf16_round(Wo).T + bo)[:, 0]
     L, gy = mlp.mse(y, targets)
     g, _ = mlp.backward(params, dims, acts, pre + [None], gy)
     gabs, _ = mlp.backward(np.abs(params), dims, [np.abs(a) for a in acts],

@@ -89,6 +89,7 @@ _SIGS = {
     "fhash_encode": [_vp, _vp, _i64, _vp, _vp],
     "fhash_encode_backward": [_vp, _vp, _vp, _i64, _vp],
     "fhash_forward": [_vp, _vp, _i64, _vp, _vp],
+    "fhash_set_forward_path": [_vp, _i32],
     "fhash_compute_grads": [_vp, _vp, _vp, _i64, _vp, _vp],
     "fhash_apply_adam": [_vp, ctypes.POINTER(fhash_adam), _vp],
     "fhash_train_step": [_vp, _vp, _vp, _i64, ctypes.POINTER(fhash_adam), _vp, _vp],
@@ -225,6 +226,13 @@ def fhash_encode(model, coords, enc, stream=None):
 
 def fhash_encode_backward(model, coords, d_enc, stream=None):
     _ok(_lib.fhash_encode_backward(model.handle, _ptr(coords), _ptr(d_enc), coords.shape[0], _stream(stream)))
+
+
+FORWARD_AUTO, FORWARD_FUSED, FORWARD_SPLIT = 0, 1, 2
+
+
+def fhash_set_forward_path(model, path):
+    _ok(_lib.fhash_set_forward_path(model.handle, path))
 
 
 def fhash_forward(model, coords, out, stream=None):

@@ -79,8 +79,9 @@ struct fhash_model {
     int* err_word = nullptr;  // device error word (0 = ok)
 
     // scratch (grown on demand; owned by the model)
-    fh::Scratch s_coords, s_target, s_out, s_acts, s_gacts, s_partial, s_loss, s_misc, s_render;
+    fh::Scratch s_coords, s_target, s_out, s_acts, s_gacts, s_partial, s_loss, s_misc, s_render, s_enc;
     uint64_t device_bytes = 0;
+    int32_t forward_path = 0;  // FHASH_FORWARD_* (precision form only)
 };
 
 namespace fh {
@@ -158,6 +159,8 @@ inline int num_sms() {
 fhash_status launch_lookup(fhash_model* m, const float* coords, int64_t n, uint64_t* rows, float* w, cudaStream_t st);
 fhash_status launch_encode(fhash_model* m, const float* coords, int64_t n, float* enc, cudaStream_t st);
 fhash_status launch_forward(fhash_model* m, const float* coords, int64_t n, float* out, cudaStream_t st);
+// Precision form, split evaluation: bf16 encoding rows, then the TMA-fed tensor-core MLP (csrc/mlp_split.cu).
+fhash_status launch_forward_split(fhash_model* m, const float* coords, int64_t n, float* out, cudaStream_t st);
 fhash_status launch_forward_seg(fhash_model* m, const float* coords, float* out, const int64_t* seg, int64_t max_n,
                                 cudaStream_t st);
 // Forward + loss + backward into the gradient buffer (csrc/train.cu).

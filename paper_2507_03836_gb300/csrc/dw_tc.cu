@@ -146,7 +146,7 @@ __global__ void k_rowsum_final(const float* __restrict__ part, int fo, float* __
     grad[o] += s;
 }
 
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
         void* p = nullptr;

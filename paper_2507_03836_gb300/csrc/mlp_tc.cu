@@ -7,175 +7,27 @@
 // K=64 as 4 x K=16) against the layer's weight tile, also bf16 in shared memory, accumulating float32
 // in 64 TMEM columns; tcgen05.commit arrives on an mbarrier when they are done.  Each warp reads its
 // 32 TMEM lanes back (tcgen05.ld), adds the bias, applies ReLU and writes the next layer's A rows.
-// The scalar output layer runs on the CUDA cores in float32.  Widths below 64 and inputs below 64 are
-// zero-padded to 64 (the padding multiplies zeros).  Every mbarrier wait is bounded: on timeout the
+// The scalar output layer is an M=128, N=16 MMA of the last hidden rows against a 16-row weight tile
+// whose row 0 holds the output weights (rows 1-15 zero) into 16 more TMEM columns; column 0 plus the
+// float32 output bias is the result.  Widths below 64 and inputs below 64 are zero-padded to 64 (the
+// padding multiplies zeros).  Every mbarrier wait is bounded: on timeout the
 // kernel reports through the model's error word, waits once more for its MMAs and frees its TMEM.
 #include <math.h>
 
 #include <algorithm>
 
-#include "kernels.cuh"
-#include "tc.cuh"
+#include "bf16.cuh"
 
 namespace fh {
 
-template <int F>
-__device__ __forceinline__ void load_row_bf16(const __nv_bfloat16* __restrict__ T, uint64_t r, float (&v)[F]) {
-    const __nv_bfloat16* p = T + r * F;
-    if constexpr (F == 1) {
-        v[0] = __bfloat162float(p[0]);
-    } else if constexpr (F == 2) {
-        uint32_t w = __ldg(reinterpret_cast<const unsigned int*>(p));
-        __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162*>(&w);
-        float2 f = __bfloat1622float2(b);
-        v[0] = f.x; v[1] = f.y;
-    } else if constexpr (F == 4) {
-        uint2 w = __ldg(reinterpret_cast<const uint2*>(p));
-        float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&w.x));
-        float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&w.y));
-        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-    } else {
-        uint4 w = __ldg(reinterpret_cast<const uint4*>(p));
-        uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&ws[q]));
-            v[2 * q] = a.x; v[2 * q + 1] = a.y;
-        }
-    }
-}
-
-template <int F>
-__device__ __forceinline__ void interp_level_bf16(const __nv_bfloat16* __restrict__ T, const Corners& k, float* out) {
-    float v[16][F];
-#pragma unroll
-    for (int c = 0; c < 16; c += 2) {
-        uint64_t r = k.r0 + ((c & 8) ? k.ot : 0ull) + ((c & 4) ? k.oz : 0u) + ((c & 2) ? k.oy : 0u);
-        load_row_bf16<F>(T, r, v[c]);
-        load_row_bf16<F>(T, r + k.ox, v[c + 1]);
-    }
-#pragma unroll
-    for (int f = 0; f < F; ++f) {
-        float vt[2];
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            float vz[2];
-#pragma unroll
-            for (int kz = 0; kz < 2; ++kz) {
-                const int c = 8 * s + 4 * kz;
-                float y0 = fmaf(k.wx, v[c + 1][f] - v[c][f], v[c][f]);
-                float y1 = fmaf(k.wx, v[c + 3][f] - v[c + 2][f], v[c + 2][f]);
-                vz[kz] = fmaf(k.wy, y1 - y0, y0);
-            }
-            vt[s] = fmaf(k.wz, vz[1] - vz[0], vz[0]);
-        }
-        out[f] = fmaf(k.wt, vt[1] - vt[0], vt[0]);
-    }
-}
-
-// enc[64] (zero beyond L*F) from the bf16 tables.
-template <int F>
-__device__ __forceinline__ void encode64_bf16(const Levels& lv, const __nv_bfloat16* __restrict__ T, float4 u,
-                                              float (&enc)[64]) {
-#pragma unroll
-    for (int i = 0; i < 64; ++i) enc[i] = 0.0f;
-#pragma unroll
-    for (int l = 0; l < 64 / F; ++l) {
-        if (l < lv.L) {
-            Corners k = corners(lv.lv[l], u);
-            float o[F];
-            interp_level_bf16<F>(T, k, o);
-#pragma unroll
-            for (int f = 0; f < F; ++f) enc[l * F + f] = o[f];
-        }
-    }
-}
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b);
-
-// Encodes one sample straight into its bf16 row t of the A tile (column l*F + f for level l, zeros
-// beyond L*F), without holding the whole encoding in registers; in training also stores the float32
-// encoding to the activation columns.
-// Shared-memory stores as explicit st.shared without a memory clobber: the compiler knows they cannot
-// alias the global gathers and keeps issuing the next level's loads ahead of them.
-__device__ __forceinline__ void sts32(uint32_t a, uint32_t v) { asm volatile("st.shared.b32 [%0], %1;" ::"r"(a), "r"(v)); }
-__device__ __forceinline__ void sts16(uint32_t a, unsigned short v) { asm volatile("st.shared.b16 [%0], %1;" ::"r"(a), "h"(v)); }
-__device__ __forceinline__ void sts64(uint32_t a, uint32_t x, uint32_t y) {
-    asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a), "r"(x), "r"(y));
-}
-__device__ __forceinline__ void sts128(uint32_t a, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
-    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w));
-}
-
-// Encodes one sample straight into its bf16 row t of the A tile (column l*F + f for level l, zeros
-// beyond L*F), without holding the whole encoding in registers; in training also stores the float32
-// encoding to the activation columns.
-template <int F, bool TRAIN>
-__device__ __forceinline__ void encode_row_bf16(const Levels& lv, const __nv_bfloat16* __restrict__ T, float4 u,
-                                                uint8_t* tile, int t, float* acts, int64_t n) {
-    const uint32_t rowa = tc::smem_addr(tile) + (t >> 3) * 1024 + (t & 7) * 128;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) sts128(rowa + ((c ^ (t & 7)) << 4), 0u, 0u, 0u, 0u);
-#pragma unroll
-    for (int l = 0; l < 64 / F; ++l) {
-        if (l < lv.L) {
-            Corners k = corners(lv.lv[l], u);
-            float o[F];
-            interp_level_bf16<F>(T, k, o);
-            if (TRAIN && acts) {
-#pragma unroll
-                for (int f = 0; f < F; ++f) acts[(int64_t)(l * F + f) * n] = o[f];
-            }
-            const int byte = l * F * 2;  // column l*F
-            const uint32_t dst = rowa + (((byte >> 4) ^ (t & 7)) << 4) + (byte & 15);
-            if constexpr (F == 1) {
-                __nv_bfloat16 h = __float2bfloat16_rn(o[0]);
-                sts16(dst, *reinterpret_cast<unsigned short*>(&h));
-            } else if constexpr (F == 2) {
-                sts32(dst, pack_bf16x2(o[0], o[1]));
-            } else if constexpr (F == 4) {
-                sts64(dst, pack_bf16x2(o[0], o[1]), pack_bf16x2(o[2], o[3]));
-            } else {
-                sts128(dst, pack_bf16x2(o[0], o[1]), pack_bf16x2(o[2], o[3]), pack_bf16x2(o[4], o[5]),
-                       pack_bf16x2(o[6], o[7]));
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<uint32_t*>(&h);
-}
-
-// Columns 32h .. 32h+31 of row r of a 128 x 64 bf16 A tile (128-byte swizzle) from 32 floats.
-__device__ __forceinline__ void write_half_row(uint8_t* tile, int r, int h, const float (&x)[32]) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int c = 4 * h + q;
-        uint4 w = make_uint4(pack_bf16x2(x[8 * q + 0], x[8 * q + 1]), pack_bf16x2(x[8 * q + 2], x[8 * q + 3]),
-                             pack_bf16x2(x[8 * q + 4], x[8 * q + 5]), pack_bf16x2(x[8 * q + 6], x[8 * q + 7]));
-        *reinterpret_cast<uint4*>(tile + tc::sw128_off(r, c)) = w;
-    }
-}
-
-// Row r of a 128 x 64 bf16 A tile (128-byte swizzle) from 64 floats.
-__device__ __forceinline__ void write_row(uint8_t* tile, int r, const float (&x)[64]) {
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        uint4 w = make_uint4(pack_bf16x2(x[8 * c + 0], x[8 * c + 1]), pack_bf16x2(x[8 * c + 2], x[8 * c + 3]),
-                             pack_bf16x2(x[8 * c + 4], x[8 * c + 5]), pack_bf16x2(x[8 * c + 6], x[8 * c + 7]));
-        *reinterpret_cast<uint4*>(tile + tc::sw128_off(r, c)) = w;
-    }
-}
-
-// Shared memory of a CTA with R sample tiles: R A tiles (128 x 64 bf16, 16 KB each), the layer weight
-// tiles (64 x 64 bf16, 8 KB each), biases, output layer, mbarrier and TMEM slot.
+// Shared memory of a CTA with R sample tiles: R A tiles (128 x 64 bf16, 16 KB each), the hidden layer
+// weight tiles (64 x 64 bf16, 8 KB each), the output weight tile (16 x 64 bf16, 2 KB), biases,
+// mbarrier and TMEM slot.
 struct TcSmem {
     __host__ __device__ static int W(int R) { return R * 16384; }
-    __host__ __device__ static int bias(int R, int nh) { return W(R) + nh * 8192; }
-    __host__ __device__ static int wout(int R, int nh) { return bias(R, nh) + nh * 64 * 4; }
-    __host__ __device__ static int bout(int R, int nh) { return wout(R, nh) + 64 * 4; }
+    __host__ __device__ static int wout(int R, int nh) { return W(R) + nh * 8192; }
+    __host__ __device__ static int bias(int R, int nh) { return wout(R, nh) + 2048; }
+    __host__ __device__ static int bout(int R, int nh) { return bias(R, nh) + nh * 64 * 4; }
     __host__ __device__ static int mbar(int R, int nh) { return bout(R, nh) + 16; }
     __host__ __device__ static int slot(int R, int nh) { return mbar(R, nh) + 8; }
     __host__ __device__ static int bytes(int R, int nh) { return slot(R, nh) + 8 + 1024; }  // + alignment slack
@@ -184,7 +36,7 @@ struct TcSmem {
 // R = samples per thread: the CTA holds R tiles of 128 samples (R MMA tiles, R x 64 TMEM columns),
 // so every thread keeps the gathers of R samples in flight.
 template <int F, bool TRAIN, int R>
-__global__ void __launch_bounds__(128) k_forward_tc(const __grid_constant__ Levels lv, const __grid_constant__ MlpShape sh,
+__global__ void __launch_bounds__(128, 3) k_forward_tc(const __grid_constant__ Levels lv, const __grid_constant__ MlpShape sh,
                                                     const __nv_bfloat16* __restrict__ Tb,
                                                     const __nv_bfloat16* __restrict__ Pmb, const float* __restrict__ Pm,
                                                     const float* __restrict__ coords, const float* __restrict__ target,
@@ -200,39 +52,27 @@ __global__ void __launch_bounds__(128) k_forward_tc(const __grid_constant__ Leve
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
     const int nh = sh.nh, Wd = sh.width;
     uint8_t* Wt = sm + TcSmem::W(R);
+    uint8_t* Wo = sm + TcSmem::wout(R, nh);
     float* bias = reinterpret_cast<float*>(sm + TcSmem::bias(R, nh));
-    float* wout = reinterpret_cast<float*>(sm + TcSmem::wout(R, nh));
     float* bout = reinterpret_cast<float*>(sm + TcSmem::bout(R, nh));
     uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + TcSmem::mbar(R, nh));
     uint32_t* slot = reinterpret_cast<uint32_t*>(sm + TcSmem::slot(R, nh));
     const int t = threadIdx.x, warp = t >> 5;
-    constexpr uint32_t kCols = 64 * R;
+    constexpr uint32_t kOut = 64 * R;                               // first output column (16 per tile)
+    constexpr uint32_t kCols = (kOut + 16 * R) <= 128 ? 128 : 256;  // power of two for tcgen05.alloc
 
     if (warp == 0) tc::tmem_alloc(slot, kCols);
     if (t == 0) {
         tc::mbar_init(mbar, 1);
         tc::fence_mbar_init();
     }
-    // weights of the hidden-producing layers as 64 x 64 bf16 tiles (rows = outputs, K = inputs)
+    // hidden-producing layers as 64 x 64 bf16 tiles (rows = outputs, K = inputs); output weights as
+    // row 0 of a 16 x 64 tile
     for (int j = 0; j < nh; ++j) {
-        const int fi = j == 0 ? sh.in : Wd;
-        for (int e = t; e < 64 * 8; e += 128) {
-            const int r = e >> 3, c = e & 7;
-            uint32_t w4[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int k0 = 8 * c + 2 * q;
-                __nv_bfloat16 lo = __float2bfloat16_rn(0.0f), hi = lo;
-                if (r < Wd && k0 < fi) lo = Pmb[sh.w_off[j] + r * fi + k0];
-                if (r < Wd && k0 + 1 < fi) hi = Pmb[sh.w_off[j] + r * fi + k0 + 1];
-                __nv_bfloat162 h2 = __halves2bfloat162(lo, hi);
-                w4[q] = *reinterpret_cast<uint32_t*>(&h2);
-            }
-            *reinterpret_cast<uint4*>(Wt + j * 8192 + tc::sw128_off(r, c)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
-        }
+        load_wtile(Wt + j * 8192, Pmb + sh.w_off[j], Wd, j == 0 ? sh.in : Wd, 64, 64);
         for (int o = t; o < 64; o += 128) bias[j * 64 + o] = (o < Wd) ? Pm[sh.b_off[j] + o] : 0.0f;
     }
-    for (int o = t; o < 64; o += 128) wout[o] = (o < Wd) ? Pm[sh.w_off[nh] + o] : 0.0f;
+    load_wtile(Wo, Pmb + sh.w_off[nh], 1, Wd, 16, 64);
     if (t == 0) bout[0] = Pm[sh.b_off[nh]];
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -240,8 +80,12 @@ __global__ void __launch_bounds__(128) k_forward_tc(const __grid_constant__ Leve
     tc::fence_after_sync();
     const uint32_t tmem = *slot;
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-    constexpr uint32_t idesc = tc::idesc_bf16(128, 64);
-    const uint32_t a_addr = tc::smem_addr(sm), w_addr = tc::smem_addr(Wt);
+    constexpr uint32_t idesc = tc::idesc_bf16(128, 64), idesc_out = tc::idesc_bf16(128, 16);
+    const uint32_t a_addr = tc::smem_addr(sm), w_addr = tc::smem_addr(Wt), wo_addr = tc::smem_addr(Wo);
+    const int nk_in = (sh.in + 15) / 16, nk_w = (Wd + 15) / 16;  // K steps that are not all zero
+#pragma unroll
+    for (int r = 0; r < R; ++r) store_bias64(lane_base + 64 * r, bias);  // layer 0 starts from its bias
+    tc::tmem_st_wait();
 
     uint32_t phase = 0;
     bool bad = false;
@@ -263,48 +107,43 @@ __global__ void __launch_bounds__(128) k_forward_tc(const __grid_constant__ Leve
         tc::fence_before_sync();
         __syncthreads();
         float y[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) y[r] = bout[0];
-        for (int j = 0; j < nh; ++j) {
+        for (int j = 0; j <= nh; ++j) {  // hidden layers onto their bias, then the output layer (j == nh)
             if (t == 0) {
                 tc::fence_after_sync();
+                const int nk = j == 0 ? nk_in : nk_w;
 #pragma unroll
                 for (int r = 0; r < R; ++r)
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        tc::mma_bf16(tmem + 64 * r, tc::sdesc_sw128(a_addr + r * 16384 + kk * 32),
-                                     tc::sdesc_sw128(w_addr + j * 8192 + kk * 32), idesc, kk > 0 ? 1u : 0u);
+                    for (int kk = 0; kk < nk; ++kk) {
+                        if (j < nh)
+                            tc::mma_bf16(tmem + 64 * r, tc::sdesc_sw128(a_addr + r * 16384 + kk * 32),
+                                         tc::sdesc_sw128(w_addr + j * 8192 + kk * 32), idesc, 1u);
+                        else
+                            tc::mma_bf16(tmem + kOut + 16 * r, tc::sdesc_sw128(a_addr + r * 16384 + kk * 32),
+                                         tc::sdesc_sw128(wo_addr + kk * 32), idesc_out, kk > 0 ? 1u : 0u);
+                    }
                 tc::mma_commit(mbar);
             }
             const bool ok = tc::mbar_wait(mbar, phase);
             phase ^= 1;
             if (__syncthreads_or(!ok)) { bad = true; break; }
             tc::fence_after_sync();
-            const bool last = j + 1 == nh;
+            if (j == nh) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) y[r] = tc::tmem_ld1(lane_base + kOut + 16 * r);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int r = 0; r < R; ++r) y[r] += bout[0];
+                break;
+            }
+            const float* next_bias = bias + (j + 1 < nh ? (j + 1) * 64 : 0);  // the next tile starts at layer 0
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {  // 32 accumulator columns at a time
-                    float v[32];
-                    tc::tmem_ld32(lane_base + 64 * r + 32 * h, v);
-                    tc::tmem_ld_wait();
-#pragma unroll
-                    for (int q = 0; q < 32; ++q) v[q] = fmaxf(v[q] + bias[j * 64 + 32 * h + q], 0.0f);
-                    if (TRAIN && valid[r]) {
-                        float* a = acts + (int64_t)(sh.in + j * Wd) * n + idx[r];
-#pragma unroll
-                        for (int q = 0; q < 32; ++q)
-                            if (32 * h + q < Wd) a[(int64_t)(32 * h + q) * n] = v[q];
-                    }
-                    if (!last) {
-                        write_half_row(sm + r * 16384, t, h, v);
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 32; ++q) y[r] = fmaf(wout[32 * h + q], v[q], y[r]);  // scalar output layer
-                    }
-                }
+                float* a = (TRAIN && valid[r]) ? acts + (int64_t)(sh.in + j * Wd) * n + idx[r] : nullptr;
+                hidden_epilogue(lane_base + 64 * r, sm + r * 16384, t, a, n, Wd);
+                store_bias64(lane_base + 64 * r, next_bias);
             }
-            if (!last) tc::fence_async_smem();
+            tc::tmem_st_wait();
+            tc::fence_async_smem();
             tc::fence_before_sync();
             __syncthreads();
         }

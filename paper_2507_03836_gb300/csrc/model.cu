@@ -244,7 +244,7 @@ static void destroy_model(fhash_model* m) {
     cudaDeviceSynchronize();
     void* ps[] = {m->param, m->grad, m->adam_m, m->adam_v, m->shadow, m->occ, m->occ_any, m->err_word,
                   m->s_coords.p, m->s_target.p, m->s_out.p, m->s_acts.p, m->s_gacts.p, m->s_partial.p,
-                  m->s_loss.p, m->s_misc.p, m->s_render.p};
+                  m->s_loss.p, m->s_misc.p, m->s_render.p, m->s_enc.p};
     for (void* p : ps)
         if (p) cudaFree(p);
     delete m;

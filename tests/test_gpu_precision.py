@@ -65,6 +65,40 @@ def test_bf16_ragged_tiles_and_positions(mask):
         assert torch().equal(a, b[77:])  # each row of the MMA depends on its own sample only
 
 
+@pytest.mark.parametrize("F,hidden,width,levels", [(2, 2, 64, 4), (8, 2, 64, 4), (4, 3, 32, 9), (1, 1, 16, 4)])
+def test_bf16_split_path(mask, F, hidden, width, levels):
+    """The split evaluation (bf16 encoding rows, then the TMA-fed tensor-core MLP) against the oracle's
+    bf16 emulation, and bit-identical to the fused kernel, over 5000 points and over two chunks
+    (2^20 + 333 points).  Encoding widths L*F = 8, 32, 36, 4: 64-byte boxes, and 128-byte boxes for 36."""
+    f, m = mask
+    sched = (W1["schedule"] if levels == 4 else
+             dict(mode="geometric", n_levels=levels, r0=[2, 2, 2, 1], r1=[32, 32, 32, 8]))
+    w = dict(W1, F=F, hidden=hidden, width=width, schedule=sched)
+    model = build(w, mask=m, dtype=fh().BF16, seed=9)
+    info = fh().fhash_get_info(model)
+    table = synth.uniform(33, 50, info["n_table_params"], -0.7, 0.7)
+    p = synth.init_mlp(33, info["mlp_dims"])
+    set_params(model, table, p)
+    with pytest.raises(fh().FHashError):
+        fh().fhash_set_forward_path(model, 7)
+    for n in (5000, (1 << 20) + 333):
+        c = synth.coords(78 + n % 7, n)
+        c[:4] = [[0, 0, 0, 0], [1, 1, 1, 1], [0.3, 0.9, 0.1, 0.5], [np.nan, 2.0, -1.0, 0.25]]
+        dc = to_dev(c)
+        outs = {}
+        for name, path in (("fused", fh().FORWARD_FUSED), ("split", fh().FORWARD_SPLIT)):
+            fh().fhash_set_forward_path(model, path)
+            o = torch().empty(n, dtype=torch().float32, device="cuda")
+            fh().fhash_forward(model, dc, o)
+            outs[name] = o.cpu().numpy()
+        assert np.array_equal(outs["fused"], outs["split"]), n
+        k = 5000
+        ref = precision.forward_bf16(info["res"], info["base"], table.reshape(-1, info["F"]), p.astype(np.float64),
+                                     info["mlp_dims"], c[-k:])
+        _check(outs["split"][-k:], ref)
+    fh().fhash_check(model)
+
+
 def _psnr(pred, truth):
     rng = truth.max() - truth.min()
     return 10 * np.log10(rng ** 2 / np.mean((pred - truth) ** 2))
