@@ -27,9 +27,14 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "train samples/s (enc+MLP fwd+bwd); render p50/p99 ms; BF16 vs FP32 @PSNR"
-# DRAM bytes per parameter of k_adam from an ncu capture of the current kernel (None: not yet taken
-# since the kernel last changed, and the bench then reports no traffic).
-ADAM_DRAM_BYTES_PER_PARAM = None
+# DRAM traffic of k_adam from one ncu capture of the current kernel on advect-128^3x32
+# (profiles/ncu_k_adam_advect-128^3x32.md): 4.106 GB read + 3.323 GB written for 256,431,321
+# parameters, 28.97 B/param, when 21% of the 4-parameter gradient groups were non-zero (algorithmic
+# 28 + 4 x 0.21 = 28.84 B/param).  The written part depends on that fraction, so the capture does not
+# scale to the full launch in proportion; the bench reports it as a small-case ratio instead.
+ADAM_SMALL_CASE = {"workload": "advect-128^3x32", "bytes_per_param_measured": (4.106175e9 + 3.323173e9) / 256431321,
+                   "bytes_per_param_algorithmic": 28.84, "grad_groups_touched": 0.2097}
+ADAM_SMALL_CASE["ratio"] = ADAM_SMALL_CASE["bytes_per_param_measured"] / ADAM_SMALL_CASE["bytes_per_param_algorithmic"]
 
 
 def _touched_fraction(fh, model, info, coords, tgt, hp, chunk=1 << 28):
@@ -592,8 +597,10 @@ def main():
         "gpu_launches": K * (4 + 2 * (w["hidden"] + 1)),
         "roofline": {"kernel": "k_adam", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                     "traffic": ADAM_DRAM_BYTES_PER_PARAM * n_params if ADAM_DRAM_BYTES_PER_PARAM and args.dtype == "f32" else None,
-                     "traffic_note": "ncu dram__bytes_read+write of k_adam on advect-128^3x32, scaled by parameters",
+                     "traffic": None,
+                     "traffic_note": "the full launch exceeds the ncu capture size rule; the small-case capture of "
+                                     "the same kernel gives measured / algorithmic bytes in traffic_small_case",
+                     "traffic_small_case": ADAM_SMALL_CASE if args.dtype == "f32" else None,
                      "peak_source": peak_kind, "bytes_per_launch": adam_bytes, "bytes_per_param": adam_bpp,
                      "grad_groups_touched": touched},
         "clocks": clk,

@@ -247,49 +247,71 @@ __global__ void __launch_bounds__(128) k_mlp_bwd_g(const __grid_constant__ MlpSh
     }
 }
 
-// Weight gradient partials of one layer over a chunk of samples: thread (ob, ib) owns the 4 x 4 tile
-// dW[4ob..4ob+3][4ib..4ib+3] (and db of its rows when ib == 0).  partial[chunk][e] as k_dw_partial.
-__global__ void __launch_bounds__(256) k_dw_tiles(const float* __restrict__ a, const float* __restrict__ d, int fi, int fo,
-                                                  int64_t n, int64_t chunk, float* __restrict__ partial) {
-    constexpr int TS = 32;
-    __shared__ float sa[64][TS + 1];
-    __shared__ float sd[64][TS + 1];
+// Weight-gradient partials of every layer over chunks of samples (blockIdx.y = layer).  Thread (ob, ib)
+// owns dW[4ob..4ob+3][4ib..4ib+3] and, when ib == 0, db of its rows.  Slabs of 32 samples are staged in
+// shared memory sample-major (sd[c][o], sa[c][i]), double-buffered through registers, so each thread
+// reads one float4 of deltas and one float4 of activations per sample: 16 FMAs per 2 shared loads.
+// partial[(chunk * layers + layer) * kDwStride + e]: e < fo*fi the weights, fo*fi + o the biases.
+constexpr int kDwStride = 64 * 64 + 64;
+struct DwLayers {
+    const float* a[FHASH_MAX_HIDDEN + 1];
+    const float* d[FHASH_MAX_HIDDEN + 1];
+    int32_t fi[FHASH_MAX_HIDDEN + 1], fo[FHASH_MAX_HIDDEN + 1];
+};
+
+__global__ void __launch_bounds__(256) k_dw_tiles(const __grid_constant__ DwLayers Ls, int64_t n, int64_t chunk,
+                                                  float* __restrict__ partial) {
+    constexpr int TS = 32, LD = 68, KS = 16;  // KS = staged values per thread: 128 rows x 32 samples / 256
+    __shared__ __align__(16) float sa[TS][LD];
+    __shared__ __align__(16) float sd[TS][LD];
+    const int layer = blockIdx.y;
+    const float* __restrict__ a = Ls.a[layer];
+    const float* __restrict__ d = Ls.d[layer];
+    const int fi = Ls.fi[layer], fo = Ls.fo[layer], rows = fi + fo;
     const int nig = (fi + 3) / 4, nob = (fo + 3) / 4;
     const int ob = threadIdx.x / nig, ib = threadIdx.x % nig;
-    const bool active = threadIdx.x < nob * nig;
+    const bool active = (int)threadIdx.x < nob * nig;
     const int64_t n0 = blockIdx.x * chunk, n1 = min(n, n0 + chunk);
-    float acc[4][4] = {}, bacc[4] = {};
-    for (int64_t t0 = n0; t0 < n1; t0 += TS) {
-        __syncthreads();
-        for (int q = threadIdx.x; q < (fi + fo) * TS; q += blockDim.x) {
-            const int r = q / TS, c = q % TS;
+    float stage[KS];
+    auto fetch = [&](int64_t t0) {
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+            const int q = threadIdx.x + 256 * k, r = q / TS, c = q % TS;
             const int64_t smp = t0 + c;
             float v = 0.0f;
-            if (smp < n1) v = (r < fi) ? a[(int64_t)r * n + smp] : d[(int64_t)(r - fi) * n + smp];
-            if (r < fi) sa[r][c] = v; else sd[r - fi][c] = v;
+            if (r < rows && smp < n1) v = r < fi ? a[(int64_t)r * n + smp] : d[(int64_t)(r - fi) * n + smp];
+            stage[k] = v;
+        }
+    };
+    float acc[4][4] = {}, bacc[4] = {};
+    if (n0 < n1) fetch(n0);
+    for (int64_t t0 = n0; t0 < n1; t0 += TS) {
+        __syncthreads();  // the previous slab has been read
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+            const int q = threadIdx.x + 256 * k, r = q / TS, c = q % TS;
+            if (r < fi) sa[c][r] = stage[k];
+            else if (r < rows) sd[c][r - fi] = stage[k];
         }
         __syncthreads();
+        if (t0 + TS < n1) fetch(t0 + TS);  // the next slab's loads stay in flight during the FMAs
         if (active) {
-#pragma unroll 4
+#pragma unroll 8
             for (int c = 0; c < TS; ++c) {
-                float dv[4], av[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    dv[u] = (4 * ob + u < fo) ? sd[4 * ob + u][c] : 0.0f;
-                    av[u] = (4 * ib + u < fi) ? sa[4 * ib + u][c] : 0.0f;
-                }
+                const float4 dv = *reinterpret_cast<const float4*>(&sd[c][4 * ob]);
+                const float4 av = *reinterpret_cast<const float4*>(&sa[c][4 * ib]);
+                const float dd[4] = {dv.x, dv.y, dv.z, dv.w}, aa[4] = {av.x, av.y, av.z, av.w};
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(dv[u], av[v], acc[u][v]);
-                    bacc[u] += dv[u];
+                    for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(dd[u], aa[v], acc[u][v]);
+                    bacc[u] += dd[u];
                 }
             }
         }
     }
     if (!active) return;
-    const int ne = fo * fi + fo;
-    float* out = partial + (int64_t)blockIdx.x * ne;
+    float* out = partial + ((int64_t)blockIdx.x * gridDim.y + layer) * kDwStride;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int o = 4 * ob + u;
@@ -303,12 +325,14 @@ __global__ void __launch_bounds__(256) k_dw_tiles(const float* __restrict__ a, c
     }
 }
 
-__global__ void k_dw_reduce2(const float* __restrict__ partial, int nchunk, int ne, float* __restrict__ grad) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= ne) return;
+// grad[off[layer] + e] += sum over chunks of the partials (weights then biases, contiguous per layer).
+__global__ void k_dw_reduce2(const float* __restrict__ partial, int nchunk, const __grid_constant__ DwLayers Ls,
+                             const __grid_constant__ MlpShape sh, float* __restrict__ gm) {
+    const int layer = blockIdx.y, e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= Ls.fo[layer] * Ls.fi[layer] + Ls.fo[layer]) return;
     float s = 0.0f;
-    for (int c = 0; c < nchunk; ++c) s += partial[(int64_t)c * ne + e];
-    grad[e] += s;
+    for (int c = 0; c < nchunk; ++c) s += partial[((int64_t)c * gridDim.y + layer) * kDwStride + e];
+    gm[sh.w_off[layer] + e] += s;
 }
 
 __global__ void k_loss2(const double* __restrict__ partial, int nb, int64_t n, double* __restrict__ loss) {
@@ -331,30 +355,39 @@ bool launch_dw_tc(fhash_model* m, const float* acts, const float* dl, int64_t n,
 template <int F>
 static cudaError_t scatter_launch(fhash_model* m, const float* coords, int64_t n, const float* denc, int64_t dsf,
                                   int64_t dss, cudaStream_t st) {
-    constexpr int64_t kPrivMax = 16384;  // floats of a level accumulated in shared memory (64 KB)
-    ScatterPlan P{};
-    int blocks = 0;
+    constexpr int64_t kPrivMax = 32768;  // floats of a level accumulated in shared memory (128 KB)
+    // Two launches: the privatised coarse levels (shared memory sized for the largest of them) and the
+    // fine levels (no shared memory, so their blocks run at full occupancy).
+    ScatterPlan Pp{}, Pf{};
+    int bp = 0, bf = 0;
     int64_t priv_floats = 0;
     for (int l = 0; l < m->lv.L; ++l) {
         const Level& L = m->lv.lv[l];
         const int64_t fl = (int64_t)L.st * L.R[3] * F;
-        P.first[l] = blocks;
+        Pp.first[l] = bp;
+        Pf.first[l] = bf;
         if (fl <= kPrivMax) {
-            P.priv[l] = 1;
-            P.per[l] = std::max<int64_t>(2048, (n + 63) / 64);  // at most 64 flushes of the level
+            Pp.priv[l] = 1;
+            Pp.per[l] = std::max<int64_t>(2048, (n + 63) / 64);  // at most 64 flushes of the level
             priv_floats = std::max(priv_floats, fl);
+            bp += (int)((n + Pp.per[l] - 1) / Pp.per[l]);
         } else {
-            P.priv[l] = 0;
-            P.per[l] = 256;
+            Pf.priv[l] = 0;
+            Pf.per[l] = 256;
+            bf += (int)((n + 255) / 256);
         }
-        blocks += (int)((n + P.per[l] - 1) / P.per[l]);
     }
-    P.first[m->lv.L] = blocks;
-    const int smem = (int)(priv_floats * 4);
-    cudaError_t e = cudaFuncSetAttribute((const void*)k_scatter_cols<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         std::max(smem, 1));
-    if (e != cudaSuccess) return e;
-    k_scatter_cols<F><<<blocks, 256, smem, st>>>(m->lv, P, m->grad, coords, n, denc, dsf, dss);
+    Pp.first[m->lv.L] = bp;
+    Pf.first[m->lv.L] = bf;
+    if (bp > 0) {
+        const int smem = (int)(priv_floats * 4);
+        cudaError_t e = cudaFuncSetAttribute((const void*)k_scatter_cols<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             std::max(smem, 1));
+        if (e != cudaSuccess) return e;
+        k_scatter_cols<F><<<bp, 256, smem, st>>>(m->lv, Pp, m->grad, coords, n, denc, dsf, dss);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (bf > 0) k_scatter_cols<F><<<bf, 256, 0, st>>>(m->lv, Pf, m->grad, coords, n, denc, dsf, dss);
     return cudaGetLastError();
 }
 
@@ -380,15 +413,12 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
     FH_TRY(grow(m, m->s_acts, (size_t)(A * n * 4)));
     FH_TRY(grow(m, m->s_gacts, (size_t)((D + 1 + sh.in) * n * 4)));
     int nb = (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, (int64_t)num_sms() * 8));  // loss partials
-    const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, (int64_t)num_sms() * 2));
+    const int nl = sh.nh + 1;
+    // weight-gradient chunks: about 4 blocks per SM over all layers, at least 512 samples each
+    const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>((n + 511) / 512, (int64_t)num_sms() * 4 / nl));
     const int64_t chunk = ((n + nchunk - 1) / nchunk + 31) / 32 * 32;
-    int ne_max = 0;
-    for (int j = 0; j <= sh.nh; ++j) {
-        const int fi = j == 0 ? sh.in : W, fo = j == sh.nh ? 1 : W;
-        ne_max = std::max(ne_max, fo * fi + fo);
-    }
-    const size_t tc_part = m->shadow ? ((size_t)num_sms() * (sh.nh + 1) * 4096 + 64 * 64) * 4 : 0;
-    FH_TRY(grow(m, m->s_partial, std::max((size_t)nchunk * ne_max * 4, tc_part) + (size_t)nb * 8 + 64));
+    const size_t tc_part = m->shadow ? ((size_t)num_sms() * nl * 4096 + 64 * 64) * 4 : 0;
+    FH_TRY(grow(m, m->s_partial, std::max((size_t)nchunk * nl * kDwStride * 4, tc_part) + (size_t)nb * 8 + 64));
     float* acts = (float*)m->s_acts.p;
     float* gy = (float*)m->s_gacts.p;
     float* dl = gy + n;
@@ -442,15 +472,16 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
             return FHASH_OK;
         }
     }
-    float* gm = m->grad + m->n_table;
-    for (int j = 0; j <= sh.nh; ++j) {
-        const int fi = j == 0 ? sh.in : W, fo = j == sh.nh ? 1 : W;
-        const float* aj = (j == 0) ? acts : acts + (int64_t)(sh.in + (j - 1) * W) * n;
-        const float* dj = dl + (int64_t)j * W * n;
-        k_dw_tiles<<<nchunk, 256, 0, st>>>(aj, dj, fi, fo, n, chunk, wpart);
-        const int ne = fo * fi + fo;
-        k_dw_reduce2<<<(ne + 255) / 256, 256, 0, st>>>(wpart, nchunk, ne, gm + sh.w_off[j]);
+    DwLayers Ls{};
+    for (int j = 0; j < nl; ++j) {
+        Ls.fi[j] = j == 0 ? sh.in : W;
+        Ls.fo[j] = j == sh.nh ? 1 : W;
+        Ls.a[j] = (j == 0) ? acts : acts + (int64_t)(sh.in + (j - 1) * W) * n;
+        Ls.d[j] = dl + (int64_t)j * W * n;
     }
+    k_dw_tiles<<<dim3(nchunk, nl), 256, 0, st>>>(Ls, n, chunk, wpart);
+    FH_CUDA(cudaGetLastError());
+    k_dw_reduce2<<<dim3((kDwStride + 255) / 256, nl), 256, 0, st>>>(wpart, nchunk, Ls, sh, m->grad + m->n_table);
     FH_CUDA(cudaGetLastError());
     return FHASH_OK;
 }
