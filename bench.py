@@ -335,6 +335,67 @@ def suite_precision(args):
     print(json.dumps(res))
 
 
+def suite_coreset(args):
+    """Coreset training (Section 3.1) on advect-256^3x64: the union of the dilated feature at 10 key frames,
+    the paper's batch of 2^21, epochs shuffled by the library.  Reports the coreset size and build time,
+    samples/s of coreset training steps, and PSNR of the coreset-trained model and of a model trained
+    for the same steps on uniform samples, on 1M held-out coreset samples (the feature region at the key
+    frames) and on 1M uniform points."""
+    import torch
+    import paper_2507_03836_gb300 as fh
+    from synth import workloads
+    w = dict(workloads.LARGE, batch=1 << 21)
+    keys = [int(round(k * (w["dims"][3] - 1) / 9)) for k in range(10)]
+    t0 = time.time()
+    field, mask = workloads.make_field_and_mask(w)
+    setup_s = time.time() - t0
+    hp = w["adam"]
+    B, K, W0 = w["batch"], args.steps, 3
+    res = {"suite": "coreset", "workload": w["name"], "key_frames": keys, "batch": B, "steps": K}
+    model, info = _build(w, fh.FP32, 5, mask)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    N = fh.fhash_coreset_build(model, field, keys)
+    res["coreset_samples"] = N
+    res["coreset_build_s"] = time.time() - t1
+    per_epoch = (N + B - 1) // B
+    res["batches_per_epoch"] = per_epoch
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for i in range(K + W0):
+        if i == W0:
+            torch.cuda.synchronize()
+            e0.record(st)
+        fh.fhash_coreset_train_step(model, 1, i // per_epoch, i % per_epoch, B, hp)
+    e1.record(st)
+    torch.cuda.synchronize()
+    fh.fhash_check(model)
+    ms = e0.elapsed_time(e1) / K
+    res["coreset_train"] = {"ms_per_step": ms, "samples_s": B / ms * 1e3}
+    # held-out evaluation sets: coreset samples of another shuffle, and uniform points
+    hc = torch.empty((1 << 20, 4), dtype=torch.float32, device="cuda")
+    ht = torch.empty(1 << 20, dtype=torch.float32, device="cuda")
+    n_h = fh.fhash_coreset_batch(model, 4242, 0, 0, 1 << 20, hc, ht)
+    hc, ht = hc[:n_h], ht[:n_h].cpu().numpy().astype(np.float64)
+
+    def feature_psnr(m):
+        o = torch.empty(n_h, dtype=torch.float32, device="cuda")
+        fh.fhash_forward(m, hc, o)
+        pred = o.cpu().numpy().astype(np.float64)
+        rng = ht.max() - ht.min()
+        return float(10 * np.log10(rng ** 2 / np.mean((pred - ht) ** 2)))
+
+    res["coreset_train"]["psnr_feature_db"] = feature_psnr(model)
+    res["coreset_train"]["psnr_uniform_db"] = _psnr(model, info, field)[0]
+    del model
+    uni, info = _build(w, fh.FP32, 5, mask)
+    ms = _train(uni, _batches(w, info, field, K + W0, 60_000), hp, warmup=W0)
+    res["uniform_train"] = {"ms_per_step": ms, "samples_s": B / ms * 1e3, "psnr_feature_db": feature_psnr(uni),
+                            "psnr_uniform_db": _psnr(uni, info, field)[0]}
+    res["setup_s"] = setup_s
+    print(json.dumps(res))
+
+
 def _serve(models, kinds, n_req, rate, budget, tf, seed=1234, decode_every=0):
     """Poisson stream through one server; kinds[i] = model index of request i; every `decode_every`-th
     request (0: none) is a time-slice decode (upsample 1 or 2), the rest renders of 256^2/512^2/1024^2."""
@@ -465,7 +526,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving and precision legs")
     ap.add_argument("--serve-requests", type=int, default=60)
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, requests/s")
-    ap.add_argument("--suite", default="train", choices=["train", "precision", "serve", "mixed"],
+    ap.add_argument("--suite", default="train", choices=["train", "precision", "serve", "mixed", "coreset"],
                     help="train: the default line; precision / serve / mixed: the other workloads")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -473,7 +534,8 @@ def main():
     if args.suite != "train":
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        return {"precision": suite_precision, "serve": suite_serve, "mixed": suite_mixed}[args.suite](args)
+        return {"precision": suite_precision, "serve": suite_serve, "mixed": suite_mixed,
+                "coreset": suite_coreset}[args.suite](args)
 
     import torch
     import synth
@@ -594,7 +656,10 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (%.1f GB of training state streamed per step)" % (adam_bytes / 1e9)},
         "phases_ms": {"encode_mlp_fwd_bwd_scatter": grads_ms, "adam": adam_ms},
-        "gpu_launches": K * (4 + 2 * (w["hidden"] + 1)),
+        # per step, float32: encode, MLP forward, loss, MLP backward, 2 scatters, weight gradients and
+        # their reduction, Adam; precision form: fused forward, loss, MLP backward, 2 scatters, the
+        # tensor-core weight gradients, 3 reductions per layer, Adam
+        "gpu_launches": K * (9 if args.dtype == "f32" else 7 + 3 * (w["hidden"] + 1)),
         "roofline": {"kernel": "k_adam", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                      "traffic": None,

@@ -214,6 +214,38 @@ fhash_status fhash_apply_adam(fhash_model* model, const fhash_adam* adam, fhash_
 fhash_status fhash_train_step(fhash_model* model, const float* coords, const float* target, int64_t n,
                               const fhash_adam* adam, double* loss, fhash_stream stream);
 
+/*
+ * Feature-based coreset (Section 3.1).  The training samples are the vertices of the dilated feature
+ * d_k at each key frame t_k (the occupancy the model built from the mask in fhash_build), each
+ * labelled with the volume value there; the coreset is their union over the key frames.  The samples
+ * stay on the device (12 bytes each) in key-frame order, then (z, y, x) order inside the Feature
+ * Bounding Box, and replace any previous coreset of the model.
+ *  volume: host or device float32 [nt][nz][ny][nx] (the build dimensions), read during the call only;
+ *  key_frames: host int32 [n_key], strictly increasing time steps in [0, nt).
+ *  count (host, may be NULL) receives the number of samples N.  Dimensions above 65535 are
+ *  FHASH_EINVAL.  The call synchronises the stream.
+ */
+fhash_status fhash_coreset_build(fhash_model* model, const float* volume, const int32_t* key_frames, int32_t n_key,
+                                 int64_t* count, fhash_stream stream);
+
+/*
+ * Batch `batch` of epoch `epoch` over the coreset.  Epoch e visits every sample once, in the order of a
+ * keyed permutation pi_e of [0, N): a balanced 4-round Feistel network on k-bit integers
+ * (k = max(2, ceil(log2 N)) rounded up to even; round function SplitMix64's output function of the
+ * right half XOR round key r, keys r = 0..3 = SplitMix64 outputs 0..3 seeded with value `epoch` of
+ * stream 400 of `seed`), applied again while the result is >= N.  The batch holds the samples at
+ * positions batch*B .. batch*B + B - 1 of pi_e (fewer in the last batch; ceil(N / B) batches per
+ * epoch).  Writes their FBB-normalised coordinates u = ((x - lo) / (S - 1), ..., t / (nt - 1)) in
+ * float32 to coords (device [n][4]) and labels to target (device [n]), and n to *n_out (host, may be
+ * NULL).  No coreset, B <= 0 or a batch past the end is FHASH_EINVAL.
+ */
+fhash_status fhash_coreset_batch(fhash_model* model, uint64_t seed, int64_t epoch, int64_t batch, int64_t batch_size,
+                                 float* coords, float* target, int64_t* n_out, fhash_stream stream);
+
+/* fhash_train_step on batch `batch` of epoch `epoch` of the coreset (as fhash_coreset_batch). */
+fhash_status fhash_coreset_train_step(fhash_model* model, uint64_t seed, int64_t epoch, int64_t batch,
+                                      int64_t batch_size, const fhash_adam* adam, double* loss, fhash_stream stream);
+
 enum { FHASH_STATE_PARAM = 0, FHASH_STATE_GRAD = 1, FHASH_STATE_ADAM_M = 2, FHASH_STATE_ADAM_V = 3 };
 
 /* Copy n float32 elements starting at flat element `offset` of a state vector ([table | MLP]

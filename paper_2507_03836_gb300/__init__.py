@@ -90,6 +90,9 @@ _SIGS = {
     "fhash_encode_backward": [_vp, _vp, _vp, _i64, _vp],
     "fhash_forward": [_vp, _vp, _i64, _vp, _vp],
     "fhash_set_forward_path": [_vp, _i32],
+    "fhash_coreset_build": [_vp, _vp, _vp, _i32, ctypes.POINTER(ctypes.c_int64), _vp],
+    "fhash_coreset_batch": [_vp, _u64, _i64, _i64, _i64, _vp, _vp, ctypes.POINTER(ctypes.c_int64), _vp],
+    "fhash_coreset_train_step": [_vp, _u64, _i64, _i64, _i64, ctypes.POINTER(fhash_adam), _vp, _vp],
     "fhash_compute_grads": [_vp, _vp, _vp, _i64, _vp, _vp],
     "fhash_apply_adam": [_vp, ctypes.POINTER(fhash_adam), _vp],
     "fhash_train_step": [_vp, _vp, _vp, _i64, ctypes.POINTER(fhash_adam), _vp, _vp],
@@ -259,6 +262,29 @@ def fhash_train_step(model, coords, target, adam=None, loss=None, stream=None):
     a = _adam(adam)
     _ok(_lib.fhash_train_step(model.handle, _ptr(coords), _ptr(target), coords.shape[0], ctypes.byref(a),
                               _ptr(loss), _stream(stream)))
+
+
+def fhash_coreset_build(model, volume, key_frames, stream=None):
+    """Returns the number of coreset samples."""
+    keys = np.ascontiguousarray(key_frames, np.int32)
+    n = ctypes.c_int64(0)
+    _ok(_lib.fhash_coreset_build(model.handle, _ptr(volume), keys.ctypes.data, keys.size, ctypes.byref(n),
+                                 _stream(stream)))
+    return int(n.value)
+
+
+def fhash_coreset_batch(model, seed, epoch, batch, batch_size, coords, target, stream=None):
+    """Returns the number of samples written."""
+    n = ctypes.c_int64(0)
+    _ok(_lib.fhash_coreset_batch(model.handle, seed, epoch, batch, batch_size, _ptr(coords), _ptr(target),
+                                 ctypes.byref(n), _stream(stream)))
+    return int(n.value)
+
+
+def fhash_coreset_train_step(model, seed, epoch, batch, batch_size, adam=None, loss=None, stream=None):
+    a = _adam(adam)
+    _ok(_lib.fhash_coreset_train_step(model.handle, seed, epoch, batch, batch_size, ctypes.byref(a), _ptr(loss),
+                                      _stream(stream)))
 
 
 def fhash_read_state(model, which, offset, buf, stream=None):

@@ -80,11 +80,23 @@ struct fhash_model {
 
     // scratch (grown on demand; owned by the model)
     fh::Scratch s_coords, s_target, s_out, s_acts, s_gacts, s_partial, s_loss, s_misc, s_render, s_enc;
+    fh::Scratch s_cs_ent, s_cs_val;  // coreset samples: packed (x, y, z, t) and labels
+    int64_t cs_n = 0;
     uint64_t device_bytes = 0;
     int32_t forward_path = 0;  // FHASH_FORWARD_* (precision form only)
 };
 
 namespace fh {
+
+// SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): output i of the generator seeded with s is
+// mix(s + (i + 1) * gamma).
+#define FH_GAMMA 0x9E3779B97F4A7C15ULL
+__host__ __device__ __forceinline__ uint64_t sm_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t sm_at(uint64_t seed, uint64_t i) { return sm_mix(seed + (i + 1) * FH_GAMMA); }
 
 fhash_status grow(fhash_model* m, Scratch& s, size_t bytes);
 bool is_device_ptr(const void* p);

@@ -7,13 +7,13 @@
 //   k_mlp_tc            the MLP on the tensor cores, fed by TMA.  128-row boxes of the encoding buffer
 //                       (64-byte swizzle for E = 32, 128-byte for E = 64) arrive in an S-stage mbarrier
 //                       ring.  Per tile, the layer-0 MMAs read the box, each hidden epilogue writes a bf16
-//                       tile H, and an N = 16 MMA gives the output.  The per-layer arithmetic is the fused
-//                       kernel's (bias stored into TMEM first, MMAs over the same K steps, ReLU, bf16
-//                       rounding, output bias added in float32), so the two paths give bit-identical
-//                       outputs.
+//                       tile H, and an N = 16 MMA gives the output; warp roles below.  The per-layer
+//                       arithmetic is the fused kernel's (bias stored into TMEM first, MMAs over the same
+//                       K steps, ReLU, bf16 rounding, output bias added in float32), so the two paths give
+//                       bit-identical outputs.
 // One chunk of at most 2^20 samples (64 MB of bf16 encoding at E = 32) stays in L2 between the two
 // kernels.  Every mbarrier wait is bounded (2 s); on a timeout the kernel reports through the model's
-// error word, waits once more for its MMAs and its copies in flight, frees its TMEM and returns.
+// error word, waits (bounded) for its MMAs and its copies in flight, frees its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -52,28 +52,43 @@ __global__ void __launch_bounds__(256) k_encode_rows_bf16(const __grid_constant_
         for (int c = lv.L * F; c < E; ++c) row[c] = __float2bfloat16_rn(0.0f);
 }
 
-// Shared memory of k_mlp_tc: the box ring, H, the layer-0 weight tile (64 x E), the other hidden
-// weight tiles (64 x 64), the output tile (16 x 64), biases, mbarriers and the TMEM slot.
+// k_mlp_tc is warp-specialised: warps 0-3 run the epilogues (warp w owns TMEM lanes 32w..32w+31, the
+// rule for tcgen05.ld/st), warp 4 allocates TMEM and its lane 0 issues every MMA, warp 5's lane 0 issues
+// the TMA copies.  Two tiles are in flight per CTA in two TMEM slots of 128 columns (64 hidden
+// accumulator columns, 16 output columns) with one bf16 tile H each, so one tile's MMAs run while the
+// other tile's epilogue reads TMEM and writes H.  Tiles are taken in pairs, and both the MMA issuer
+// and the epilogue warps walk each pair layer by layer, slot 0 then slot 1.  mbarriers:
+//   a_full[s]    the box in stage s has landed (TMA transaction count)
+//   a_empty[s]   the layer-0 MMAs reading stage s are done (tcgen05.commit), so it can be refilled
+//   acc_full[i]  the MMAs of slot i's current layer are done (tcgen05.commit)
+//   h_full[i]    the four epilogue warps wrote H[i] and the next layer's bias into slot i's TMEM
+//   acc_empty[i] the four epilogue warps read slot i's output column, so the slot takes a new tile
+// Every wait is bounded and also gives up once any role has given up (a shared abort flag).
+constexpr int kWsEpiWarps = 4, kWsMmaWarp = 4, kWsTmaWarp = 5, kWsThreads = 192;
+
 template <int E>
 struct SplitSmem {
-    static constexpr int S = E == 32 ? 4 : 2;  // ring stages
+    static constexpr int S = E == 32 ? 6 : 3;  // ring stages
     static constexpr int kBox = 128 * E * 2;   // bytes of one box: 128 rows x E bf16
+    static constexpr int kBars = 2 * S + 7;    // a_full, a_empty, acc_full[2], h_full[2], acc_empty[2], fin
     __host__ __device__ static int H() { return S * kBox; }
-    __host__ __device__ static int W0() { return H() + 16384; }
+    __host__ __device__ static int W0() { return H() + 2 * 16384; }
     __host__ __device__ static int Wh() { return W0() + 64 * E * 2; }
     __host__ __device__ static int Wo(int nh) { return Wh() + (nh - 1) * 8192; }
     __host__ __device__ static int bias(int nh) { return Wo(nh) + 2048; }
     __host__ __device__ static int bout(int nh) { return bias(nh) + nh * 64 * 4; }
     __host__ __device__ static int bars(int nh) { return bout(nh) + 16; }
-    __host__ __device__ static int slot(int nh) { return bars(nh) + (S + 1) * 8; }
+    __host__ __device__ static int flag(int nh) { return bars(nh) + kBars * 8; }
+    __host__ __device__ static int slot(int nh) { return flag(nh) + 8; }
     __host__ __device__ static int bytes(int nh) { return slot(nh) + 8 + 1024; }  // + alignment slack
 };
 
 template <int E>
-__global__ void __launch_bounds__(128, 1) k_mlp_tc(const __grid_constant__ CUtensorMap map,
-                                                   const __grid_constant__ MlpShape sh,
-                                                   const __nv_bfloat16* __restrict__ Pmb, const float* __restrict__ Pm,
-                                                   int64_t n, float* __restrict__ out, int* __restrict__ err) {
+__global__ void __launch_bounds__(kWsThreads, 1) k_mlp_tc(const __grid_constant__ CUtensorMap map,
+                                                          const __grid_constant__ MlpShape sh,
+                                                          const __nv_bfloat16* __restrict__ Pmb,
+                                                          const float* __restrict__ Pm, int64_t n,
+                                                          float* __restrict__ out, int* __restrict__ err) {
     using C = SplitSmem<E>;
     constexpr int S = C::S;
     extern __shared__ uint8_t smraw[];
@@ -85,106 +100,152 @@ __global__ void __launch_bounds__(128, 1) k_mlp_tc(const __grid_constant__ CUten
     uint8_t* Wo = sm + C::Wo(nh);
     float* bias = reinterpret_cast<float*>(sm + C::bias(nh));
     float* bout = reinterpret_cast<float*>(sm + C::bout(nh));
-    uint64_t* full = reinterpret_cast<uint64_t*>(sm + C::bars(nh));
-    uint64_t* mbar = full + S;
+    uint64_t* a_full = reinterpret_cast<uint64_t*>(sm + C::bars(nh));
+    uint64_t* a_empty = a_full + S;
+    uint64_t* acc_full = a_empty + S;
+    uint64_t* h_full = acc_full + 2;
+    uint64_t* acc_empty = h_full + 2;
+    uint64_t* fin = acc_empty + 2;
+    volatile int* abort = reinterpret_cast<volatile int*>(sm + C::flag(nh));
     uint32_t* slot = reinterpret_cast<uint32_t*>(sm + C::slot(nh));
-    const int t = threadIdx.x, warp = t >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    if (warp == 0) tc::tmem_alloc(slot, 128);
-    if (t == 0) {
-        for (int s = 0; s < S; ++s) tc::mbar_init(&full[s], 1);
-        tc::mbar_init(mbar, 1);
+    if (warp == kWsMmaWarp) tc::tmem_alloc(slot, 256);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            tc::mbar_init(&a_full[s], 1);
+            tc::mbar_init(&a_empty[s], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&acc_full[i], 1);
+            tc::mbar_init(&h_full[i], kWsEpiWarps);
+            tc::mbar_init(&acc_empty[i], kWsEpiWarps);
+        }
+        tc::mbar_init(fin, 1);
+        *abort = 0;
         tc::fence_mbar_init();
     }
     load_wtile(W0, Pmb + sh.w_off[0], Wd, sh.in, 64, E);
     for (int j = 1; j < nh; ++j) load_wtile(Wh + (j - 1) * 8192, Pmb + sh.w_off[j], Wd, Wd, 64, 64);
     load_wtile(Wo, Pmb + sh.w_off[nh], 1, Wd, 16, 64);
-    for (int e = t; e < nh * 64; e += 128) bias[e] = (e % 64 < Wd) ? Pm[sh.b_off[e / 64] + e % 64] : 0.0f;
-    if (t == 0) bout[0] = Pm[sh.b_off[nh]];
+    for (int e = threadIdx.x; e < nh * 64; e += blockDim.x) bias[e] = (e % 64 < Wd) ? Pm[sh.b_off[e / 64] + e % 64] : 0.0f;
+    if (threadIdx.x == 0) bout[0] = Pm[sh.b_off[nh]];
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *slot;
-    const uint32_t lane = tmem + ((uint32_t)(warp * 32) << 16);
+    if (warp < kWsEpiWarps) {  // both slots start at layer 0 from its bias
+        store_bias64(tmem + ((uint32_t)(warp * 32) << 16), bias);
+        store_bias64(tmem + 128 + ((uint32_t)(warp * 32) << 16), bias);
+        tc::tmem_st_wait();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+
     const int64_t ntiles = (n + 127) / 128;
     const int64_t mine = (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    int64_t issued = 0;  // boxes requested so far (thread 0)
-    auto request = [&](int64_t q) {
-        const int s = (int)(q % S);
-        tc::mbar_expect_tx(&full[s], C::kBox);
-        tc::tma_load_2d(sm + s * C::kBox, &map, 0, (int)((blockIdx.x + q * gridDim.x) * 128), &full[s]);
-    };
-    if (t == 0)
-        for (; issued < mine && issued < S; ++issued) request(issued);
-    store_bias64(lane, bias);  // layer 0 starts from its bias
-    tc::tmem_st_wait();
-    tc::fence_before_sync();
-    __syncthreads();
-
-    constexpr uint32_t idesc = tc::idesc_bf16(128, 64), idesc_out = tc::idesc_bf16(128, 16);
-    const uint32_t a0 = tc::smem_addr(sm), h0 = tc::smem_addr(H), w0 = tc::smem_addr(W0), wh = tc::smem_addr(Wh),
-                   wo = tc::smem_addr(Wo);
     const int nk_in = (sh.in + 15) / 16, nk_w = (Wd + 15) / 16;
-    uint32_t phase = 0;
-    bool bad = false;
-    int64_t i = 0;
-    for (; i < mine; ++i) {
-        const int s = (int)(i % S);
-        for (int j = 0; j <= nh; ++j) {
+    if (warp == kWsTmaWarp) {
+        if (lane == 0) {
+            int64_t issued = 0;
+            for (int64_t k = 0; k < mine; ++k) {
+                const int s = (int)(k % S);
+                if (k >= S && !tc::mbar_wait_or_abort(&a_empty[s], (uint32_t)((k / S) - 1) & 1u, abort)) break;
+                tc::mbar_expect_tx(&a_full[s], C::kBox);
+                tc::tma_load_2d(sm + s * C::kBox, &map, 0, (int)((blockIdx.x + k * gridDim.x) * 128), &a_full[s]);
+                issued = k + 1;
+            }
+            // no copy may still be landing when the CTA leaves: wait (bounded) for the last ones
+            for (int64_t k = issued > S ? issued - S : 0; k < issued; ++k)
+                tc::mbar_wait(&a_full[k % S], (uint32_t)(k / S) & 1u);
+        }
+    } else if (warp == kWsMmaWarp) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16(128, 64), idesc_out = tc::idesc_bf16(128, 16);
+            const uint32_t a0 = tc::smem_addr(sm), h0 = tc::smem_addr(H), w0 = tc::smem_addr(W0),
+                           wh = tc::smem_addr(Wh), wo = tc::smem_addr(Wo);
             bool ok = true;
-            if (t == 0) {
-                if (j == 0) ok = tc::mbar_wait(&full[s], (uint32_t)(i / S) & 1u);
-                if (ok) {
-                    tc::fence_after_sync();
-                    if (j == 0) {
-                        for (int kk = 0; kk < nk_in; ++kk) {
-                            const uint32_t a = a0 + s * C::kBox + kk * 32, b = w0 + kk * 32;
-                            tc::mma_bf16(tmem, E == 32 ? tc::sdesc_sw64(a) : tc::sdesc_sw128(a),
-                                         E == 32 ? tc::sdesc_sw64(b) : tc::sdesc_sw128(b), idesc, 1u);
+            for (int64_t k0 = 0; k0 < mine && ok; k0 += 2) {
+                const int np = mine - k0 < 2 ? (int)(mine - k0) : 2;
+                for (int j = 0; j <= nh && ok; ++j) {
+                    for (int sl = 0; sl < np && ok; ++sl) {
+                        const int64_t k = k0 + sl, u = k >> 1;
+                        const uint32_t acc = tmem + sl * 128, hs = h0 + sl * 16384;
+                        if (j == 0) {
+                            const int s = (int)(k % S);
+                            if (u > 0 && !(ok = tc::mbar_wait_or_abort(&acc_empty[sl], (uint32_t)(u - 1) & 1u, abort))) break;
+                            if (!(ok = tc::mbar_wait_or_abort(&a_full[s], (uint32_t)(k / S) & 1u, abort))) break;
+                            tc::fence_after_sync();
+                            for (int kk = 0; kk < nk_in; ++kk) {
+                                const uint32_t a = a0 + s * C::kBox + kk * 32, b = w0 + kk * 32;
+                                tc::mma_bf16(acc, E == 32 ? tc::sdesc_sw64(a) : tc::sdesc_sw128(a),
+                                             E == 32 ? tc::sdesc_sw64(b) : tc::sdesc_sw128(b), idesc, 1u);
+                            }
+                            tc::mma_commit(&a_empty[s]);
+                        } else {
+                            if (!(ok = tc::mbar_wait_or_abort(&h_full[sl], (uint32_t)(u * nh + j - 1) & 1u, abort))) break;
+                            tc::fence_after_sync();
+                            if (j < nh) {
+                                for (int kk = 0; kk < nk_w; ++kk)
+                                    tc::mma_bf16(acc, tc::sdesc_sw128(hs + kk * 32),
+                                                 tc::sdesc_sw128(wh + (j - 1) * 8192 + kk * 32), idesc, 1u);
+                            } else {
+                                for (int kk = 0; kk < nk_w; ++kk)
+                                    tc::mma_bf16(acc + 64, tc::sdesc_sw128(hs + kk * 32), tc::sdesc_sw128(wo + kk * 32),
+                                                 idesc_out, kk > 0 ? 1u : 0u);
+                            }
                         }
-                    } else if (j < nh) {
-                        for (int kk = 0; kk < nk_w; ++kk)
-                            tc::mma_bf16(tmem, tc::sdesc_sw128(h0 + kk * 32), tc::sdesc_sw128(wh + (j - 1) * 8192 + kk * 32),
-                                         idesc, 1u);
-                    } else {
-                        for (int kk = 0; kk < nk_w; ++kk)
-                            tc::mma_bf16(tmem + 64, tc::sdesc_sw128(h0 + kk * 32), tc::sdesc_sw128(wo + kk * 32), idesc_out,
-                                         kk > 0 ? 1u : 0u);
+                        tc::mma_commit(&acc_full[sl]);
                     }
-                    tc::mma_commit(mbar);
                 }
             }
-            if (j == 0 && __syncthreads_or(!ok)) { bad = true; break; }  // the box never arrived
-            ok = tc::mbar_wait(mbar, phase);
-            phase ^= 1;
-            if (__syncthreads_or(!ok)) { bad = true; break; }
-            tc::fence_after_sync();
-            if (j == 0 && t == 0 && issued < mine) request(issued++);  // stage s has been read: refill it
-            if (j == nh) {
-                float y = tc::tmem_ld1(lane + 64);
-                tc::tmem_ld_wait();
-                const int64_t idx = (blockIdx.x + i * gridDim.x) * 128 + t;
-                if (idx < n) out[idx] = y + bout[0];
-                break;
-            }
-            hidden_epilogue(lane, H, t, nullptr, 0, Wd);
-            store_bias64(lane, bias + (j + 1 < nh ? (j + 1) * 64 : 0));  // the next tile starts at layer 0
-            tc::tmem_st_wait();
-            tc::fence_async_smem();
-            tc::fence_before_sync();
-            __syncthreads();
+            tc::mma_commit(fin);     // arrives when every MMA issued above has completed
+            tc::mbar_wait(fin, 0u);  // so none is in flight when TMEM is freed
         }
-        if (bad) break;
-    }
-    if (bad && t == 0) {
-        raise_error(err, 0x7C08);
-        tc::mbar_wait(mbar, phase ^ 1);  // MMAs possibly in flight
-        for (int64_t q = i; q < issued; ++q) tc::mbar_wait(&full[q % S], (uint32_t)(q / S) & 1u);  // copies in flight
+    } else {  // epilogue warps
+        const int row = warp * 32 + lane;
+        const uint32_t lanes = (uint32_t)(warp * 32) << 16;
+        bool ok = true;
+        for (int64_t k0 = 0; k0 < mine && ok; k0 += 2) {
+            const int np = mine - k0 < 2 ? (int)(mine - k0) : 2;
+            for (int j = 0; j <= nh && ok; ++j) {
+                for (int sl = 0; sl < np && ok; ++sl) {
+                    const int64_t k = k0 + sl, u = k >> 1;
+                    const uint32_t acc = tmem + sl * 128 + lanes;
+                    // warp-uniform outcome: tcgen05.ld/st and __syncwarp below need the whole warp
+                    ok = __all_sync(0xffffffffu, tc::mbar_wait_or_abort(&acc_full[sl], (uint32_t)(u * (nh + 1) + j) & 1u, abort));
+                    if (!ok) break;
+                    tc::fence_after_sync();
+                    if (j < nh) {
+                        hidden_epilogue(acc, H + sl * 16384, row, nullptr, 0, Wd);
+                        store_bias64(acc, bias + (j + 1 < nh ? (j + 1) * 64 : 0));  // the next tile starts at layer 0
+                        tc::tmem_st_wait();
+                        tc::fence_async_smem();
+                        tc::fence_before_sync();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&h_full[sl]);
+                    } else {
+                        const float y = tc::tmem_ld1(acc + 64);
+                        tc::tmem_ld_wait();
+                        const int64_t idx = (blockIdx.x + k * gridDim.x) * 128 + row;
+                        if (idx < n) out[idx] = y + bout[0];
+                        tc::fence_before_sync();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&acc_empty[sl]);
+                    }
+                }
+            }
+        }
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, 128);
+    if (threadIdx.x == 0 && *abort) raise_error(err, 0x7C08);
+    if (warp == kWsMmaWarp) {
+        __syncwarp();
+        tc::tmem_dealloc(tmem, 256);
+    }
 }
 
 // Rows [rows][E] bf16 as a 2D tensor (x = column, y = row) with E x 128 boxes, zero fill past the end.
@@ -207,14 +268,14 @@ static fhash_status mlp_chunk(fhash_model* m, const void* enc, int64_t cnt, floa
     const void* fn = (const void*)k_mlp_tc<E>;
     FH_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     FH_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    // at most 3 CTAs (3 x 128 TMEM columns) per SM; shared memory never admits more than 4
-    const int per_sm = std::max(1, std::min(3, (227 * 1024) / smem));
+    // at most two CTAs (2 x 256 TMEM columns) per SM; shared memory (over 76 KB each) never admits a third
+    const int per_sm = std::max(1, std::min(2, (227 * 1024) / smem));
     CUtensorMap map;
     if (!make_enc_map(&map, enc, cnt, E)) return set_error(FHASH_ECUDA, "split forward: tensor map encoding failed");
     const int64_t tiles = (cnt + 127) / 128;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)num_sms() * per_sm));
-    k_mlp_tc<E><<<grid, 128, smem, st>>>(map, m->mlp, m->shadow + m->n_table, m->param + m->n_table, cnt, out,
-                                         m->err_word);
+    k_mlp_tc<E><<<grid, kWsThreads, smem, st>>>(map, m->mlp, m->shadow + m->n_table, m->param + m->n_table, cnt, out,
+                                                m->err_word);
     FH_CUDA(cudaGetLastError());
     return FHASH_OK;
 }

@@ -80,15 +80,7 @@ fhash_status stage_in(fhash_model* m, Scratch& s, const void* p, size_t bytes, c
     return FHASH_OK;
 }
 
-// ------------------------------------------------------------------ SplitMix64 (device + host)
-// Steele, Lea, Flood (OOPSLA 2014).  Output i of the generator seeded with s: mix(s + (i+1)*gamma).
-#define FH_GAMMA 0x9E3779B97F4A7C15ULL
-__host__ __device__ __forceinline__ uint64_t sm_mix(uint64_t z) {
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-    return z ^ (z >> 31);
-}
-__host__ __device__ __forceinline__ uint64_t sm_at(uint64_t seed, uint64_t i) { return sm_mix(seed + (i + 1) * FH_GAMMA); }
+// ------------------------------------------------------------------ SplitMix64 uniforms (device + host)
 // (float)(lo + (hi - lo) * U) with the multiply and the add rounded separately (no FMA contraction).
 __host__ __device__ __forceinline__ float sm_uniform(uint64_t key, uint64_t i, double lo, double hi) {
     double u = (double)(sm_at(key, i) >> 40) * (1.0 / 16777216.0);
@@ -244,7 +236,7 @@ static void destroy_model(fhash_model* m) {
     cudaDeviceSynchronize();
     void* ps[] = {m->param, m->grad, m->adam_m, m->adam_v, m->shadow, m->occ, m->occ_any, m->err_word,
                   m->s_coords.p, m->s_target.p, m->s_out.p, m->s_acts.p, m->s_gacts.p, m->s_partial.p,
-                  m->s_loss.p, m->s_misc.p, m->s_render.p, m->s_enc.p};
+                  m->s_loss.p, m->s_misc.p, m->s_render.p, m->s_enc.p, m->s_cs_ent.p, m->s_cs_val.p};
     for (void* p : ps)
         if (p) cudaFree(p);
     delete m;

@@ -92,8 +92,24 @@ __global__ void __launch_bounds__(256) k_scatter_cols(const __grid_constant__ Le
         float g[F];
 #pragma unroll
         for (int f = 0; f < F; ++f) g[f] = denc[(int64_t)(l * F + f) * dsf + s * dss];
+        if constexpr (F == 2) {
+            // x-neighbours are consecutive rows: when the lower row is even the pair is one aligned 16-byte
+            // reduction instead of two 8-byte ones (fewer L2 atomic operations)
 #pragma unroll
-        for (int c = 0; c < 16; ++c) red_row<F>(G + corner_row(k, c) * F, corner_weight(k, c), g);
+            for (int c = 0; c < 16; c += 2) {
+                const uint64_t r = corner_row(k, c);
+                const float w0 = corner_weight(k, c), w1 = corner_weight(k, c + 1);
+                if (k.ox == 1u && (r & 1u) == 0u) {
+                    red_add4(G + r * 2, w0 * g[0], w0 * g[1], w1 * g[0], w1 * g[1]);
+                } else {
+                    red_add2(G + r * 2, w0 * g[0], w0 * g[1]);
+                    red_add2(G + (r + k.ox) * 2, w1 * g[0], w1 * g[1]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) red_row<F>(G + corner_row(k, c) * F, corner_weight(k, c), g);
+        }
     }
 }
 
