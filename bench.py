@@ -396,6 +396,44 @@ def suite_coreset(args):
     print(json.dumps(res))
 
 
+def suite_forward(args):
+    """The two evaluation paths of the precision form on uniform points: the fused kernel and the split
+    pair (bf16 encoding rows, then the TMA-fed tensor-core MLP).  --workload picks the model (random
+    initial tables, U(-0.5, 0.5)), --forward-points the batch, --steps the timed calls after 3 warm-up
+    calls; --forward-paths restricts the paths.  Both paths give bit-identical outputs (checked)."""
+    import torch
+    import synth
+    import paper_2507_03836_gb300 as fh
+    from synth import workloads
+    w = dict(_workload(args.workload), init_range=0.5)
+    field, mask = workloads.make_field_and_mask(w)
+    model, info = _build(w, fh.BF16, 1, mask)
+    n = args.forward_points
+    c = torch.from_numpy(synth.coords(5, n)).cuda()
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    res = {"suite": "forward", "workload": w["name"], "points": n, "steps": args.steps}
+    sums = {}
+    st = torch.cuda.current_stream()
+    for name in args.forward_paths.split(","):
+        fh.fhash_set_forward_path(model, {"fused": fh.FORWARD_FUSED, "split": fh.FORWARD_SPLIT}[name])
+        for _ in range(3):
+            fh.fhash_forward(model, c, out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            fh.fhash_forward(model, c, out)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        res[name] = {"ms": ms, "samples_s": n / ms * 1e3}
+        sums[name] = out.clone()
+    fh.fhash_check(model)
+    if len(sums) == 2:
+        res["bit_identical"] = bool(torch.equal(sums["fused"], sums["split"]))
+    print(json.dumps(res))
+
+
 def _serve(models, kinds, n_req, rate, budget, tf, seed=1234, decode_every=0):
     """Poisson stream through one server; kinds[i] = model index of request i; every `decode_every`-th
     request (0: none) is a time-slice decode (upsample 1 or 2), the rest renders of 256^2/512^2/1024^2."""
@@ -526,7 +564,9 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving and precision legs")
     ap.add_argument("--serve-requests", type=int, default=60)
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, requests/s")
-    ap.add_argument("--suite", default="train", choices=["train", "precision", "serve", "mixed", "coreset"],
+    ap.add_argument("--forward-points", type=int, default=1 << 22, help="--suite forward: points per call")
+    ap.add_argument("--forward-paths", default="fused,split", help="--suite forward: paths to time")
+    ap.add_argument("--suite", default="train", choices=["train", "precision", "serve", "mixed", "coreset", "forward"],
                     help="train: the default line; precision / serve / mixed: the other workloads")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -535,7 +575,7 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         return {"precision": suite_precision, "serve": suite_serve, "mixed": suite_mixed,
-                "coreset": suite_coreset}[args.suite](args)
+                "coreset": suite_coreset, "forward": suite_forward}[args.suite](args)
 
     import torch
     import synth

@@ -150,16 +150,28 @@ __device__ inline void load_wtile(uint8_t* dst, const __nv_bfloat16* __restrict_
 }
 
 // Every warp writes bias[0..63] into 64 TMEM columns of its 32 lanes starting at lane_taddr, so that
-// the layer's MMAs accumulate onto the bias.  The caller waits (tcgen05.wait::st) before the barrier
-// that precedes the MMAs.
+// the layer's MMAs accumulate onto the bias.  `bias` is 16-byte aligned shared memory.  The caller
+// waits (tcgen05.wait::st) before the barrier that precedes the MMAs.
 __device__ __forceinline__ void store_bias64(uint32_t lane_taddr, const float* bias) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         float b[32];
 #pragma unroll
-        for (int q = 0; q < 32; ++q) b[q] = bias[32 * h + q];
+        for (int q = 0; q < 8; ++q) {
+            const float4 v = reinterpret_cast<const float4*>(bias + 32 * h)[q];
+            b[4 * q] = v.x; b[4 * q + 1] = v.y; b[4 * q + 2] = v.z; b[4 * q + 3] = v.w;
+        }
         tc::tmem_st32(lane_taddr + 32 * h, b);
     }
+}
+
+// max(a, 0) and max(b, 0) rounded to bf16 (nearest even) and packed, b in the upper half: one
+// cvt.rn.relu.bf16x2.f32.  For finite inputs this equals pack_bf16x2(fmaxf(b, 0), fmaxf(a, 0))
+// with the halves swapped back, since rounding keeps the sign.
+__device__ __forceinline__ uint32_t relu_pack_bf16x2(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
 }
 
 // Hidden-layer epilogue of one sample row: the 64 accumulator columns of this thread's lane (bias +
@@ -172,14 +184,17 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t lane_taddr, uint8_t* H,
         float v[32];
         tc::tmem_ld32(lane_taddr + 32 * h, v);
         tc::tmem_ld_wait();
-#pragma unroll
-        for (int q = 0; q < 32; ++q) v[q] = fmaxf(v[q], 0.0f);
         if (a) {
 #pragma unroll
             for (int q = 0; q < 32; ++q)
-                if (32 * h + q < width) a[(int64_t)(32 * h + q) * stride] = v[q];
+                if (32 * h + q < width) a[(int64_t)(32 * h + q) * stride] = fmaxf(v[q], 0.0f);
         }
-        write_half_row(H, r, h, v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint4 w = make_uint4(relu_pack_bf16x2(v[8 * q + 0], v[8 * q + 1]), relu_pack_bf16x2(v[8 * q + 2], v[8 * q + 3]),
+                                       relu_pack_bf16x2(v[8 * q + 4], v[8 * q + 5]), relu_pack_bf16x2(v[8 * q + 6], v[8 * q + 7]));
+            *reinterpret_cast<uint4*>(H + tc::sw128_off(r, 4 * h + q)) = w;
+        }
     }
 }
 
