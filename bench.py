@@ -434,6 +434,37 @@ def suite_forward(args):
     print(json.dumps(res))
 
 
+def suite_peaks(args):
+    """Ceilings of the encoding's access pattern on this GPU: random gathers of 4, 8 and 16 bytes from a
+    64 MB table (resident in the 129 MB L2) and from an 8 GB table (HBM), through the library's
+    fhash_diag_random_gather kernel.  Reports gathers/s, useful GB/s and 32-byte-sector GB/s, plus
+    MEASURED_PEAKS.json for reference."""
+    import torch
+    import paper_2507_03836_gb300 as fh
+    res = {"suite": "peaks", "measured_peaks": _peaks()[0]}
+    out = torch.zeros(1, dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+    for name, nbytes in (("l2_64MB", 64 << 20), ("hbm_8GB", 8 << 30)):
+        table = torch.rand(nbytes // 4, dtype=torch.float32, device="cuda")
+        for width in (4, 8, 16):
+            n = 1 << 28
+            for _ in range(2):
+                fh.fhash_diag_random_gather(table, width, n, 7, out)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            reps = 5
+            for r in range(reps):
+                fh.fhash_diag_random_gather(table, width, n, 100 + r, out)
+            e1.record(st)
+            torch.cuda.synchronize()
+            s = e0.elapsed_time(e1) / 1e3 / reps
+            res["%s_w%d" % (name, width)] = {"gathers_s": n / s, "useful_gbs": n * width / s / 1e9,
+                                              "sector_gbs": n * 32 / s / 1e9}
+        del table
+    print(json.dumps(res))
+
+
 def _serve(models, kinds, n_req, rate, budget, tf, seed=1234, decode_every=0):
     """Poisson stream through one server; kinds[i] = model index of request i; every `decode_every`-th
     request (0: none) is a time-slice decode (upsample 1 or 2), the rest renders of 256^2/512^2/1024^2."""
@@ -566,7 +597,7 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--forward-points", type=int, default=1 << 22, help="--suite forward: points per call")
     ap.add_argument("--forward-paths", default="fused,split", help="--suite forward: paths to time")
-    ap.add_argument("--suite", default="train", choices=["train", "precision", "serve", "mixed", "coreset", "forward"],
+    ap.add_argument("--suite", default="train", choices=["train", "precision", "serve", "mixed", "coreset", "forward", "peaks"],
                     help="train: the default line; precision / serve / mixed: the other workloads")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -575,7 +606,7 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         return {"precision": suite_precision, "serve": suite_serve, "mixed": suite_mixed,
-                "coreset": suite_coreset, "forward": suite_forward}[args.suite](args)
+                "coreset": suite_coreset, "forward": suite_forward, "peaks": suite_peaks}[args.suite](args)
 
     import torch
     import synth

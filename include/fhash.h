@@ -156,6 +156,25 @@ const char* fhash_last_error(void);
 fhash_status fhash_get_info(const fhash_model* model, fhash_info* out);
 
 /*
+ * Level schedule and Feature Bounding Box of a model (the subset of fhash_get_info that defines
+ * the Eq. 9 rows): *L levels; res[l] = (Rx, Ry, Rz, Rt) and base[l] = first row of level l,
+ * coarse to fine; fbb = (lo_x, lo_y, lo_z, size_x, size_y, size_z).  The arrays need room for L
+ * levels (at most FHASH_MAX_LEVELS); any output pointer may be NULL.
+ */
+fhash_status fhash_level_info(const fhash_model* model, int32_t* L, int32_t (*res)[4], uint64_t* base, int64_t fbb[6]);
+
+/*
+ * The model's float32 master parameters in two caller-owned buffers, host or device: tables
+ * [total_rows][F] (Eq. 9 rows, levels concatenated coarse to fine) and the MLP vector
+ * [n_mlp_params] (per layer W[out][in] then b[out]).  Either pointer may be NULL.  Returns after the
+ * copy when a buffer is host memory.  fhash_set_params writes them (and refreshes the bf16 shadows of
+ * FHASH_BF16 models).  Equivalent to fhash_read_state / fhash_write_state of FHASH_STATE_PARAM over
+ * the two ranges.
+ */
+fhash_status fhash_get_params(fhash_model* model, float* tables, float* mlp, fhash_stream stream);
+fhash_status fhash_set_params(fhash_model* model, const float* tables, const float* mlp, fhash_stream stream);
+
+/*
  * Encoding steps 1-3 of Section 3.2.4 for inspection: per sample and level, the 16 corner rows
  * through Eq. 9 (with level base) and their quadrilinear weights (Eqs. 10-12), corner index
  * c = i + 2j + 4k + 8s (i, j, k: upper corner on x, y, z; s = 1 for t_Next).
@@ -276,6 +295,15 @@ fhash_status fhash_load(const char* path, fhash_stream stream, fhash_model** out
  * wait gives up, the kernel records the timeout in the model's device error word and returns; the
  * next fhash_check reports FHASH_EDEVICE.  Nothing traps or hangs.  Asynchronous. */
 fhash_status fhash_diag_wait_timeout(fhash_model* model, uint64_t limit_ns, fhash_stream stream);
+
+/* Measurement aid with no counterpart in the paper: the ceiling of the encoding's access pattern.
+ * It performs n gathers of `width` bytes (4, 8 or 16) at uniformly random aligned positions of a
+ * device table of `bytes` bytes (16-byte aligned), 8 independent loads in flight per thread, and adds
+ * a float checksum into *sum (device).  Time it with events on `stream`: for a table that fits in L2
+ * it gives the L2 random-gather rate, and for one far larger than L2 the HBM rate at 32-byte
+ * sectors.  Asynchronous; bad arguments are FHASH_EINVAL. */
+fhash_status fhash_diag_random_gather(const void* table, uint64_t bytes, int32_t width, int64_t n, uint64_t seed,
+                                      float* sum, fhash_stream stream);
 
 /* Synchronise `stream` and report FHASH_EDEVICE if a kernel of this model raised the device
  * error word since the last check (the word is then cleared). */

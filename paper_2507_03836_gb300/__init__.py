@@ -97,11 +97,15 @@ _SIGS = {
     "fhash_apply_adam": [_vp, ctypes.POINTER(fhash_adam), _vp],
     "fhash_train_step": [_vp, _vp, _vp, _i64, ctypes.POINTER(fhash_adam), _vp, _vp],
     "fhash_read_state": [_vp, _i32, _u64, _u64, _vp, _vp],
+    "fhash_get_params": [_vp, _vp, _vp, _vp],
+    "fhash_set_params": [_vp, _vp, _vp, _vp],
+    "fhash_level_info": [_vp, ctypes.POINTER(_i32), _vp, _vp, _vp],
     "fhash_write_state": [_vp, _i32, _u64, _u64, _vp, _vp],
     "fhash_read_occupancy": [_vp, _i64, _vp, _vp],
     "fhash_check": [_vp, _vp],
     "fhash_save": [_vp, ctypes.c_char_p],
     "fhash_diag_wait_timeout": [_vp, _u64, _vp],
+    "fhash_diag_random_gather": [_vp, _u64, _i32, _i64, _u64, _vp, _vp],
     "fhash_load": [ctypes.c_char_p, _vp, ctypes.POINTER(_vp)],
     "fhash_compute_grads_noalloc": [_vp, _vp, _vp, _i64, _vp, _vp],
     "fhash_render": [_vp, ctypes.POINTER(fhash_camera), ctypes.c_float, _vp, _i32, _i32, _i32, _vp, _vp,
@@ -287,6 +291,25 @@ def fhash_coreset_train_step(model, seed, epoch, batch, batch_size, adam=None, l
                                       _stream(stream)))
 
 
+def fhash_get_params(model, tables=None, mlp=None, stream=None):
+    _ok(_lib.fhash_get_params(model.handle, _ptr(tables), _ptr(mlp), _stream(stream)))
+
+
+def fhash_set_params(model, tables=None, mlp=None, stream=None):
+    _ok(_lib.fhash_set_params(model.handle, _ptr(tables), _ptr(mlp), _stream(stream)))
+
+
+def fhash_level_info(model):
+    """Returns (res [L][4], base [L], fbb [6]) as lists."""
+    L = ctypes.c_int32(0)
+    res = (ctypes.c_int32 * (4 * MAX_LEVELS))()
+    base = (ctypes.c_uint64 * MAX_LEVELS)()
+    fbb = (ctypes.c_int64 * 6)()
+    _ok(_lib.fhash_level_info(model.handle, ctypes.byref(L), res, base, fbb))
+    n = L.value
+    return [list(res[4 * l:4 * l + 4]) for l in range(n)], [int(b) for b in base[:n]], list(fbb)
+
+
 def fhash_read_state(model, which, offset, buf, stream=None):
     n = buf.numel() if hasattr(buf, "numel") else buf.size
     _ok(_lib.fhash_read_state(model.handle, which, int(offset), int(n), _ptr(buf), _stream(stream)))
@@ -349,6 +372,11 @@ def fhash_load(path, stream=None):
 
 def fhash_diag_wait_timeout(model, limit_ns, stream=None):
     _ok(_lib.fhash_diag_wait_timeout(model.handle, int(limit_ns), _stream(stream)))
+
+
+def fhash_diag_random_gather(table, width, n, seed, sum_out, stream=None):
+    nbytes = table.numel() * table.element_size()
+    _ok(_lib.fhash_diag_random_gather(_ptr(table), nbytes, width, n, seed, _ptr(sum_out), _stream(stream)))
 
 
 def fhash_check(model, stream=None):

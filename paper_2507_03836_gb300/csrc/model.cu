@@ -459,6 +459,40 @@ fhash_status fhash_write_state(fhash_model* m, int32_t which, uint64_t off, uint
     return FHASH_OK;
 }
 
+fhash_status fhash_get_params(fhash_model* m, float* tables, float* mlp, fhash_stream stream) {
+    if (!m) return set_error(FHASH_EINVAL, "fhash_get_params: null model");
+    if (tables) FH_TRY(fhash_read_state(m, FHASH_STATE_PARAM, 0, m->n_table, tables, stream));
+    if (mlp) FH_TRY(fhash_read_state(m, FHASH_STATE_PARAM, m->n_table, m->n_params - m->n_table, mlp, stream));
+    if ((tables && !is_device_ptr(tables)) || (mlp && !is_device_ptr(mlp)))
+        FH_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return FHASH_OK;
+}
+
+fhash_status fhash_set_params(fhash_model* m, const float* tables, const float* mlp, fhash_stream stream) {
+    if (!m) return set_error(FHASH_EINVAL, "fhash_set_params: null model");
+    if (tables) FH_TRY(fhash_write_state(m, FHASH_STATE_PARAM, 0, m->n_table, tables, stream));
+    if (mlp) FH_TRY(fhash_write_state(m, FHASH_STATE_PARAM, m->n_table, m->n_params - m->n_table, mlp, stream));
+    if ((tables && !is_device_ptr(tables)) || (mlp && !is_device_ptr(mlp)))
+        FH_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return FHASH_OK;
+}
+
+fhash_status fhash_level_info(const fhash_model* m, int32_t* L, int32_t (*res)[4], uint64_t* base, int64_t fbb[6]) {
+    if (!m) return set_error(FHASH_EINVAL, "fhash_level_info: null model");
+    if (L) *L = m->lv.L;
+    for (int l = 0; l < m->lv.L; ++l) {
+        if (res)
+            for (int d = 0; d < 4; ++d) res[l][d] = m->lv.lv[l].R[d];
+        if (base) base[l] = m->lv.lv[l].base;
+    }
+    if (fbb)
+        for (int d = 0; d < 3; ++d) {
+            fbb[d] = m->fbb_lo[d];
+            fbb[3 + d] = m->fbb_size[d];
+        }
+    return FHASH_OK;
+}
+
 fhash_status fhash_read_occupancy(fhash_model* m, int64_t t, uint8_t* out, fhash_stream stream) {
     if (!m || !out) return set_error(FHASH_EINVAL, "fhash_read_occupancy: null argument");
     if (t < 0 || t >= m->nt) return set_error(FHASH_EINVAL, "fhash_read_occupancy: t out of range");

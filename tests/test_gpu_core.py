@@ -228,3 +228,21 @@ def test_training_curve_parity(small):
     lg, lo = np.array(losses_g), np.array(losses_o)
     assert lo[-1] < 0.5 * lo[0]
     assert (np.abs(lg - lo) <= 1e-4 * lo).all(), np.max(np.abs(lg - lo) / lo)
+
+
+def test_params_and_level_info_entry_points(small):
+    info, model = small["info"], small["model"]
+    res, base, fbb = fh().fhash_level_info(model)
+    assert res == info["res"] and base == info["base"] and fbb == info["fbb_lo"] + info["fbb_size"]
+    table, p = _random_params(info, seed=17)
+    t0 = np.empty_like(table)
+    p0 = np.empty_like(p)
+    fh().fhash_get_params(model, t0, p0)
+    fh().fhash_set_params(model, table, p)  # host buffers
+    t1 = torch().empty(table.size, dtype=torch().float32, device="cuda")
+    p1 = torch().empty(p.size, dtype=torch().float32, device="cuda")
+    fh().fhash_get_params(model, t1, p1)  # device buffers
+    torch().cuda.synchronize()
+    assert np.array_equal(t1.cpu().numpy(), table) and np.array_equal(p1.cpu().numpy(), p)
+    assert np.array_equal(read(model, fh().STATE_PARAM, 0, table.size), table)
+    fh().fhash_set_params(model, t0, p0)  # restore the module fixture's parameters

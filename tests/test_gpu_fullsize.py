@@ -109,3 +109,56 @@ def test_fullsize_forward_train_step(large):
         got[k] = one
     assert (np.abs(got - p1) <= 1e-6 * HP32[0] + 3e-7 * np.abs(p1)).all()
     fh().fhash_check(model)
+
+
+def test_fullsize_finite_differences(large):
+    """Central differences of the full-batch loss (2^18 samples, the bench's launch configuration)
+    against the GPU's analytic gradient on 48 touched table entries across the levels and 16 MLP
+    parameters.  The loss is piecewise quadratic in each parameter, so the quotient is exact up to
+    float32 rounding unless a ReLU flips inside +-h: a point whose quotients at h and h/10 disagree
+    by more than 1% is dropped (at least 48 of the 64 must be checked).  h = 1e-2 for table entries
+    (only a few samples see them, so a larger step keeps float32 rounding of the outputs small) and
+    1e-3 for MLP parameters.  Bound: 2% relative."""
+    info, model = large["info"], large["model"]
+    lv, b, F = info["res"], info["base"], info["F"]
+    n_t = info["n_table_params"]
+    c = synth.coords(20_000, W["batch"])
+    tgt = synth.sample(large["field"], info["fbb_lo"], info["fbb_size"], c)
+    dc, dt = to_dev(c), to_dev(tgt)
+    loss = np.zeros(1, np.float64)
+    g = np.zeros(1, np.float32)
+    # a clean gradient: the previous test ended with an Adam step, which clears the buffer
+    fh().fhash_compute_grads(model, dc, dt, loss)
+    pick = np.random.default_rng(5)
+    params = []
+    for level in (0, 3, 6, 9, 12, 15, 15, 15):
+        rows, _ = encode.level_corners(c[:64], lv[level], b[level])
+        for r in pick.choice(rows.ravel(), 6, replace=False):
+            params.append(int(r) * F + int(pick.integers(0, F)))
+    params += [n_t + int(k) for k in pick.choice(info["n_mlp_params"], 16, replace=False)]
+    grads = []
+    for off in params:
+        fh().fhash_read_state(model, fh().STATE_GRAD, off, g)
+        grads.append(float(g[0]))
+
+    def L(off, v):
+        fh().fhash_write_state(model, fh().STATE_PARAM, off, np.array([v], np.float32))
+        fh().fhash_compute_grads(model, dc, dt, loss)
+        return loss[0]
+
+    p = np.zeros(1, np.float32)
+    checked = 0
+    for off, gr in zip(params, grads):
+        fh().fhash_read_state(model, fh().STATE_PARAM, off, p)
+        v0 = float(p[0])
+        fd = []
+        for h in ((1e-2, 1e-3) if off < n_t else (1e-3, 1e-4)):
+            vp, vm = float(np.float32(v0 + h)), float(np.float32(v0 - h))
+            fd.append((L(off, vp) - L(off, vm)) / (vp - vm))
+        fh().fhash_write_state(model, fh().STATE_PARAM, off, np.array([v0], np.float32))
+        if abs(fd[0] - fd[1]) > 1e-2 * max(abs(fd[0]), 1e-12):
+            continue  # a ReLU kink inside +-h
+        assert abs(fd[0] - gr) <= 2e-2 * abs(fd[0]) + 1e-12, (off, fd, gr)
+        checked += 1
+    assert checked >= 48, checked
+    fh().fhash_check(model)
