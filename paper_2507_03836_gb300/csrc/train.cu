@@ -1,8 +1,9 @@
 // Training pass split by access pattern (float32 and the backward of the bf16 form):
 //   k_encode_cols   level-major gathers (thread per level and sample), encoding to global columns;
-//   k_mlp_fwd_g     MLP forward + MSE from those columns (weights in shared memory, activations in
-//                   registers and global columns), dL/dy and float64 loss partials;
-//   k_mlp_bwd_g     MLP backward data path: deltas per layer and d(loss)/d(encoding) to global columns;
+//   k_mlp_fwd_t     MLP forward + MSE from those columns on 128-sample tiles (weights and activation
+//                   tiles in shared memory, register-tiled GEMMs), dL/dy and float64 loss partials;
+//   k_mlp_bwd_t     MLP backward data path on the same tiles: deltas per layer and d(loss)/d(encoding)
+//                   to global columns;
 //   k_scatter_cols  backward of Eqs. 10-12: level-major vector reductions into the table gradient, with
 //                   coarse levels accumulated in shared memory first (privatised) to avoid thousands of
 //                   same-address atomics per row;
@@ -113,152 +114,180 @@ __global__ void __launch_bounds__(256) k_scatter_cols(const __grid_constant__ Le
     }
 }
 
-// ------------------------------------------------------------------ MLP, activations in registers
-// Forward weights transposed (Wt[in][out]) and backward weights row-major (W[out][in]) in shared memory.
-struct GLayout {
-    int wt[FHASH_MAX_HIDDEN + 1], wr[FHASH_MAX_HIDDEN + 1], b[FHASH_MAX_HIDDEN + 1], floats;
-};
+// ------------------------------------------------------------------ MLP on 128-sample tiles (float32 SIMT)
+// A block of 256 threads takes 128 samples at a time.  Layer inputs and outputs live in shared memory
+// feature-major, X[k][s] (k < 64 features, s < 128 samples), and every layer is a small GEMM: thread
+// (to = tid / 32, ts = tid % 32) owns outputs o = 8 to .. 8 to + 7 of samples s = 4 ts .. 4 ts + 3,
+// reading per k one float4 of X (a warp reads 512 contiguous bytes) and two float4 of the weights
+// (the same address across the warp): 32 FMAs per 3 shared loads.  Weights are staged once per block,
+// zero-padded to 64 outputs.
+constexpr int kTileS = 128, kTileF = 64;
 
-__host__ __device__ inline GLayout g_layout(const MlpShape& sh) {
-    GLayout L{};
-    int off = 0;
-    for (int k = 0; k <= sh.nh; ++k) {
-        const int fi = k == 0 ? sh.in : sh.width, fo = k == sh.nh ? 1 : sh.width;
-        const int n4 = (fi * fo + 3) / 4 * 4;
-        L.wt[k] = off; off += n4;
-        L.wr[k] = off; off += fo * ((fi + 3) / 4 * 4);  // rows padded to a multiple of 4
-        L.b[k] = off; off += (fo + 3) / 4 * 4;
-    }
-    L.floats = off;
-    return L;
-}
-
-__device__ inline void g_load(const float* __restrict__ g, const MlpShape& sh, const GLayout& L, float* s) {
-    for (int k = 0; k <= sh.nh; ++k) {
-        const int fi = k == 0 ? sh.in : sh.width, fo = k == sh.nh ? 1 : sh.width;
-        const int fi4 = (fi + 3) / 4 * 4;
-        for (int e = threadIdx.x; e < fi4 * fo; e += blockDim.x) {
-            const int o = e / fi4, i = e % fi4;
-            const float w = (i < fi) ? g[sh.w_off[k] + o * fi + i] : 0.0f;
-            if (i < fi) s[L.wt[k] + i * fo + o] = w;
-            s[L.wr[k] + e] = w;
-        }
-        for (int e = threadIdx.x; e < fo; e += blockDim.x) s[L.b[k] + e] = g[sh.b_off[k] + e];
-    }
-}
-
-// acc[o] = b[o] + sum_i Wt[i][o] x[i * xs], o < fo (fo a multiple of 4, at most 64): one load of each
-// input, 16 float4 weight broadcasts per input.
-__device__ __forceinline__ void dense_g(const float* __restrict__ Wt, const float* __restrict__ b, int fi, int fo,
-                                        const float* __restrict__ x, int64_t xs, float (&acc)[64]) {
+// acc[u][v] += sum over k < K of Wk[k][8 to + u] * X[k][4 ts + v] (row strides 64 and 128 floats).
+__device__ __forceinline__ void tile_gemm(const float* __restrict__ X, const float* __restrict__ Wk, int K,
+                                          float (&acc)[8][4]) {
+    const int ts = threadIdx.x & 31, to = threadIdx.x >> 5;
+#pragma unroll 4
+    for (int k = 0; k < K; ++k) {
+        const float4 x = *reinterpret_cast<const float4*>(X + k * kTileS + 4 * ts);
+        const float4 w0 = *reinterpret_cast<const float4*>(Wk + k * kTileF + 8 * to);
+        const float4 w1 = *reinterpret_cast<const float4*>(Wk + k * kTileF + 8 * to + 4);
+        const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+        const float xv[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-    for (int o = 0; o < 64; ++o) acc[o] = (o < fo) ? b[o] : 0.0f;
-#pragma unroll 2
-    for (int i = 0; i < fi; ++i) {
-        const float xv = x[i * xs];
-        const float4* w4 = reinterpret_cast<const float4*>(Wt + i * fo);
+        for (int u = 0; u < 8; ++u)
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            if (4 * q < fo) {
-                const float4 w = w4[q];
-                acc[4 * q + 0] = fmaf(w.x, xv, acc[4 * q + 0]);
-                acc[4 * q + 1] = fmaf(w.y, xv, acc[4 * q + 1]);
-                acc[4 * q + 2] = fmaf(w.z, xv, acc[4 * q + 2]);
-                acc[4 * q + 3] = fmaf(w.w, xv, acc[4 * q + 3]);
-            }
-        }
+            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(w[u], xv[v], acc[u][v]);
     }
 }
 
-__global__ void __launch_bounds__(128) k_mlp_fwd_g(const __grid_constant__ MlpShape sh, const float* __restrict__ Pm,
+// Rows [r][c] of a layer's weights in shared memory with row stride 64: transposed (Wt[in][out], the
+// forward's Wk) or as stored (W[out][in], the backward's Wk); zero outside fo x fi.
+__device__ inline void stage_weights(float* dst, const float* __restrict__ W, int fo, int fi, bool transpose) {
+    for (int e = threadIdx.x; e < kTileF * kTileF; e += blockDim.x) {
+        const int r = e / kTileF, c = e % kTileF;
+        float v = 0.0f;
+        if (transpose) { if (r < fi && c < fo) v = W[c * fi + r]; }
+        else if (r < fo && c < fi) v = W[r * fi + c];
+        dst[e] = v;
+    }
+}
+
+// Global column rows [rows][n] of a tile into X[k][s] (zero past n).
+__device__ inline void load_tile(float* X, const float* __restrict__ cols, int rows, int64_t n, int64_t t0) {
+    for (int e = threadIdx.x; e < rows * kTileS; e += blockDim.x) {
+        const int k = e / kTileS, sidx = e % kTileS;
+        X[e] = (t0 + sidx < n) ? cols[(int64_t)k * n + t0 + sidx] : 0.0f;
+    }
+}
+
+// Shared memory (floats): nh weight blocks of 64 x 64, biases [nh][64], output weights [64], two tiles.
+__host__ __device__ inline int tile_smem_floats(int nh) { return nh * kTileF * kTileF + nh * kTileF + kTileF + 2 * kTileF * kTileS; }
+
+__global__ void __launch_bounds__(256) k_mlp_fwd_t(const __grid_constant__ MlpShape sh, const float* __restrict__ Pm,
                                                    const float* __restrict__ target, int64_t n, float two_over_n,
                                                    float* __restrict__ acts, float* __restrict__ gy,
                                                    double* __restrict__ partial) {
     extern __shared__ float4 sm4[];
-    float* s = reinterpret_cast<float*>(sm4);
-    const GLayout L = g_layout(sh);
-    g_load(Pm, sh, L, s);
-    __syncthreads();
-    const int W = sh.width;
+    float* Wk = reinterpret_cast<float*>(sm4);
+    const int nh = sh.nh, Wd = sh.width;
+    float* bias = Wk + nh * kTileF * kTileF;
+    float* wout = bias + nh * kTileF;
+    float* T0 = wout + kTileF;
+    float* T1 = T0 + kTileF * kTileS;
+    for (int j = 0; j < nh; ++j) {
+        stage_weights(Wk + j * kTileF * kTileF, Pm + sh.w_off[j], Wd, j == 0 ? sh.in : Wd, true);
+        for (int o = threadIdx.x; o < kTileF; o += blockDim.x) bias[j * kTileF + o] = o < Wd ? Pm[sh.b_off[j] + o] : 0.0f;
+    }
+    for (int o = threadIdx.x; o < kTileF; o += blockDim.x) wout[o] = o < Wd ? Pm[sh.w_off[nh] + o] : 0.0f;
+    const float bo = Pm[sh.b_off[nh]];
+    const int ts = threadIdx.x & 31, to = threadIdx.x >> 5;
     double lsum = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        float acc[64];
-        const float* x = acts + i;
-        for (int k = 0; k < sh.nh; ++k) {
-            const int fi = k == 0 ? sh.in : W;
-            dense_g(s + L.wt[k], s + L.b[k], fi, W, x, n, acc);
-            float* y = acts + (int64_t)(sh.in + k * W) * n + i;
+    for (int64_t t0 = (int64_t)blockIdx.x * kTileS; t0 < n; t0 += (int64_t)gridDim.x * kTileS) {
+        __syncthreads();  // weights staged / the previous tile consumed
+        load_tile(T0, acts, sh.in, n, t0);
+        __syncthreads();
+        float* src = T0;
+        float* dst = T1;
+        for (int j = 0; j < nh; ++j) {
+            float acc[8][4];
 #pragma unroll
-            for (int o = 0; o < 64; ++o)
-                if (o < W) y[(int64_t)o * n] = fmaxf(acc[o], 0.0f);
-            x = y;
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = bias[j * kTileF + 8 * to + u];
+            tile_gemm(src, Wk + j * kTileF * kTileF, j == 0 ? sh.in : Wd, acc);
+            float* arow = acts + (int64_t)(sh.in + j * Wd) * n;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int o = 8 * to + u;
+                float r[4];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) r[v] = fmaxf(acc[u][v], 0.0f);
+                *reinterpret_cast<float4*>(dst + o * kTileS + 4 * ts) = make_float4(r[0], r[1], r[2], r[3]);
+                if (o < Wd) {
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+                        if (t0 + 4 * ts + v < n) arow[(int64_t)o * n + t0 + 4 * ts + v] = r[v];
+                }
+            }
+            __syncthreads();
+            float* t = src; src = dst; dst = t;
         }
-        // output layer from the last hidden activations (still in registers)
-        const float* wo = s + L.wt[sh.nh];
-        float yv = s[L.b[sh.nh]];
-#pragma unroll
-        for (int o = 0; o < 64; ++o)
-            if (o < W) yv = fmaf(wo[o], fmaxf(acc[o], 0.0f), yv);
-        const float r = yv - __ldg(target + i);
-        gy[i] = two_over_n * r;
-        lsum += (double)r * (double)r;
+        if (threadIdx.x < kTileS && t0 + threadIdx.x < n) {  // scalar output layer on the last hidden tile
+            float y = bo;
+            for (int o = 0; o < Wd; ++o) y = fmaf(wout[o], src[o * kTileS + threadIdx.x], y);
+            const int64_t i = t0 + threadIdx.x;
+            const float d = y - __ldg(target + i);
+            gy[i] = two_over_n * d;
+            lsum += (double)d * (double)d;
+        }
     }
     const double t = block_sum(lsum);
     if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
 // dl[(j*W + o) * n + i] = delta of layer j's output (the output layer's at row nh*W); denc[c * n + i] =
-// d(loss)/d(encoding c).
-__global__ void __launch_bounds__(128) k_mlp_bwd_g(const __grid_constant__ MlpShape sh, const float* __restrict__ Pm,
+// d(loss)/d(encoding c).  Delta tiles stay in shared memory from layer to layer.
+__global__ void __launch_bounds__(256) k_mlp_bwd_t(const __grid_constant__ MlpShape sh, const float* __restrict__ Pm,
                                                    int64_t n, const float* __restrict__ acts, const float* __restrict__ gy,
                                                    float* __restrict__ dl, float* __restrict__ denc) {
     extern __shared__ float4 sm4[];
-    float* s = reinterpret_cast<float*>(sm4);
-    const GLayout L = g_layout(sh);
-    g_load(Pm, sh, L, s);
-    __syncthreads();
-    const int W = sh.width;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float g = gy[i];
-        dl[(int64_t)(sh.nh * W) * n + i] = g;
-        const float* wo = s + L.wt[sh.nh];  // output layer: W[0][o], same in both layouts
-        const float* a = acts + (int64_t)(sh.in + (sh.nh - 1) * W) * n + i;
-        float* d = dl + (int64_t)((sh.nh - 1) * W) * n + i;
-        for (int o = 0; o < W; ++o) d[(int64_t)o * n] = (a[(int64_t)o * n] > 0.0f) ? wo[o] * g : 0.0f;
-        for (int j = sh.nh - 1; j >= 0; --j) {
-            // p[c] = sum_o W_j[o][c] delta_j[o], outer-product order: one load of each delta
-            const int fi = j == 0 ? sh.in : W, fi4 = (fi + 3) / 4 * 4;
-            const float* Wr = s + L.wr[j];
-            const float* dj = dl + (int64_t)(j * W) * n + i;
-            float p[64];
+    float* Wk = reinterpret_cast<float*>(sm4);
+    const int nh = sh.nh, Wd = sh.width;
+    float* wout = Wk + nh * kTileF * kTileF + nh * kTileF;
+    float* T0 = wout + kTileF;
+    float* T1 = T0 + kTileF * kTileS;
+    for (int j = 0; j < nh; ++j) stage_weights(Wk + j * kTileF * kTileF, Pm + sh.w_off[j], Wd, j == 0 ? sh.in : Wd, false);
+    for (int o = threadIdx.x; o < kTileF; o += blockDim.x) wout[o] = o < Wd ? Pm[sh.w_off[nh] + o] : 0.0f;
+    const int ts = threadIdx.x & 31, to = threadIdx.x >> 5;
+    for (int64_t t0 = (int64_t)blockIdx.x * kTileS; t0 < n; t0 += (int64_t)gridDim.x * kTileS) {
+        __syncthreads();
+        // output layer: delta of the last hidden layer = (a > 0) * wout * dL/dy
+        const float* alast = acts + (int64_t)(sh.in + (nh - 1) * Wd) * n;
+        float* dlast = dl + (int64_t)((nh - 1) * Wd) * n;
+        for (int e = threadIdx.x; e < kTileF * kTileS; e += blockDim.x) {
+            const int o = e / kTileS, sidx = e % kTileS;
+            const int64_t i = t0 + sidx;
+            float d = 0.0f;
+            if (o < Wd && i < n) {
+                const float g = gy[i];
+                d = alast[(int64_t)o * n + i] > 0.0f ? wout[o] * g : 0.0f;
+                dlast[(int64_t)o * n + i] = d;
+                if (o == 0) dl[(int64_t)(nh * Wd) * n + i] = g;
+            }
+            T0[e] = d;
+        }
+        __syncthreads();
+        float* src = T0;
+        float* dst = T1;
+        for (int j = nh - 1; j >= 0; --j) {
+            const int fi = j == 0 ? sh.in : Wd;
+            float acc[8][4] = {};
+            tile_gemm(src, Wk + j * kTileF * kTileF, Wd, acc);  // p[c][s] = sum_o W_j[o][c] delta_j[o][s]
 #pragma unroll
-            for (int c = 0; c < 64; ++c) p[c] = 0.0f;
-#pragma unroll 2
-            for (int o = 0; o < W; ++o) {
-                const float dv = dj[(int64_t)o * n];
-                const float4* row = reinterpret_cast<const float4*>(Wr + o * fi4);
+            for (int u = 0; u < 8; ++u) {
+                const int c = 8 * to + u;
+                if (j > 0) {
+                    const float* arow = acts + (int64_t)(sh.in + (j - 1) * Wd + c) * n;
+                    float* drow = dl + (int64_t)((j - 1) * Wd + c) * n;
+                    float r[4];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    if (4 * q < fi4) {
-                        const float4 w = row[q];
-                        p[4 * q + 0] = fmaf(w.x, dv, p[4 * q + 0]);
-                        p[4 * q + 1] = fmaf(w.y, dv, p[4 * q + 1]);
-                        p[4 * q + 2] = fmaf(w.z, dv, p[4 * q + 2]);
-                        p[4 * q + 3] = fmaf(w.w, dv, p[4 * q + 3]);
+                    for (int v = 0; v < 4; ++v) {
+                        const int64_t i = t0 + 4 * ts + v;
+                        r[v] = (c < Wd && i < n && arow[i] > 0.0f) ? acc[u][v] : 0.0f;
+                        if (c < Wd && i < n) drow[i] = r[v];
+                    }
+                    *reinterpret_cast<float4*>(dst + c * kTileS + 4 * ts) = make_float4(r[0], r[1], r[2], r[3]);
+                } else if (c < fi) {
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const int64_t i = t0 + 4 * ts + v;
+                        if (i < n) denc[(int64_t)c * n + i] = acc[u][v];
                     }
                 }
             }
-            if (j > 0) {
-                const float* aj = acts + (int64_t)(sh.in + (j - 1) * W) * n + i;
-                float* dn = dl + (int64_t)((j - 1) * W) * n + i;
-#pragma unroll
-                for (int c = 0; c < 64; ++c)
-                    if (c < W) dn[(int64_t)c * n] = (aj[(int64_t)c * n] > 0.0f) ? p[c] : 0.0f;
-            } else {
-#pragma unroll
-                for (int c = 0; c < 64; ++c)
-                    if (c < fi) denc[(int64_t)c * n + i] = p[c];
-            }
+            __syncthreads();
+            float* t = src; src = dst; dst = t;
         }
     }
 }
@@ -443,8 +472,10 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
     const size_t wpart_off = ((size_t)nb * 8 + 63) / 64 * 64;  // fixed before nb shrinks to the grid used
     float* wpart = (float*)((char*)m->s_partial.p + wpart_off);
     const float* Pm = m->param + m->n_table;
-    const GLayout GL = g_layout(sh);
-    const int gsmem = GL.floats * 4;
+    const int tsmem = tile_smem_floats(sh.nh) * 4;
+    // resident blocks only: each stages the weights once and then walks its share of the tiles
+    const int tile_grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + kTileS - 1) / kTileS,
+                                                                       (int64_t)num_sms() * std::max(1, (227 * 1024) / tsmem)));
 
     // forward: encoding + MLP (bf16 form: one tensor-core kernel writes the same activations)
     if (m->shadow) {
@@ -462,16 +493,17 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
             default: return set_error(FHASH_EINVAL, "F=%d unsupported", F);
         }
         FH_CUDA(cudaGetLastError());
-        FH_CUDA(cudaFuncSetAttribute((const void*)k_mlp_fwd_g, cudaFuncAttributeMaxDynamicSharedMemorySize, gsmem));
-        k_mlp_fwd_g<<<nb, 128, gsmem, st>>>(sh, Pm, target, n, 2.0f / (float)n, acts, gy, lpart);
+        FH_CUDA(cudaFuncSetAttribute((const void*)k_mlp_fwd_t, cudaFuncAttributeMaxDynamicSharedMemorySize, tsmem));
+        nb = std::min(nb, tile_grid);  // one loss partial per block
+        k_mlp_fwd_t<<<nb, 256, tsmem, st>>>(sh, Pm, target, n, 2.0f / (float)n, acts, gy, lpart);
         FH_CUDA(cudaGetLastError());
     }
     k_loss2<<<1, 256, 0, st>>>(lpart, nb, n, loss_dev);
     FH_CUDA(cudaGetLastError());
     // backward: MLP data path, table scatter, weight gradients
-    const int bb = (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, (int64_t)num_sms() * 8));
-    FH_CUDA(cudaFuncSetAttribute((const void*)k_mlp_bwd_g, cudaFuncAttributeMaxDynamicSharedMemorySize, gsmem));
-    k_mlp_bwd_g<<<bb, 128, gsmem, st>>>(sh, Pm, n, acts, gy, dl, denc);
+    const int bb = tile_grid;
+    FH_CUDA(cudaFuncSetAttribute((const void*)k_mlp_bwd_t, cudaFuncAttributeMaxDynamicSharedMemorySize, tsmem));
+    k_mlp_bwd_t<<<bb, 256, tsmem, st>>>(sh, Pm, n, acts, gy, dl, denc);
     FH_CUDA(cudaGetLastError());
     switch (F) {
         case 1: FH_CUDA(scatter_launch<1>(m, coords, n, denc, n, 1, st)); break;

@@ -116,7 +116,8 @@ def test_fullsize_finite_differences(large):
     against the GPU's analytic gradient on 48 touched table entries across the levels and 16 MLP
     parameters.  The loss is piecewise quadratic in each parameter, so the quotient is exact up to
     float32 rounding unless a ReLU flips inside +-h: a point whose quotients at h and h/10 disagree
-    by more than 1% is dropped (at least 48 of the 64 must be checked).  h = 1e-2 for table entries
+    by more than 5% is dropped (at least 48 of the 64 must be checked; at h/10 a table entry moves the
+    outputs of the few samples that see it by about 1e-5, so float32 rounding alone gives about 1%).  h = 1e-2 for table entries
     (only a few samples see them, so a larger step keeps float32 rounding of the outputs small) and
     1e-3 for MLP parameters.  Bound: 2% relative."""
     info, model = large["info"], large["model"]
@@ -156,7 +157,7 @@ def test_fullsize_finite_differences(large):
             vp, vm = float(np.float32(v0 + h)), float(np.float32(v0 - h))
             fd.append((L(off, vp) - L(off, vm)) / (vp - vm))
         fh().fhash_write_state(model, fh().STATE_PARAM, off, np.array([v0], np.float32))
-        if abs(fd[0] - fd[1]) > 1e-2 * max(abs(fd[0]), 1e-12):
+        if abs(fd[0] - fd[1]) > 5e-2 * max(abs(fd[0]), 1e-12):
             continue  # a ReLU kink inside +-h
         assert abs(fd[0] - gr) <= 2e-2 * abs(fd[0]) + 1e-12, (off, fd, gr)
         checked += 1
