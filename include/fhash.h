@@ -202,8 +202,9 @@ fhash_status fhash_encode_backward(fhash_model* model, const float* coords, cons
                                    fhash_stream stream);
 
 /*
- * How fhash_forward, fhash_render and fhash_decode evaluate FHASH_BF16 models (float32 models have
- * one path).  FUSED: one kernel encodes each 128-sample tile into shared memory and runs the MLP on
+ * No counterpart in the paper (an implementation choice of the bf16 precision form): how
+ * fhash_forward, fhash_render and fhash_decode evaluate FHASH_BF16 models (float32 models have one
+ * path).  FUSED: one kernel encodes each 128-sample tile into shared memory and runs the MLP on
  * it.  SPLIT: per chunk of up to 2^20 samples, one kernel writes the bf16 encoding rows and a second
  * one runs the MLP on the tensor cores, fed by TMA from those rows.  Both give bit-identical outputs;
  * they differ only in speed.  AUTO (the default) takes FUSED, the faster of the two on GB300 at every

@@ -189,6 +189,7 @@ __global__ void __launch_bounds__(256) k_mlp_fwd_t(const __grid_constant__ MlpSh
         __syncthreads();
         float* src = T0;
         float* dst = T1;
+        const bool vec = (n & 3) == 0 && t0 + kTileS <= n;  // whole tile, 16-byte aligned rows
         for (int j = 0; j < nh; ++j) {
             float acc[8][4];
 #pragma unroll
@@ -205,9 +206,14 @@ __global__ void __launch_bounds__(256) k_mlp_fwd_t(const __grid_constant__ MlpSh
                 for (int v = 0; v < 4; ++v) r[v] = fmaxf(acc[u][v], 0.0f);
                 *reinterpret_cast<float4*>(dst + o * kTileS + 4 * ts) = make_float4(r[0], r[1], r[2], r[3]);
                 if (o < Wd) {
+                    float* a4 = arow + (int64_t)o * n + t0 + 4 * ts;
+                    if (vec) {
+                        *reinterpret_cast<float4*>(a4) = make_float4(r[0], r[1], r[2], r[3]);
+                    } else {
 #pragma unroll
-                    for (int v = 0; v < 4; ++v)
-                        if (t0 + 4 * ts + v < n) arow[(int64_t)o * n + t0 + 4 * ts + v] = r[v];
+                        for (int v = 0; v < 4; ++v)
+                            if (t0 + 4 * ts + v < n) a4[v] = r[v];
+                    }
                 }
             }
             __syncthreads();
@@ -260,6 +266,7 @@ __global__ void __launch_bounds__(256) k_mlp_bwd_t(const __grid_constant__ MlpSh
         __syncthreads();
         float* src = T0;
         float* dst = T1;
+        const bool vec = (n & 3) == 0 && t0 + kTileS <= n;  // whole tile, 16-byte aligned rows
         for (int j = nh - 1; j >= 0; --j) {
             const int fi = j == 0 ? sh.in : Wd;
             float acc[8][4] = {};
@@ -267,22 +274,35 @@ __global__ void __launch_bounds__(256) k_mlp_bwd_t(const __grid_constant__ MlpSh
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int c = 8 * to + u;
+                const int64_t i0 = t0 + 4 * ts;
                 if (j > 0) {
                     const float* arow = acts + (int64_t)(sh.in + (j - 1) * Wd + c) * n;
                     float* drow = dl + (int64_t)((j - 1) * Wd + c) * n;
-                    float r[4];
+                    float r[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                    if (c < Wd && vec) {
+                        const float4 a = *reinterpret_cast<const float4*>(arow + i0);
+                        r[0] = a.x > 0.0f ? acc[u][0] : 0.0f;
+                        r[1] = a.y > 0.0f ? acc[u][1] : 0.0f;
+                        r[2] = a.z > 0.0f ? acc[u][2] : 0.0f;
+                        r[3] = a.w > 0.0f ? acc[u][3] : 0.0f;
+                        *reinterpret_cast<float4*>(drow + i0) = make_float4(r[0], r[1], r[2], r[3]);
+                    } else if (c < Wd) {
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        const int64_t i = t0 + 4 * ts + v;
-                        r[v] = (c < Wd && i < n && arow[i] > 0.0f) ? acc[u][v] : 0.0f;
-                        if (c < Wd && i < n) drow[i] = r[v];
+                        for (int v = 0; v < 4; ++v) {
+                            if (i0 + v >= n) continue;
+                            r[v] = arow[i0 + v] > 0.0f ? acc[u][v] : 0.0f;
+                            drow[i0 + v] = r[v];
+                        }
                     }
                     *reinterpret_cast<float4*>(dst + c * kTileS + 4 * ts) = make_float4(r[0], r[1], r[2], r[3]);
                 } else if (c < fi) {
+                    float* e4 = denc + (int64_t)c * n + i0;
+                    if (vec) {
+                        *reinterpret_cast<float4*>(e4) = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+                    } else {
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        const int64_t i = t0 + 4 * ts + v;
-                        if (i < n) denc[(int64_t)c * n + i] = acc[u][v];
+                        for (int v = 0; v < 4; ++v)
+                            if (i0 + v < n) e4[v] = acc[u][v];
                     }
                 }
             }
