@@ -88,3 +88,22 @@ def test_coreset_training(small):
             fh().fhash_coreset_train_step(model, 11, epoch, b, B, hp, loss)
     assert loss[0] < 0.5 * first, (first, loss[0])
     fh().fhash_check(model)
+
+
+def test_coreset_without_mask_covers_every_voxel():
+    # no mask: the feature is the whole volume, so the coreset is every voxel of every key frame
+    dims = (9, 5, 7, 4)
+    w = dict(W, dims=dims, schedule=dict(mode="explicit", res=[[3, 3, 3, 2], [9, 5, 7, 4]]))
+    model = build(w, mask=None, dims=dims)
+    vol = np.arange(np.prod(dims[::-1]), dtype=np.float32).reshape(dims[::-1])
+    keys = [1, 3]
+    N = fh().fhash_coreset_build(model, vol, keys)
+    assert N == 9 * 5 * 7 * len(keys)
+    c = torch().empty((N, 4), dtype=torch().float32, device="cuda")
+    t = torch().empty(N, dtype=torch().float32, device="cuda")
+    assert fh().fhash_coreset_batch(model, 5, 0, 0, N, c, t) == N
+    m = np.ones(dims[::-1], np.uint8)
+    ents, labels, lo, size = coreset.build(m, vol, keys)
+    rc, rt = coreset.batch(ents, labels, lo, size, dims[3], 5, 0, 0, N)
+    assert np.array_equal(c.cpu().numpy(), rc) and np.array_equal(t.cpu().numpy(), rt)
+    assert np.array_equal(np.sort(t.cpu().numpy()), np.sort(vol[keys].ravel()))
