@@ -163,3 +163,57 @@ def test_fullsize_finite_differences(large):
         checked += 1
     assert checked >= 48, checked
     fh().fhash_check(model)
+
+
+def test_fullsize_render_and_decode(large):
+    """The ARM renderer and the time-slice decode on a model of the full bench shape (16 levels to
+    256^3 x 64, F=2, MLP 2x64, 3.56e9 parameters), in the launch configuration the serving leg uses:
+    a 32 x 24 image through fhash_render and a 256^3 decode at fractional t, against the oracle on
+    the same parameters (the library's initial tables, U(-0.5, 0.5), and MLP from its documented
+    SplitMix64 streams; output bias 0.45).  Tolerances as on the small workload: composited sample
+    counts equal on >= 99.9% of pixels, matched pixels within 2e-4, PSNR >= 60 dB; decode values on
+    3000 sampled grid points within 1e-4 x max(|o|, RMS(o))."""
+    from oracle import render
+    nx, ny, nz, nt = W["dims"]
+    seed = 17
+    model = fh().fhash_build(nx, ny, nz, nt, mask=large["mask"], schedule=fh().make_schedule(**W["schedule"]),
+                             F=W["F"], mlp_hidden_layers=W["hidden"], mlp_width=W["width"], seed=seed, init_range=0.5)
+    info = fh().fhash_get_info(model)
+    lv, b, F, dims = info["res"], info["base"], info["F"], info["mlp_dims"]
+    p = rng.init_mlp(seed, dims).astype(np.float64)
+    p[-1] = 0.45
+    fh().fhash_write_state(model, fh().STATE_PARAM, info["n_table_params"] + info["n_mlp_params"] - 1,
+                           np.array([0.45], np.float32))
+    table = rng.InitTable(seed, F, float(np.float32(0.5)))
+    ev = render.model_eval_fn(lv, b, table, p, dims)
+
+    if "occ" not in large:
+        d = index.dilate(large["mask"])
+        large["occ"] = index.occupancy(d, info["fbb_lo"], info["fbb_size"])
+    w, h, t = 32, 24, np.float32(0.41)
+    cam = synth.camera(synth.sphere_eye(8, 2), w, h)
+    tf = synth.transfer_function(0.5)
+    rgba = torch().empty((h, w, 4), dtype=torch().float32, device="cuda")
+    cnt = torch().empty((h, w), dtype=torch().int32, device="cuda")
+    fh().fhash_render(model, cam, float(t), to_dev(tf), w, h, rgba, cnt)
+    img, cnt = rgba.cpu().numpy(), cnt.cpu().numpy()
+    ref, rcnt = render.render(ev, cam, w, h, info["fbb_size"], large["occ"], t, tf)
+    same = cnt == rcnt
+    assert rcnt.sum() > 0 and same.mean() >= 0.999, (same.mean(), int((~same).sum()))
+    assert np.abs(img[same] - ref[same]).max() <= 2e-4
+    mse = np.mean((img - ref) ** 2)
+    assert mse == 0 or 10 * np.log10(1.0 / mse) >= 60
+
+    up, tq = 1, np.float32(0.37)
+    ddims = fh().fhash_decode_dims(model, up)
+    out = torch().empty((ddims[2], ddims[1], ddims[0]), dtype=torch().float32, device="cuda")
+    fh().fhash_decode(model, float(tq), up, out)
+    got = out.cpu().numpy().ravel()
+    u, shape = render.decode_coords(info["fbb_size"], up, tq)
+    assert list(shape) == [ddims[2], ddims[1], ddims[0]]
+    pick = np.random.default_rng(2).choice(u.shape[0], 3000, replace=False)
+    refd = ev(u[pick])
+    tol = 1e-4 * np.maximum(np.abs(refd), np.sqrt(np.mean(refd ** 2)))
+    assert (np.abs(got[pick] - refd) <= tol).all(), np.abs(got[pick] - refd).max()
+    fh().fhash_check(model)
+    del model
