@@ -3,7 +3,8 @@
 //   k_encode_rows_bf16  one thread per (level, sample): 16 gathers from the bf16 shadow tables and the
 //                       quadrilinear interpolation in float32 (Section 3.2.4, Eqs. 9-12), stored as F bf16
 //                       values of row s of an [n][E] bf16 buffer (E = 32 or 64 columns, zero beyond L*F).
-//                       It holds no shared memory or TMEM, so it runs at full occupancy.
+//                       It holds no shared memory or TMEM, so it runs at full occupancy; blocks
+//                       interleave the levels.
 //   k_mlp_tc            the MLP on the tensor cores, fed by TMA.  128-row boxes of the encoding buffer
 //                       (64-byte swizzle for E = 32, 128-byte for E = 64) arrive in an S-stage mbarrier
 //                       ring.  Per tile, the layer-0 MMAs read the box, each hidden epilogue writes a bf16
@@ -30,10 +31,10 @@ __global__ void __launch_bounds__(256) k_encode_rows_bf16(const __grid_constant_
                                                           const __nv_bfloat16* __restrict__ T,
                                                           const float* __restrict__ coords, int64_t n, int E,
                                                           __nv_bfloat16* __restrict__ enc) {
-    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= n * lv.L) return;
-    const int l = (int)(idx / n);
-    const int64_t s = idx - (int64_t)l * n;
+    // block b serves level b % L, so resident blocks mix L2-resident and HBM-resident levels
+    const int l = (int)(blockIdx.x % (unsigned)lv.L);
+    const int64_t s = (int64_t)(blockIdx.x / (unsigned)lv.L) * blockDim.x + threadIdx.x;
+    if (s >= n) return;
     Corners k = corners(lv.lv[l], load_coord(coords, s));
     float o[F];
     interp_level_bf16<F>(T, k, o);
@@ -290,7 +291,7 @@ fhash_status launch_forward_split(fhash_model* m, const float* coords, int64_t n
     const int L = m->lv.L;
     for (int64_t c0 = 0; c0 < n; c0 += chunk) {
         const int64_t cnt = std::min(chunk, n - c0);
-        const unsigned g = (unsigned)((cnt * L + 255) / 256);
+        const unsigned g = (unsigned)(((cnt + 255) / 256) * L);
         const float* c = coords + 4 * c0;
         switch (m->lv.F) {
             case 1: k_encode_rows_bf16<1><<<g, 256, 0, st>>>(m->lv, m->shadow, c, cnt, E, enc); break;
