@@ -37,6 +37,22 @@ ADAM_SMALL_CASE = {"workload": "advect-128^3x32", "bytes_per_param_measured": (4
 ADAM_SMALL_CASE["ratio"] = ADAM_SMALL_CASE["bytes_per_param_measured"] / ADAM_SMALL_CASE["bytes_per_param_algorithmic"]
 
 
+def max_over_ranks(dist, x, device="cuda"):
+    """The slowest rank's value, on every rank (x itself without a process group).  Replicas run the
+    same work on their own GPU, so the job's time is the maximum over ranks."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, seconds):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def _touched_fraction(fh, model, info, coords, tgt, hp, chunk=1 << 28):
     """One more training step, untimed: the fraction of 4-parameter gradient groups that are non-zero
     before its Adam update."""
@@ -671,11 +687,7 @@ def main():
     e_end.record(st)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    elapsed = e_start.elapsed_time(e_end) / 1e3
-    if dist:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(dist, e_start.elapsed_time(e_end) / 1e3)
     grads_ms = float(np.mean([ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]))
     adam_ms = float(np.mean([ev[k][1].elapsed_time(ev[k][2]) for k in range(K)]))
     losses = loss_d.cpu().numpy()
@@ -697,11 +709,7 @@ def main():
     for k in range(K):
         fh.fhash_train_step(model, pin_c[k].numpy(), pin_t[k].numpy(), hp, lh)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t1
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(dist, time.perf_counter() - t1)
     fh.fhash_check(model)
 
     serve = None
@@ -716,7 +724,7 @@ def main():
     adam_bpp = (30.0 if args.dtype == "bf16" else 28.0) + 4.0 * touched
     adam_bytes = adam_bpp * n_params
     achieved = adam_bytes / (adam_ms / 1e3) / 1e9
-    value = world * B * K / elapsed
+    value = job_rate(world, B * K, elapsed)
 
     out = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -740,7 +748,7 @@ def main():
                      "peak_source": peak_kind, "bytes_per_launch": adam_bytes, "bytes_per_param": adam_bpp,
                      "grad_groups_touched": touched},
         "clocks": clk,
-        "e2e": {"value": world * B * K / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": B * 20,
+        "e2e": {"value": job_rate(world, B * K, e2e_s), "unit": "samples/s", "h2d_bytes_per_step": B * 20,
                 "d2h_bytes_per_step": 8},
         "loss_first_last": [float(losses[0]), float(losses[-1])],
         "setup_s": setup_s,
