@@ -28,13 +28,15 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// Bounded wait: returns false if the phase did not complete within `limit_ns` (default 2 s).
+// Bounded wait: returns false if the phase did not complete within `limit_ns` (default 2 s).  The
+// clock is read every 256 polls only, so a completed phase is seen without a timer read in between.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = 2000000000ull) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
-    while (!mbar_try_wait(bar, parity))
-        if (globaltimer_ns() - t0 > limit_ns) return false;
-    return true;
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 0u && globaltimer_ns() - t0 > limit_ns) return false;
+    }
 }
 
 // Plain arrive (count 1) on an mbarrier.
@@ -47,14 +49,14 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parit
                                                    uint64_t limit_ns = 2000000000ull) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
-    while (!mbar_try_wait(bar, parity)) {
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
         if (*abort) return false;
-        if (globaltimer_ns() - t0 > limit_ns) {
+        if ((it & 255u) == 0u && globaltimer_ns() - t0 > limit_ns) {
             *abort = 1;
             return false;
         }
     }
-    return true;
 }
 
 // ---- proxy / ordering fences
