@@ -37,6 +37,12 @@ ADAM_SMALL_CASE = {"workload": "advect-128^3x32", "bytes_per_param_measured": (4
 ADAM_SMALL_CASE["ratio"] = ADAM_SMALL_CASE["bytes_per_param_measured"] / ADAM_SMALL_CASE["bytes_per_param_algorithmic"]
 
 
+def _layout(args):
+    """Row layout of the tables: brick (4x4x4 bricks per time slice, a linearisation Section 3.2.3
+    allows; the bench's default because it gathers faster) or linear (Eq. 9, the library's default)."""
+    return {"linear": 0, "brick": 1}[getattr(args, "layout", "brick")]
+
+
 def max_over_ranks(dist, x, device="cuda"):
     """The slowest rank's value, on every rank (x itself without a process group).  Replicas run the
     same work on their own GPU, so the job's time is the maximum over ranks."""
@@ -209,7 +215,7 @@ def serving_leg(args, w, model, info, field, mask, rank):
     nx, ny, nz, nt = w["dims"]
     m16 = fh.fhash_build(nx, ny, nz, nt, mask=mask, schedule=fh.make_schedule(**w["schedule"]), F=w["F"],
                          dtype=fh.BF16, mlp_hidden_layers=w["hidden"], mlp_width=w["width"], seed=1 + rank,
-                         init_range=w["init_range"])
+                         init_range=w["init_range"], layout=_layout(args))
     n_all = info["n_table_params"] + info["n_mlp_params"]
     _copy_params(model, m16, n_all)
 
@@ -281,11 +287,12 @@ def serving_leg(args, w, model, info, field, mask, rank):
 
 
 # ------------------------------------------------------------------ suites beyond the default line
-def _build(w, dtype, seed, mask):
+def _build(w, dtype, seed, mask, layout=0):
     import paper_2507_03836_gb300 as fh
     nx, ny, nz, nt = w["dims"]
     m = fh.fhash_build(nx, ny, nz, nt, mask=mask, schedule=fh.make_schedule(**w["schedule"]), F=w["F"], dtype=dtype,
-                       mlp_hidden_layers=w["hidden"], mlp_width=w["width"], seed=seed, init_range=w["init_range"])
+                       mlp_hidden_layers=w["hidden"], mlp_width=w["width"], seed=seed, init_range=w["init_range"],
+                       layout=layout)
     return m, fh.fhash_get_info(m)
 
 
@@ -339,7 +346,7 @@ def suite_precision(args):
     field, mask = workloads.make_field_and_mask(w)
     res = {"suite": "precision", "workload": w["name"], "steps": args.steps, "batch": w["batch"]}
     for name, dt in (("fp32", fh.FP32), ("bf16", fh.BF16)):
-        model, info = _build(w, dt, 5, mask)
+        model, info = _build(w, dt, 5, mask, _layout(args))
         batches = _batches(w, info, field, args.steps + 3, 50_000)
         ms = _train(model, batches, w["adam"])
         p, e = _psnr(model, info, field)
@@ -368,7 +375,7 @@ def suite_coreset(args):
     hp = w["adam"]
     B, K, W0 = w["batch"], args.steps, 3
     res = {"suite": "coreset", "workload": w["name"], "key_frames": keys, "batch": B, "steps": K}
-    model, info = _build(w, fh.FP32, 5, mask)
+    model, info = _build(w, fh.FP32, 5, mask, _layout(args))
     torch.cuda.synchronize()
     t1 = time.time()
     N = fh.fhash_coreset_build(model, field, keys)
@@ -404,7 +411,7 @@ def suite_coreset(args):
     res["coreset_train"]["psnr_feature_db"] = feature_psnr(model)
     res["coreset_train"]["psnr_uniform_db"] = _psnr(model, info, field)[0]
     del model
-    uni, info = _build(w, fh.FP32, 5, mask)
+    uni, info = _build(w, fh.FP32, 5, mask, _layout(args))
     ms = _train(uni, _batches(w, info, field, K + W0, 60_000), hp, warmup=W0)
     res["uniform_train"] = {"ms_per_step": ms, "samples_s": B / ms * 1e3, "psnr_feature_db": feature_psnr(uni),
                             "psnr_uniform_db": _psnr(uni, info, field)[0]}
@@ -423,11 +430,11 @@ def suite_forward(args):
     from synth import workloads
     w = dict(_workload(args.workload), init_range=0.5)
     field, mask = workloads.make_field_and_mask(w)
-    model, info = _build(w, fh.BF16, 1, mask)
+    model, info = _build(w, fh.BF16, 1, mask, _layout(args))
     n = args.forward_points
     c = torch.from_numpy(synth.coords(5, n)).cuda()
     out = torch.empty(n, dtype=torch.float32, device="cuda")
-    res = {"suite": "forward", "workload": w["name"], "points": n, "steps": args.steps}
+    res = {"suite": "forward", "workload": w["name"], "layout": args.layout, "points": n, "steps": args.steps}
     sums = {}
     st = torch.cuda.current_stream()
     for name in args.forward_paths.split(","):
@@ -558,9 +565,9 @@ def suite_serve(args):
     w = workloads.SHELL
     t0 = time.time()
     field, mask = workloads.make_field_and_mask(w)
-    m32, info = _build(w, fh.FP32, 6, mask)
+    m32, info = _build(w, fh.FP32, 6, mask, _layout(args))
     ms = _train(m32, _batches(w, info, field, args.steps + 3, 60_000), w["adam"])
-    m16, _ = _build(w, fh.BF16, 6, mask)
+    m16, _ = _build(w, fh.BF16, 6, mask, _layout(args))
     _copy_params(m32, m16, info["n_table_params"] + info["n_mlp_params"])
     tf = torch.from_numpy(synth.transfer_function(0.5)).cuda()
     res = {"suite": "serve", "workload": w["name"], "train_steps": args.steps + 3, "train_ms_per_step": ms,
@@ -584,7 +591,7 @@ def suite_mixed(args):
     for w, dt, seed in ((workloads.LARGE, fh.FP32, 7), (workloads.FRONT, fh.BF16, 8),
                         (dict(workloads.LARGE, seed=4, name="advect2-256^3x64"), fh.BF16, 9)):
         field, mask = workloads.make_field_and_mask(w)
-        m, info = _build(w, dt, seed, mask)
+        m, info = _build(w, dt, seed, mask, _layout(args))
         _train(m, _batches(w, info, field, args.steps + 3, 70_000 + seed * 1000), w["adam"])
         models.append(m)
         infos.append((w["name"], info))
@@ -611,6 +618,9 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving and precision legs")
     ap.add_argument("--serve-requests", type=int, default=60)
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--layout", default="brick", choices=["linear", "brick"],
+                    help="table row layout: 4x4x4 bricks per time slice (the default: the faster F-Hash "
+                         "linearisation on this GPU), or Eq. 9")
     ap.add_argument("--forward-points", type=int, default=1 << 22, help="--suite forward: points per call")
     ap.add_argument("--forward-paths", default="fused,split", help="--suite forward: paths to time")
     ap.add_argument("--suite", default="train", choices=["train", "precision", "serve", "mixed", "coreset", "forward", "peaks"],
@@ -645,7 +655,7 @@ def main():
     model = fh.fhash_build(nx, ny, nz, nt, mask=mask, schedule=fh.make_schedule(**w["schedule"]), F=w["F"],
                            dtype=fh.BF16 if args.dtype == "bf16" else fh.FP32,
                            mlp_hidden_layers=w["hidden"], mlp_width=w["width"], seed=1 + rank,
-                           init_range=w["init_range"])
+                           init_range=w["init_range"], layout=_layout(args))
     mask_for_bf16 = mask if not args.no_serve else None
     del mask
     info = fh.fhash_get_info(model)
@@ -731,6 +741,7 @@ def main():
         "ms_per_step": elapsed / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.dtype, "data": "synthetic",
         "config": {"workload": w["name"], "global_batch": B * world, "levels": len(info["res"]), "F": info["F"],
+                   "layout": args.layout,
                    "mlp": info["mlp_dims"], "table_params": info["n_table_params"],
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (%.1f GB of training state streamed per step)" % (adam_bytes / 1e9)},

@@ -104,6 +104,16 @@ typedef struct {
  *    with `seed`, top 24 bits as U in [0,1), value = (float)(lo + (hi - lo) * U) in double; MLP
  *    layer k uses streams 300 + 2k (W) and 301 + 2k (b).
  */
+/* Row order of a level's vertices.  LINEAR is Eq. 9: t*Rx*Ry*Rz + z*Rx*Ry + y*Rx + x.  BRICK is a
+ * locality-preserving linearisation, which Section 3.2.3 allows in place of Eq. 9: each time slice is
+ * cut into 4x4x4 spatial bricks (narrower at the high end of an axis when R is not a multiple of 4),
+ * bricks in (bz, by, bx) order and vertices inside a brick in (iz, iy, ix) order.  With b = v / 4,
+ * i = v % 4 and w(b) = min(4, R - 4b) per axis the row is
+ *   t*Rx*Ry*Rz + 4*bz*Rx*Ry + wz*4*by*Rx + wz*wy*4*bx + (iz*wy + iy)*wx + ix,
+ * a bijection onto [0, Rx*Ry*Rz*Rt) like Eq. 9.  The 16 corners of a cell then lie in 1 to 8 bricks
+ * per time slice, which cuts the random memory accesses of the gathers at HBM-resident levels. */
+enum { FHASH_LAYOUT_LINEAR = 0, FHASH_LAYOUT_BRICK = 1 };
+
 typedef struct {
     int64_t nx, ny, nz, nt;
     const uint8_t* mask;
@@ -114,6 +124,7 @@ typedef struct {
     int32_t mlp_width;
     uint64_t seed;
     float init_range;
+    int32_t layout;  /* FHASH_LAYOUT_LINEAR (Eq. 9, the default) or FHASH_LAYOUT_BRICK */
 } fhash_build_desc;
 
 /* Read-only description of a built model. */

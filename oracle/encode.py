@@ -35,13 +35,28 @@ def locate(u, R):
     return c, c1, w
 
 
-def fhash(t, x, y, z, R):
-    """Eq. 9: F-Hash^l(t, x, y, z) = t*Rx*Ry*Rz + z*Rx*Ry + y*Rx + x (row within level l)."""
+def fhash(t, x, y, z, R, layout="linear"):
+    """Row of vertex (t, x, y, z) within level l.
+
+    "linear" is Eq. 9: F-Hash^l(t, x, y, z) = t*Rx*Ry*Rz + z*Rx*Ry + y*Rx + x.
+    "brick" is the locality-preserving linearisation that Section 3.2.3 allows: each time slice is cut
+    into 4x4x4 spatial bricks (narrower at the high end of an axis when R is not a multiple of 4),
+    bricks in (bz, by, bx) order and vertices inside a brick in (iz, iy, ix) order.  With b = v // 4,
+    i = v % 4 and w(b) = min(4, R - 4b) per axis, the row is
+        t*Rx*Ry*Rz + 4 bz Rx Ry + wz 4 by Rx + wz wy 4 bx + (iz wy + iy) wx + ix,
+    a bijection onto [0, Rx*Ry*Rz*Rt) like Eq. 9 (no bucket is wasted)."""
     Rx, Ry, Rz = (np.int64(R[0]), np.int64(R[1]), np.int64(R[2]))
-    return t * (Rx * Ry * Rz) + z * (Rx * Ry) + y * Rx + x
+    if layout == "linear":
+        return t * (Rx * Ry * Rz) + z * (Rx * Ry) + y * Rx + x
+    x, y, z, t = (np.asarray(a, np.int64) for a in (x, y, z, t))
+    bx, by, bz = x // 4, y // 4, z // 4
+    ix, iy, iz = x % 4, y % 4, z % 4
+    wx, wy, wz = np.minimum(4, Rx - 4 * bx), np.minimum(4, Ry - 4 * by), np.minimum(4, Rz - 4 * bz)
+    return (t * (Rx * Ry * Rz) + 4 * bz * Rx * Ry + wz * 4 * by * Rx + wz * wy * 4 * bx
+            + (iz * wy + iy) * wx + ix)
 
 
-def level_corners(coords, R, base):
+def level_corners(coords, R, base, layout="linear"):
     """Rows [N][16] (int64, concatenated-table rows) and float64 weights [N][16] of one level."""
     coords = np.asarray(coords, np.float32)
     cx, cx1, wx = locate(coords[:, 0], R[0])
@@ -57,12 +72,12 @@ def level_corners(coords, R, base):
             for j, (yy, wj) in enumerate(((cy, 1.0 - wy), (cy1, wy))):
                 for i, (xx, wi) in enumerate(((cx, 1.0 - wx), (cx1, wx))):
                     c = i + 2 * j + 4 * k + 8 * s
-                    rows[:, c] = base + fhash(tt, xx, yy, zz, R)
+                    rows[:, c] = base + fhash(tt, xx, yy, zz, R, layout)
                     wts[:, c] = ws * wk * wj * wi
     return rows, wts
 
 
-def interpolate_level(coords, R, base, table):
+def interpolate_level(coords, R, base, table, layout="linear"):
     """Steps 3-4 for one level: Eqs. 10-11 (trilinear at t_Previous and t_Next), then Eq. 12."""
     coords = np.asarray(coords, np.float32)
     cx, cx1, wx = locate(coords[:, 0], R[0])
@@ -76,7 +91,7 @@ def interpolate_level(coords, R, base, table):
         for i, xx in ((0, cx), (1, cx1)):
             for j, yy in ((0, cy), (1, cy1)):
                 for k, zz in ((0, cz), (1, cz1)):
-                    Vijk = np.asarray(table[base + fhash(tt, xx, yy, zz, R)], np.float64)
+                    Vijk = np.asarray(table[base + fhash(tt, xx, yy, zz, R, layout)], np.float64)
                     acc = acc + Vijk * (x ** i * (1 - x) ** (1 - i)) * (y ** j * (1 - y) ** (1 - j)) \
                         * (z ** k * (1 - z) ** (1 - k))
         return acc
@@ -84,20 +99,20 @@ def interpolate_level(coords, R, base, table):
     return (1.0 - t) * V(tp) + t * V(tn)
 
 
-def encode(levels, level_bases, coords, table):
+def encode(levels, level_bases, coords, table, layout="linear"):
     """Concatenated encoding [N][L*F] float64; `table` is indexable by int64 row arrays and
     returns [n][F] values (a dense [rows][F] array, or any lazy equivalent)."""
-    parts = [interpolate_level(coords, R, b, table) for R, b in zip(levels, level_bases)]
+    parts = [interpolate_level(coords, R, b, table, layout) for R, b in zip(levels, level_bases)]
     return np.concatenate(parts, axis=1)
 
 
-def encode_backward(levels, level_bases, coords, d_enc, F):
+def encode_backward(levels, level_bases, coords, d_enc, F, layout="linear"):
     """Gradient of sum(d_enc * enc) with respect to the table: each of the 16 corner rows of every
     level receives weight * d_enc of that level (Eqs. 10-12 are linear in the table).
     Returns (unique rows int64, gradient [n_rows][F] float64)."""
     all_rows, all_vals = [], []
     for l, (R, b) in enumerate(zip(levels, level_bases)):
-        rows, wts = level_corners(coords, R, b)
+        rows, wts = level_corners(coords, R, b, layout)
         g = np.asarray(d_enc, np.float64)[:, l * F:(l + 1) * F]
         all_rows.append(rows.reshape(-1))
         all_vals.append((wts[:, :, None] * g[:, None, :]).reshape(-1, F))

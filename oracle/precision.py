@@ -21,10 +21,10 @@ def bf16_round(x):
     return np.where(np.isnan(f), np.nan, out)
 
 
-def forward_bf16(levels, level_bases, table, params, dims, coords):
+def forward_bf16(levels, level_bases, table, params, dims, coords, layout="linear"):
     """y [N] of the precision form: bf16 table values, quadrilinear interpolation (float64), then every
     layer on bf16 inputs and bf16 weights with float32 biases (ReLU after the hidden layers)."""
-    enc = encode.encode(levels, level_bases, coords, bf16_round(np.asarray(table, np.float32)))
+    enc = encode.encode(levels, level_bases, coords, bf16_round(np.asarray(table, np.float32)), layout)
     layers = mlp.unpack(params, dims)
     x = enc
     for k, (W, b) in enumerate(layers[:-1]):

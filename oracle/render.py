@@ -148,9 +148,9 @@ def render(model_eval, cam, width, height, fbb_size, occ, t_norm, tf):
     return img.reshape(height, width, 4), counts.reshape(height, width)
 
 
-def model_eval_fn(levels, level_bases, table, mlp_params, dims):
+def model_eval_fn(levels, level_bases, table, mlp_params, dims, layout="linear"):
     def f(u):
-        return mlp.forward(mlp_params, dims, encode.encode(levels, level_bases, u, table))[0]
+        return mlp.forward(mlp_params, dims, encode.encode(levels, level_bases, u, table, layout))[0]
     return f
 
 

@@ -30,13 +30,13 @@ class Model:
         return mlp.forward(self.mlp, self.dims, enc)[0]
 
 
-def loss_and_grads(levels, level_bases, F, dims, table, mlp_params, coords, targets):
+def loss_and_grads(levels, level_bases, F, dims, table, mlp_params, coords, targets, layout="linear"):
     """Returns (loss, y, MLP gradient, (rows, table gradient for those rows))."""
-    enc = encode.encode(levels, level_bases, coords, table)
+    enc = encode.encode(levels, level_bases, coords, table, layout)
     y, a, z = mlp.forward(mlp_params, dims, enc)
     L, g_y = mlp.mse(y, targets)
     g_mlp, d_enc = mlp.backward(mlp_params, dims, a, z, g_y)
-    rows, g_tab = encode.encode_backward(levels, level_bases, coords, d_enc, F)
+    rows, g_tab = encode.encode_backward(levels, level_bases, coords, d_enc, F, layout)
     return L, y, g_mlp, (rows, g_tab)
 
 

@@ -42,7 +42,7 @@ class fhash_build_desc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64), ("nt", ctypes.c_int64),
                 ("mask", ctypes.c_void_p), ("sched", fhash_schedule), ("F", ctypes.c_int32), ("dtype", ctypes.c_int32),
                 ("mlp_hidden_layers", ctypes.c_int32), ("mlp_width", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("init_range", ctypes.c_float)]
+                ("init_range", ctypes.c_float), ("layout", ctypes.c_int32)]
 
 
 class fhash_info(ctypes.Structure):
@@ -193,8 +193,11 @@ def make_schedule(mode="explicit", res=None, fold=2, levels_rule=LEVELS_MAX, n_l
     return s
 
 
+LAYOUT_LINEAR, LAYOUT_BRICK = 0, 1
+
+
 def fhash_build(nx, ny, nz, nt, mask=None, schedule=None, F=2, dtype=FP32, mlp_hidden_layers=2, mlp_width=64,
-                seed=0, init_range=1e-4, stream=None):
+                seed=0, init_range=1e-4, layout=LAYOUT_LINEAR, stream=None):
     """fhash_build: mask is a host numpy uint8 array [nt][nz][ny][nx] or None."""
     d = fhash_build_desc()
     d.nx, d.ny, d.nz, d.nt = int(nx), int(ny), int(nz), int(nt)
@@ -207,6 +210,7 @@ def fhash_build(nx, ny, nz, nt, mask=None, schedule=None, F=2, dtype=FP32, mlp_h
     d.F, d.dtype = int(F), int(dtype)
     d.mlp_hidden_layers, d.mlp_width = int(mlp_hidden_layers), int(mlp_width)
     d.seed, d.init_range = int(seed), float(init_range)
+    d.layout = int(layout)
     h = _vp()
     _ok(_lib.fhash_build(ctypes.byref(d), _stream(stream), ctypes.byref(h)))
     return Model(h.value)

@@ -39,14 +39,19 @@ __device__ __forceinline__ void load_row_bf16(const __nv_bfloat16* __restrict__ 
     }
 }
 
-template <int F>
+template <int F, int LAYOUT = -1>
 __device__ __forceinline__ void interp_level_bf16(const __nv_bfloat16* __restrict__ T, const Corners& k, float* out) {
     float v[16][F];
+    if (LAYOUT < 0 ? k.brick != 0 : LAYOUT == 1) {
 #pragma unroll
-    for (int c = 0; c < 16; c += 2) {
-        uint64_t r = k.r0 + ((c & 8) ? k.ot : 0ull) + ((c & 4) ? k.oz : 0u) + ((c & 2) ? k.oy : 0u);
-        load_row_bf16<F>(T, r, v[c]);
-        load_row_bf16<F>(T, r + k.ox, v[c + 1]);
+        for (int c = 0; c < 16; ++c) load_row_bf16<F>(T, corner_row<1>(k, c), v[c]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 16; c += 2) {
+            uint64_t r = k.r0 + ((c & 8) ? k.ot : 0ull) + ((c & 4) ? k.oz : 0u) + ((c & 2) ? k.oy : 0u);
+            load_row_bf16<F>(T, r, v[c]);
+            load_row_bf16<F>(T, r + k.ox, v[c + 1]);
+        }
     }
 #pragma unroll
     for (int f = 0; f < F; ++f) {
@@ -82,7 +87,7 @@ __device__ __forceinline__ void sts128(uint32_t a, uint32_t x, uint32_t y, uint3
 // Encodes one sample straight into its bf16 row t of the A tile (column l*F + f for level l, zeros
 // beyond L*F), without holding the whole encoding in registers; in training also stores the float32
 // encoding to the activation columns.
-template <int F, bool TRAIN>
+template <int F, bool TRAIN, int LAYOUT>
 __device__ __forceinline__ void encode_row_bf16(const Levels& lv, const __nv_bfloat16* __restrict__ T, float4 u,
                                                 uint8_t* tile, int t, float* acts, int64_t n) {
     const uint32_t rowa = tc::smem_addr(tile) + (t >> 3) * 1024 + (t & 7) * 128;
@@ -91,9 +96,9 @@ __device__ __forceinline__ void encode_row_bf16(const Levels& lv, const __nv_bfl
 #pragma unroll
     for (int l = 0; l < 64 / F; ++l) {
         if (l < lv.L) {
-            Corners k = corners(lv.lv[l], u);
+            Corners k = corners<LAYOUT>(lv.lv[l], u);
             float o[F];
-            interp_level_bf16<F>(T, k, o);
+            interp_level_bf16<F, LAYOUT>(T, k, o);
             if (TRAIN && acts) {
 #pragma unroll
                 for (int f = 0; f < F; ++f) acts[(int64_t)(l * F + f) * n] = o[f];

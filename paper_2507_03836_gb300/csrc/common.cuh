@@ -32,6 +32,7 @@ struct Level {
     uint32_t sy, sz;  // Rx, Rx*Ry
     uint64_t st;      // Rx*Ry*Rz
     uint64_t base;    // first row of the level
+    int32_t brick;    // row order inside a time slice: 0 = Eq. 9, 1 = 4x4x4 bricks (FHASH_LAYOUT_BRICK)
 };
 
 struct Levels {
@@ -119,14 +120,31 @@ __device__ __forceinline__ void cell(float u, int R, float Rm1, int& c, int& d1,
 }
 
 // Per-level corner geometry of one sample: base row (lower corner at t_Previous), the row offsets of
-// the upper corners on each axis, and the four axis fractions.
+// the upper corners on each axis, and the four axis fractions.  In the brick layout r0 is the first
+// row of the t_Previous slice, ot the slice stride or 0, ox/oy/oz the upper-corner steps (1 or 0) and
+// (cx, cy, cz) the lower cell corner; corner rows then come from brick_row3.
 struct Corners {
     uint64_t r0;
     uint32_t ox, oy, oz;
     uint64_t ot;
     float wx, wy, wz, wt;
+    uint32_t brick, cx, cy, cz, Rx, Ry, Rz;
 };
 
+// Row of vertex (x, y, z) inside a time slice in the brick layout (Section 3.2.3 allows other
+// linearisations than Eq. 9): 4x4x4 bricks in (bz, by, bx) order, vertices in (iz, iy, ix) order
+// inside a brick, bricks narrower at the high end of an axis (w = min(4, R - 4b)); a bijection onto
+// [0, Rx*Ry*Rz).  The build keeps Rx*Ry*Rz below 2^32.
+__device__ __forceinline__ uint32_t brick_row3(uint32_t x, uint32_t y, uint32_t z, uint32_t Rx, uint32_t Ry, uint32_t Rz) {
+    const uint32_t bx = x >> 2, by = y >> 2, bz = z >> 2;
+    const uint32_t wx = min(4u, Rx - 4u * bx), wy = min(4u, Ry - 4u * by), wz = min(4u, Rz - 4u * bz);
+    return 4u * bz * Rx * Ry + wz * (4u * by * Rx + wy * 4u * bx) + ((z & 3u) * wy + (y & 3u)) * wx + (x & 3u);
+}
+
+// LAYOUT: 0 = Eq. 9, 1 = bricks, -1 = read from the level (kernels over one level per thread take the
+// runtime form; kernels that walk all levels of a sample are instantiated per layout, so that no
+// branch sits between the gathers of consecutive levels).
+template <int LAYOUT = -1>
 __device__ __forceinline__ Corners corners(const Level& L, float4 u) {
     int cx, cy, cz, ct, dx, dy, dz, dt;
     Corners k;
@@ -134,12 +152,33 @@ __device__ __forceinline__ Corners corners(const Level& L, float4 u) {
     cell(u.y, L.R[1], L.Rm1[1], cy, dy, k.wy);
     cell(u.z, L.R[2], L.Rm1[2], cz, dz, k.wz);
     cell(u.w, L.R[3], L.Rm1[3], ct, dt, k.wt);
-    k.r0 = L.base + (uint64_t)ct * L.st + (uint64_t)cz * L.sz + (uint64_t)cy * L.sy + (uint64_t)cx;
-    k.ox = dx;
-    k.oy = dy ? L.sy : 0u;
-    k.oz = dz ? L.sz : 0u;
     k.ot = dt ? L.st : 0ull;
+    const bool brick = LAYOUT < 0 ? L.brick != 0 : LAYOUT == 1;
+    k.brick = brick ? 1u : 0u;
+    if (brick) {
+        k.r0 = L.base + (uint64_t)ct * L.st;
+        k.ox = dx; k.oy = dy; k.oz = dz;
+        k.cx = cx; k.cy = cy; k.cz = cz;
+        k.Rx = L.R[0]; k.Ry = L.R[1]; k.Rz = L.R[2];
+    } else {
+        k.r0 = L.base + (uint64_t)ct * L.st + (uint64_t)cz * L.sz + (uint64_t)cy * L.sy + (uint64_t)cx;
+        k.ox = dx;
+        k.oy = dy ? L.sy : 0u;
+        k.oz = dz ? L.sz : 0u;
+        k.cx = k.cy = k.cz = k.Rx = k.Ry = k.Rz = 0;
+    }
     return k;
+}
+
+// Row of corner c = i + 2j + 4k + 8s (i, j, k: upper corner on x, y, z; s = 1 for t_Next).
+template <int LAYOUT = -1>
+__device__ __forceinline__ uint64_t corner_row(const Corners& k, int c) {
+    const bool brick = LAYOUT < 0 ? k.brick != 0 : LAYOUT == 1;
+    if (brick)
+        return k.r0 + ((c & 8) ? k.ot : 0ull) +
+               brick_row3(k.cx + ((c & 1) ? k.ox : 0u), k.cy + ((c & 2) ? k.oy : 0u), k.cz + ((c & 4) ? k.oz : 0u),
+                          k.Rx, k.Ry, k.Rz);
+    return k.r0 + ((c & 8) ? k.ot : 0ull) + ((c & 4) ? k.oz : 0u) + ((c & 2) ? k.oy : 0u) + ((c & 1) ? k.ox : 0u);
 }
 
 __device__ __forceinline__ void raise_error(int* word, int code) {

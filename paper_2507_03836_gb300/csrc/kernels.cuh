@@ -29,14 +29,19 @@ __device__ __forceinline__ void load_row(const float* __restrict__ T, uint64_t r
 
 // Steps 3-4 of Section 3.2.4 for one level: the 16 look-ups, trilinear interpolation inside the cells
 // at t_Previous and t_Next (Eqs. 10-11) and the linear blend in time (Eq. 12).
-template <int F>
+template <int F, int LAYOUT = -1>
 __device__ __forceinline__ void interp_level(const float* __restrict__ T, const Corners& k, float* out) {
     float v[16][F];
+    if (LAYOUT < 0 ? k.brick != 0 : LAYOUT == 1) {
 #pragma unroll
-    for (int c = 0; c < 16; c += 2) {
-        uint64_t r = k.r0 + ((c & 8) ? k.ot : 0ull) + ((c & 4) ? k.oz : 0u) + ((c & 2) ? k.oy : 0u);
-        load_row<F>(T, r, v[c]);
-        load_row<F>(T, r + k.ox, v[c + 1]);
+        for (int c = 0; c < 16; ++c) load_row<F>(T, corner_row<1>(k, c), v[c]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 16; c += 2) {
+            uint64_t r = k.r0 + ((c & 8) ? k.ot : 0ull) + ((c & 4) ? k.oz : 0u) + ((c & 2) ? k.oy : 0u);
+            load_row<F>(T, r, v[c]);
+            load_row<F>(T, r + k.ox, v[c + 1]);
+        }
     }
 #pragma unroll
     for (int f = 0; f < F; ++f) {
@@ -66,9 +71,6 @@ __device__ __forceinline__ float corner_weight(const Corners& k, int c) {
     return ((e * d) * b) * a;
 }
 
-__device__ __forceinline__ uint64_t corner_row(const Corners& k, int c) {
-    return k.r0 + ((c & 8) ? k.ot : 0ull) + ((c & 4) ? k.oz : 0u) + ((c & 2) ? k.oy : 0u) + ((c & 1) ? k.ox : 0u);
-}
 
 __device__ __forceinline__ float4 load_coord(const float* __restrict__ coords, int64_t n) {
     return __ldg(reinterpret_cast<const float4*>(coords) + n);
@@ -166,12 +168,12 @@ __device__ __forceinline__ float layer_out(const float* __restrict__ w, const fl
 }
 
 // Encodes one sample into column x (x[(l*F + f) * TB]).
-template <int F>
+template <int F, int LAYOUT>
 __device__ __forceinline__ void encode_to_col(const Levels& lv, const float* __restrict__ T, float4 u, float* x) {
     for (int l = 0; l < lv.L; ++l) {
-        Corners k = corners(lv.lv[l], u);
+        Corners k = corners<LAYOUT>(lv.lv[l], u);
         float o[F];
-        interp_level<F>(T, k, o);
+        interp_level<F, LAYOUT>(T, k, o);
 #pragma unroll
         for (int f = 0; f < F; ++f) x[(l * F + f) * TB] = o[f];
     }
@@ -200,7 +202,7 @@ __device__ __forceinline__ float mlp_fwd_col(const MlpShape& sh, const MlpSmemLa
 // ------------------------------------------------------------------ forward (inference)
 // seg (optional, device): {offset, count} read at run time, so that one captured launch can serve
 // batches of any size placed anywhere in a packed buffer (the serving loop replays it every tick).
-template <int F>
+template <int F, int LAYOUT>
 __global__ void __launch_bounds__(TB) k_forward(const __grid_constant__ Levels lv, const __grid_constant__ MlpShape sh,
                                                 const float* __restrict__ T, const float* __restrict__ Pm,
                                                 const float* __restrict__ coords, int64_t n, float* __restrict__ out,
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(TB) k_forward(const __grid_constant__ Levels l
     float* bufB = bufA + sh.in * TB;
     float* bufC = bufB + sh.width * TB;
     for (int64_t i = blockIdx.x * (int64_t)TB + threadIdx.x; i < n; i += (int64_t)gridDim.x * TB) {
-        encode_to_col<F>(lv, T, load_coord(coords, i), bufA);
+        encode_to_col<F, LAYOUT>(lv, T, load_coord(coords, i), bufA);
         out[i] = mlp_fwd_col(sh, L, s, bufA, bufB, bufC, nullptr, n, i);
     }
 }
@@ -242,7 +244,7 @@ __device__ __forceinline__ double block_sum(double v) {
 // Stores what the backward needs, column-major [feature][n]: acts = enc (sh.in rows) then each
 // hidden layer's output (width rows each); gy[n] = dL/dy = 2 (y - target) / N (MSE mean);
 // per-block float64 partial sums of (y - target)^2.
-template <int F>
+template <int F, int LAYOUT>
 __global__ void __launch_bounds__(TB) k_train_fwd(const __grid_constant__ Levels lv, const __grid_constant__ MlpShape sh,
                                                   const float* __restrict__ T, const float* __restrict__ Pm,
                                                   const float* __restrict__ coords, const float* __restrict__ target,
@@ -258,7 +260,7 @@ __global__ void __launch_bounds__(TB) k_train_fwd(const __grid_constant__ Levels
     float* bufC = bufB + sh.width * TB;
     double lsum = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)TB + threadIdx.x; i < n; i += (int64_t)gridDim.x * TB) {
-        encode_to_col<F>(lv, T, load_coord(coords, i), bufA);
+        encode_to_col<F, LAYOUT>(lv, T, load_coord(coords, i), bufA);
         for (int c = 0; c < sh.in; ++c) acts[(int64_t)c * n + i] = bufA[c * TB];
         float y = mlp_fwd_col(sh, L, s, bufA, bufB, bufC, acts, n, i);
         float r = y - __ldg(target + i);
@@ -295,17 +297,17 @@ __device__ __forceinline__ void layer_bwd(const float* __restrict__ Wr, int fi4,
     }
 }
 
-template <int F>
+template <int F, int LAYOUT>
 __device__ __forceinline__ void scatter_sample(const Levels& lv, float* __restrict__ G, float4 u, const float* de) {
     for (int l = 0; l < lv.L; ++l) {
-        Corners k = corners(lv.lv[l], u);
+        Corners k = corners<LAYOUT>(lv.lv[l], u);
         float g[F];
 #pragma unroll
         for (int f = 0; f < F; ++f) g[f] = de[(l * F + f) * TB];
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
             float w = corner_weight(k, c);
-            float* dst = G + corner_row(k, c) * F;
+            float* dst = G + corner_row<LAYOUT>(k, c) * F;
             if constexpr (F == 2) {
                 red_add2(dst, w * g[0], w * g[1]);
             } else if constexpr (F == 4) {
@@ -321,7 +323,7 @@ __device__ __forceinline__ void scatter_sample(const Levels& lv, float* __restri
     }
 }
 
-template <int F>
+template <int F, int LAYOUT>
 __global__ void __launch_bounds__(TB) k_train_bwd(const __grid_constant__ Levels lv, const __grid_constant__ MlpShape sh,
                                                   float* __restrict__ G, const float* __restrict__ Pm,
                                                   const float* __restrict__ coords, int64_t n,
@@ -352,7 +354,7 @@ __global__ void __launch_bounds__(TB) k_train_bwd(const __grid_constant__ Levels
                 for (int c = 0; c < W; ++c) d[c * TB] = (aj[(int64_t)c * n] > 0.0f) ? p[c * TB] : 0.0f;
             }
         }
-        scatter_sample<F>(lv, G, load_coord(coords, i), p);  // p now holds d_enc (sh.in rows)
+        scatter_sample<F, LAYOUT>(lv, G, load_coord(coords, i), p);  // p now holds d_enc (sh.in rows)
     }
 }
 
@@ -376,23 +378,31 @@ struct FusedArgs {
     const int64_t* seg;  // optional device {offset, count} for the forward kernels
 };
 
-template <int F>
-cudaError_t run_fused(int which, const FusedArgs& a) {
+template <int F, int LAYOUT>
+cudaError_t run_fused_layout(int which, const FusedArgs& a) {
     const MlpShape& sh = *a.sh;
     const int W = sh.width;
     const int cols_f = sh.in + 2 * W, cols_b = ((sh.in > W ? sh.in : W) + 3) / 4 * 4 + W;
     const int smem = (which == 2 ? mlp_layout(sh, true, cols_b).floats : mlp_layout(sh, false, cols_f).floats) * 4;
-    const void* fn = which == 0 ? (const void*)k_forward<F> : which == 1 ? (const void*)k_train_fwd<F> : (const void*)k_train_bwd<F>;
+    const void* fn = which == 0   ? (const void*)k_forward<F, LAYOUT>
+                     : which == 1 ? (const void*)k_train_fwd<F, LAYOUT>
+                                  : (const void*)k_train_bwd<F, LAYOUT>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     if (which == 0)
-        k_forward<F><<<a.grid, TB, smem, a.st>>>(*a.lv, sh, a.T, a.Pm, a.coords, a.n, a.out, a.seg);
+        k_forward<F, LAYOUT><<<a.grid, TB, smem, a.st>>>(*a.lv, sh, a.T, a.Pm, a.coords, a.n, a.out, a.seg);
     else if (which == 1)
-        k_train_fwd<F><<<a.grid, TB, smem, a.st>>>(*a.lv, sh, a.T, a.Pm, a.coords, a.target, a.n, 2.0f / (float)a.n,
-                                                   a.acts, a.gy, a.partial);
+        k_train_fwd<F, LAYOUT><<<a.grid, TB, smem, a.st>>>(*a.lv, sh, a.T, a.Pm, a.coords, a.target, a.n,
+                                                           2.0f / (float)a.n, a.acts, a.gy, a.partial);
     else
-        k_train_bwd<F><<<a.grid, TB, smem, a.st>>>(*a.lv, sh, a.G, a.Pm, a.coords, a.n, a.acts, a.gy, a.dl);
+        k_train_bwd<F, LAYOUT><<<a.grid, TB, smem, a.st>>>(*a.lv, sh, a.G, a.Pm, a.coords, a.n, a.acts, a.gy, a.dl);
     return cudaGetLastError();
+}
+
+// All levels of a model share one layout; the per-sample kernels are instantiated for each.
+template <int F>
+cudaError_t run_fused(int which, const FusedArgs& a) {
+    return a.lv->lv[0].brick ? run_fused_layout<F, 1>(which, a) : run_fused_layout<F, 0>(which, a);
 }
 
 }  // namespace fh

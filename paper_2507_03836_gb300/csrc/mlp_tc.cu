@@ -35,7 +35,7 @@ struct TcSmem {
 
 // R = samples per thread: the CTA holds R tiles of 128 samples (R MMA tiles, R x 64 TMEM columns),
 // so every thread keeps the gathers of R samples in flight.
-template <int F, bool TRAIN, int R>
+template <int F, bool TRAIN, int R, int LAYOUT>
 __global__ void __launch_bounds__(128, 3) k_forward_tc(const __grid_constant__ Levels lv, const __grid_constant__ MlpShape sh,
                                                     const __nv_bfloat16* __restrict__ Tb,
                                                     const __nv_bfloat16* __restrict__ Pmb, const float* __restrict__ Pm,
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(128, 3) k_forward_tc(const __grid_constant__ L
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             float4 u = valid[r] ? load_coord(coords, idx[r]) : make_float4(0.f, 0.f, 0.f, 0.f);
-            encode_row_bf16<F, TRAIN>(lv, Tb, u, sm + r * 16384, t, valid[r] ? acts + idx[r] : nullptr, n);
+            encode_row_bf16<F, TRAIN, LAYOUT>(lv, Tb, u, sm + r * 16384, t, valid[r] ? acts + idx[r] : nullptr, n);
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
@@ -183,11 +183,12 @@ constexpr int kRInfer = 1, kRTrain = 1;
 // as 6 or 8; 2 samples per thread (more registers, fewer warps) is slower.  3 x 64 TMEM columns per SM
 // never approach the 512 available.  a.grid returns the grid used.
 constexpr int kCtasPerSm = 3;
-template <int F>
+template <int F, int LAYOUT>
 static cudaError_t run_tc(fhash_model* m, bool train, FusedArgs& a) {
     const int R = train ? kRTrain : kRInfer;
     const int smem = TcSmem::bytes(R, m->mlp.nh);
-    const void* fn = train ? (const void*)k_forward_tc<F, true, kRTrain> : (const void*)k_forward_tc<F, false, kRInfer>;
+    const void* fn = train ? (const void*)k_forward_tc<F, true, kRTrain, LAYOUT>
+                           : (const void*)k_forward_tc<F, false, kRInfer, LAYOUT>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 50);
     if (e != cudaSuccess) return e;
@@ -197,22 +198,27 @@ static cudaError_t run_tc(fhash_model* m, bool train, FusedArgs& a) {
     const __nv_bfloat16* Pmb = m->shadow + m->n_table;
     const float* Pm = m->param + m->n_table;
     if (train)
-        k_forward_tc<F, true, kRTrain><<<a.grid, 128, smem, a.st>>>(m->lv, m->mlp, Tb, Pmb, Pm, a.coords, a.target, a.n,
-                                                                    nullptr, a.acts, a.gy, a.partial, 2.0f / (float)a.n,
-                                                                    m->err_word, nullptr);
+        k_forward_tc<F, true, kRTrain, LAYOUT><<<a.grid, 128, smem, a.st>>>(
+            m->lv, m->mlp, Tb, Pmb, Pm, a.coords, a.target, a.n, nullptr, a.acts, a.gy, a.partial, 2.0f / (float)a.n,
+            m->err_word, nullptr);
     else
-        k_forward_tc<F, false, kRInfer><<<a.grid, 128, smem, a.st>>>(m->lv, m->mlp, Tb, Pmb, Pm, a.coords, nullptr, a.n,
-                                                                     a.out, nullptr, nullptr, nullptr, 0.0f, m->err_word,
-                                                                     a.seg);
+        k_forward_tc<F, false, kRInfer, LAYOUT><<<a.grid, 128, smem, a.st>>>(
+            m->lv, m->mlp, Tb, Pmb, Pm, a.coords, nullptr, a.n, a.out, nullptr, nullptr, nullptr, 0.0f, m->err_word, a.seg);
     return cudaGetLastError();
+}
+
+// All levels of a model share one layout; the kernel is instantiated for each.
+template <int F>
+static cudaError_t run_tc_f(fhash_model* m, bool train, FusedArgs& a) {
+    return m->lv.lv[0].brick ? run_tc<F, 1>(m, train, a) : run_tc<F, 0>(m, train, a);
 }
 
 cudaError_t run_tc_any(fhash_model* m, bool train, FusedArgs& a) {
     switch (m->lv.F) {
-        case 1: return run_tc<1>(m, train, a);
-        case 2: return run_tc<2>(m, train, a);
-        case 4: return run_tc<4>(m, train, a);
-        case 8: return run_tc<8>(m, train, a);
+        case 1: return run_tc_f<1>(m, train, a);
+        case 2: return run_tc_f<2>(m, train, a);
+        case 4: return run_tc_f<4>(m, train, a);
+        case 8: return run_tc_f<8>(m, train, a);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -265,6 +265,8 @@ fhash_status fhash_build(const fhash_build_desc* d, fhash_stream stream, fhash_m
     if (d->mlp_width != 16 && d->mlp_width != 32 && d->mlp_width != 64)
         return set_error(FHASH_EINVAL, "mlp_width must be 16, 32 or 64");
     if (!(d->init_range >= 0.0f)) return set_error(FHASH_EINVAL, "init_range");
+    if (d->layout != FHASH_LAYOUT_LINEAR && d->layout != FHASH_LAYOUT_BRICK)
+        return set_error(FHASH_EINVAL, "layout must be FHASH_LAYOUT_LINEAR or FHASH_LAYOUT_BRICK");
 
     fhash_model* m = new fhash_model();
     m->desc = *d;
@@ -356,6 +358,7 @@ fhash_status fhash_build(const fhash_build_desc* d, fhash_stream stream, fhash_m
         if (sxyz >= (1ull << 32)) return set_error(FHASH_EINVAL, "level %d: Rx*Ry*Rz too large", l);
         v.st = sxyz;
         v.base = acc;
+        v.brick = d->layout == FHASH_LAYOUT_BRICK ? 1 : 0;
         acc += sxyz * (uint64_t)res[l][3];
     }
     m->total_rows = acc;
@@ -569,7 +572,7 @@ fhash_status fhash_save(const fhash_model* mc, const char* path) {
     CkptHeader h;
     memset(&h, 0, sizeof h);
     memcpy(h.magic, kMagic, 8);
-    h.version = 1;
+    h.version = 2;  // 2: levels carry their row layout
     h.header_bytes = sizeof h;
     h.desc = m->desc;
     h.desc.mask = nullptr;
@@ -598,7 +601,7 @@ fhash_status fhash_load(const char* path, fhash_stream stream, fhash_model** out
     FILE* f = fopen(path, "rb");
     if (!f) return set_error(FHASH_EIO, "fhash_load: cannot open %s", path);
     CkptHeader h;
-    if (fread(&h, sizeof h, 1, f) != 1 || memcmp(h.magic, kMagic, 8) != 0 || h.version != 1 ||
+    if (fread(&h, sizeof h, 1, f) != 1 || memcmp(h.magic, kMagic, 8) != 0 || h.version != 2 ||
         h.header_bytes != sizeof h || h.lv.L < 1 || h.lv.L > FHASH_MAX_LEVELS || h.n_params < h.n_table) {
         fclose(f);
         return set_error(FHASH_EIO, "fhash_load: %s is not an F-Hash checkpoint of this version", path);

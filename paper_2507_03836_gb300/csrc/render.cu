@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(TB) k_decode(const __grid_constant__ Levels lv
         int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((int64_t)nx * ny));
         float4 u = make_float4(__fdiv_rn((float)x, (float)(nx - 1)), __fdiv_rn((float)y, (float)(ny - 1)),
                                __fdiv_rn((float)z, (float)(nz - 1)), t_norm);
-        encode_to_col<F>(lv, T, u, bufA);
+        encode_to_col<F, -1>(lv, T, u, bufA);
         out[i] = mlp_fwd_col(sh, L, s, bufA, bufB, bufC, nullptr, n, i);
     }
 }

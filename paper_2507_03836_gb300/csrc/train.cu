@@ -98,13 +98,13 @@ __global__ void __launch_bounds__(256) k_scatter_cols(const __grid_constant__ Le
             // reduction instead of two 8-byte ones (fewer L2 atomic operations)
 #pragma unroll
             for (int c = 0; c < 16; c += 2) {
-                const uint64_t r = corner_row(k, c);
+                const uint64_t r = corner_row(k, c), r1 = corner_row(k, c + 1);
                 const float w0 = corner_weight(k, c), w1 = corner_weight(k, c + 1);
-                if (k.ox == 1u && (r & 1u) == 0u) {
+                if (r1 == r + 1 && (r & 1u) == 0u) {
                     red_add4(G + r * 2, w0 * g[0], w0 * g[1], w1 * g[0], w1 * g[1]);
                 } else {
                     red_add2(G + r * 2, w0 * g[0], w0 * g[1]);
-                    red_add2(G + (r + k.ox) * 2, w1 * g[0], w1 * g[1]);
+                    red_add2(G + r1 * 2, w1 * g[0], w1 * g[1]);
                 }
             }
         } else {

@@ -51,7 +51,20 @@ def test_fullsize_build(large):
 
 
 def test_fullsize_forward_train_step(large):
-    info, model = large["info"], large["model"]
+    _forward_train_step(large["model"], large["info"], large["field"], "linear")
+
+
+def test_fullsize_brick_forward_train_step(large):
+    """The same checks on a model in the brick row layout (the bench's default layout)."""
+    nx, ny, nz, nt = W["dims"]
+    model = fh().fhash_build(nx, ny, nz, nt, mask=large["mask"], schedule=fh().make_schedule(**W["schedule"]),
+                             F=W["F"], mlp_hidden_layers=W["hidden"], mlp_width=W["width"], seed=SEED,
+                             init_range=W["init_range"], layout=fh().LAYOUT_BRICK)
+    _forward_train_step(model, fh().fhash_get_info(model), large["field"], "brick")
+    del model
+
+
+def _forward_train_step(model, info, field, layout):
     lv, b, F, dims = info["res"], info["base"], info["F"], info["mlp_dims"]
     table = rng.InitTable(SEED, F, R32)
     p = rng.init_mlp(SEED, dims)
@@ -61,29 +74,29 @@ def test_fullsize_forward_train_step(large):
     c = synth.coords(31, 4096)
     out = torch().empty(c.shape[0], dtype=torch().float32, device="cuda")
     fh().fhash_forward(model, to_dev(c), out)
-    ref = mlp.forward(p, dims, encode.encode(lv, b, c, table))[0]
+    ref = mlp.forward(p, dims, encode.encode(lv, b, c, table, layout))[0]
     tol = 1e-4 * np.maximum(np.abs(ref), np.sqrt(np.mean(ref ** 2)))
     assert (np.abs(out.cpu().numpy() - ref) <= tol).all()
 
     # one full training step at the bench's batch
     B = W["batch"]
     c = synth.coords(10_000, B)
-    tgt = synth.sample(large["field"], info["fbb_lo"], info["fbb_size"], c)
+    tgt = synth.sample(field, info["fbb_lo"], info["fbb_size"], c)
     loss = np.zeros(1, np.float64)
     fh().fhash_compute_grads(model, to_dev(c), to_dev(tgt), loss)
-    L, _, g_mlp, (rows, g_rows) = train.loss_and_grads(lv, b, F, dims, table, p, c, tgt)
+    L, _, g_mlp, (rows, g_rows) = train.loss_and_grads(lv, b, F, dims, table, p, c, tgt, layout)
     assert abs(loss[0] - L) <= 1e-5 * L, (loss[0], L)
 
     g_dev = np.empty(info["n_mlp_params"], np.float32)
     fh().fhash_read_state(model, fh().STATE_GRAD, n_t, g_dev)
-    enc = encode.encode(lv, b, c, table)
+    enc = encode.encode(lv, b, c, table, layout)
     y, a, z = mlp.forward(p, dims, enc)
     _, gy = mlp.mse(y, tgt)
     abs_mlp, abs_denc = mlp.backward(np.abs(p), dims, [np.abs(x) for x in a], [np.where(x > 0, 1.0, -1.0) for x in z],
                                      np.abs(gy))
     assert (np.abs(g_dev - g_mlp) <= 1e-4 * abs_mlp + 1e-12).all()
 
-    r_abs, g_abs = encode.encode_backward(lv, b, c, abs_denc, F)
+    r_abs, g_abs = encode.encode_backward(lv, b, c, abs_denc, F, layout)
     assert np.array_equal(r_abs, rows)
     pick = np.random.default_rng(0).choice(rows.size, 20000, replace=False)
     touched = rows[pick]

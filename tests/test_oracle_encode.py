@@ -118,3 +118,47 @@ def test_backward_is_transpose_of_forward():
     r, g = encode.encode_backward(levels, b, co, d, F)
     rhs = np.sum(g * table[r])
     assert abs(lhs - rhs) <= 1e-10 * abs(lhs)
+
+
+@pytest.mark.parametrize("R", [(5, 6, 7, 3), (4, 4, 4, 2), (9, 1, 2, 1), (8, 12, 3, 2)])
+def test_brick_rows_are_the_rank_of_the_brick_order(R):
+    """The brick linearisation (Section 3.2.3 allows locality-preserving orders): every vertex's row is
+    its rank in lexicographic (t, bz, by, bx, iz, iy, ix) order, brute force over all vertices, partial
+    bricks included; so it is a bijection onto [0, Rx*Ry*Rz*Rt) like Eq. 9."""
+    Rx, Ry, Rz, Rt = R
+    t, z, y, x = (a.ravel() for a in np.meshgrid(np.arange(Rt), np.arange(Rz), np.arange(Ry), np.arange(Rx),
+                                                 indexing="ij"))
+    rows = encode.fhash(t, x, y, z, R, "brick")
+    key = np.lexsort((x % 4, y % 4, z % 4, x // 4, y // 4, z // 4, t))  # last key is primary
+    rank = np.empty_like(key)
+    rank[key] = np.arange(key.size)
+    assert np.array_equal(rows, rank)
+    assert np.array_equal(np.sort(rows), np.arange(Rx * Ry * Rz * Rt))
+
+
+def test_brick_layout_is_a_relabelling_of_eq9():
+    """With the same vertex values stored at each layout's rows, both layouts give the same encoding
+    and the same gradient per vertex: only where a vertex lives changes."""
+    levels = [[3, 4, 5, 2], [6, 7, 9, 3]]
+    bases, total = schedule.bases(levels)
+    F = 2
+    rng = np.random.default_rng(3)
+    t_lin = rng.standard_normal((total, F))
+    t_brk = np.empty_like(t_lin)
+    for R, b in zip(levels, bases):
+        Rx, Ry, Rz, Rt = R
+        t, z, y, x = (a.ravel() for a in np.meshgrid(*[np.arange(k) for k in (Rt, Rz, Ry, Rx)], indexing="ij"))
+        t_brk[b + encode.fhash(t, x, y, z, R, "brick")] = t_lin[b + encode.fhash(t, x, y, z, R)]
+    c = rng.random((500, 4)).astype(np.float32)
+    assert np.allclose(encode.encode(levels, bases, c, t_lin), encode.encode(levels, bases, c, t_brk, "brick"),
+                       rtol=0, atol=1e-12)
+    d = rng.standard_normal((500, len(levels) * F))
+    r1, g1 = encode.encode_backward(levels, bases, c, d, F)
+    r2, g2 = encode.encode_backward(levels, bases, c, d, F, "brick")
+    m = np.empty(total, np.int64)  # brick row -> linear row
+    for R, b in zip(levels, bases):
+        Rx, Ry, Rz, Rt = R
+        t, z, y, x = (a.ravel() for a in np.meshgrid(*[np.arange(k) for k in (Rt, Rz, Ry, Rx)], indexing="ij"))
+        m[b + encode.fhash(t, x, y, z, R, "brick")] = b + encode.fhash(t, x, y, z, R)
+    order = np.argsort(m[r2])
+    assert np.array_equal(m[r2][order], r1) and np.allclose(g2[order], g1, rtol=0, atol=1e-12)
