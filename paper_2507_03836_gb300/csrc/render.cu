@@ -83,8 +83,31 @@ __global__ void k_ray_init(const __grid_constant__ RenderGeo g, RayState* __rest
     }
 }
 
+// Index of the last sample that surely still lies in the empty 8^3 brick holding voxel v, for a ray
+// whose sample k is in it.  The brick holds the samples whose nearest voxel is in [8b, 8b + 7] on each
+// axis, that is model coordinate q = u (S - 1) in [8b - 0.5, 8b + 7.5); the ray parameter where q
+// reaches that box's far faces, pulled in by 0.01 voxel (far more than the float32 rounding of q), bounds
+// the samples that can be skipped.  Samples never evaluated there are unoccupied, so the set of samples
+// (and the image) is the same as stepping through them one by one.
+__device__ __forceinline__ int empty_brick_last_sample(const RenderGeo& g, const RayState& s, const int v[3], int k) {
+    double t_exit = 1e30;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const double d = s.d[ax];
+        if (d == 0.0) continue;
+        const int b8 = (v[ax] >> 3) * 8;
+        const double qf = d > 0.0 ? b8 + 7.5 - 0.01 : b8 - 0.5 + 0.01;  // the face the ray runs to
+        const double uf = qf / (double)(g.S[ax] - 1);
+        const double tf = ((2.0 * uf - 1.0) - (double)g.eye[ax]) / d;  // u = (eye + t d + 1) / 2
+        t_exit = fmin(t_exit, tf);
+    }
+    const double kl = floor((t_exit - (double)s.tmin) / (double)g.delta);
+    return kl > (double)k ? (int)fmin(kl, (double)(1 << 24)) : k;
+}
+
 // Marches each alive ray on until it has up to Ns occupied samples (or leaves the box); writes their
-// model coordinates to slots [a*Ns, a*Ns + cnt).
+// model coordinates to slots [a*Ns, a*Ns + cnt).  A sample in an 8^3 brick that is empty at both time
+// steps in use jumps the ray to the last sample inside that brick (empty-space skipping).
 __global__ void k_arm_generate(const __grid_constant__ RenderGeo g, RayState* __restrict__ rs,
                                const int* __restrict__ alive, int na, int ns, float4* __restrict__ coords,
                                int* __restrict__ cnt, unsigned long long* __restrict__ marched) {
@@ -101,9 +124,24 @@ __global__ void k_arm_generate(const __grid_constant__ RenderGeo g, RayState* __
         float u[3];
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) u[ax] = __fmul_rn(__fadd_rn(__fadd_rn(g.eye[ax], __fmul_rn(sk, s.d[ax])), 1.0f), 0.5f);
-        ++k;
         ++steps;
-        if (sample_occupied(g, u)) coords[(int64_t)a * ns + c++] = make_float4(u[0], u[1], u[2], g.t_norm);
+        int v[3];
+        bool inside = true;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            v[ax] = (int)floorf(__fadd_rn(__fmul_rn(u[ax], (float)(g.S[ax] - 1)), 0.5f));
+            inside = inside && v[ax] >= 0 && v[ax] < g.S[ax];
+        }
+        if (inside) {
+            const int64_t b = ((int64_t)(v[2] >> 3) * g.nby + (v[1] >> 3)) * g.nbx + (v[0] >> 3);
+            const bool any = g.occ_any[(int64_t)g.tp * g.nbrick + b] || (g.use_tn && g.occ_any[(int64_t)g.tn * g.nbrick + b]);
+            if (!any) {
+                k = empty_brick_last_sample(g, s, v, k) + 1;  // samples up to the returned one are empty
+                continue;
+            }
+        }
+        ++k;
+        if (inside && sample_occupied(g, u)) coords[(int64_t)a * ns + c++] = make_float4(u[0], u[1], u[2], g.t_norm);
     }
     rs[pix].k = k;
     rs[pix].flags = s.flags;
