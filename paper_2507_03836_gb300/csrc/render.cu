@@ -86,23 +86,23 @@ __global__ void k_ray_init(const __grid_constant__ RenderGeo g, RayState* __rest
 // Index of the last sample that surely still lies in the empty 8^3 brick holding voxel v, for a ray
 // whose sample k is in it.  The brick holds the samples whose nearest voxel is in [8b, 8b + 7] on each
 // axis, that is model coordinate q = u (S - 1) in [8b - 0.5, 8b + 7.5); the ray parameter where q
-// reaches that box's far faces, pulled in by 0.01 voxel (far more than the float32 rounding of q), bounds
-// the samples that can be skipped.  Samples never evaluated there are unoccupied, so the set of samples
-// (and the image) is the same as stepping through them one by one.
+// reaches that box's far faces, pulled in by 0.01 voxel (far more than the float32 rounding of q and of
+// this bound, about 1e-4 voxel), limits the samples that can be skipped.  Samples never evaluated there
+// are unoccupied, so the set of samples (and the image) is the same as stepping through them one by one.
+// Float32 throughout: the FP64 rate of this GPU is a small fraction of its FP32 rate.
 __device__ __forceinline__ int empty_brick_last_sample(const RenderGeo& g, const RayState& s, const int v[3], int k) {
-    double t_exit = 1e30;
+    float t_exit = 3.0e38f;
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
-        const double d = s.d[ax];
-        if (d == 0.0) continue;
+        const float d = s.d[ax];
+        if (d == 0.0f) continue;
         const int b8 = (v[ax] >> 3) * 8;
-        const double qf = d > 0.0 ? b8 + 7.5 - 0.01 : b8 - 0.5 + 0.01;  // the face the ray runs to
-        const double uf = qf / (double)(g.S[ax] - 1);
-        const double tf = ((2.0 * uf - 1.0) - (double)g.eye[ax]) / d;  // u = (eye + t d + 1) / 2
-        t_exit = fmin(t_exit, tf);
+        const float qf = d > 0.0f ? (float)b8 + 7.49f : (float)b8 - 0.49f;  // the face the ray runs to
+        const float uf = qf / (float)(g.S[ax] - 1);
+        t_exit = fminf(t_exit, ((2.0f * uf - 1.0f) - g.eye[ax]) / d);  // u = (eye + t d + 1) / 2
     }
-    const double kl = floor((t_exit - (double)s.tmin) / (double)g.delta);
-    return kl > (double)k ? (int)fmin(kl, (double)(1 << 24)) : k;
+    const float kl = floorf((t_exit - s.tmin) / g.delta);
+    return kl > (float)k ? (int)fminf(kl, (float)(1 << 24)) : k;
 }
 
 // Marches each alive ray on until it has up to Ns occupied samples (or leaves the box); writes their
@@ -132,16 +132,17 @@ __global__ void k_arm_generate(const __grid_constant__ RenderGeo g, RayState* __
             v[ax] = (int)floorf(__fadd_rn(__fmul_rn(u[ax], (float)(g.S[ax] - 1)), 0.5f));
             inside = inside && v[ax] >= 0 && v[ax] < g.S[ax];
         }
-        if (inside) {
-            const int64_t b = ((int64_t)(v[2] >> 3) * g.nby + (v[1] >> 3)) * g.nbx + (v[0] >> 3);
-            const bool any = g.occ_any[(int64_t)g.tp * g.nbrick + b] || (g.use_tn && g.occ_any[(int64_t)g.tn * g.nbrick + b]);
-            if (!any) {
-                k = empty_brick_last_sample(g, s, v, k) + 1;  // samples up to the returned one are empty
-                continue;
-            }
+        if (!inside) { ++k; continue; }
+        const int64_t b = ((int64_t)(v[2] >> 3) * g.nby + (v[1] >> 3)) * g.nbx + (v[0] >> 3);
+        const bool any_p = g.occ_any[(int64_t)g.tp * g.nbrick + b] != 0;
+        const bool any_n = g.use_tn && g.occ_any[(int64_t)g.tn * g.nbrick + b] != 0;
+        if (!any_p && !any_n) {
+            k = empty_brick_last_sample(g, s, v, k) + 1;  // samples up to the returned one are empty
+            continue;
         }
         ++k;
-        if (inside && sample_occupied(g, u)) coords[(int64_t)a * ns + c++] = make_float4(u[0], u[1], u[2], g.t_norm);
+        if ((any_p && occ_bit(g, g.tp, v[0], v[1], v[2])) || (any_n && occ_bit(g, g.tn, v[0], v[1], v[2])))
+            coords[(int64_t)a * ns + c++] = make_float4(u[0], u[1], u[2], g.t_norm);
     }
     rs[pix].k = k;
     rs[pix].flags = s.flags;
