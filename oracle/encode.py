@@ -19,6 +19,9 @@ Everything after the float32 cell step is float64.
 
 Corner order used for row/weight arrays: c = i + 2j + 4k + 8s with i, j, k the upper/lower
 corner on x, y, z and s = 0 for t_Previous, 1 for t_Next.
+
+`layout` is "linear" (Eq. 9), "brick", or a masked layout (oracle/masked.py: rows only for the
+vertices near the features; an inactive corner has row -1, reads 0 and takes no gradient).
 """
 import numpy as np
 
@@ -56,8 +59,21 @@ def fhash(t, x, y, z, R, layout="linear"):
             + (iz * wy + iy) * wx + ix)
 
 
+def _level_layout(layout, l):
+    return layout if isinstance(layout, str) else layout.level(l)
+
+
+def _rows(t, x, y, z, R, base, layout):
+    """Concatenated-table rows of vertices (t, x, y, z) of one level; -1 for an inactive vertex of a
+    masked level."""
+    if isinstance(layout, str):
+        return base + fhash(t, x, y, z, R, layout)
+    return layout.rows(t, x, y, z)
+
+
 def level_corners(coords, R, base, layout="linear"):
-    """Rows [N][16] (int64, concatenated-table rows) and float64 weights [N][16] of one level."""
+    """Rows [N][16] (int64, concatenated-table rows; -1 = inactive corner of a masked level) and
+    float64 weights [N][16] of one level.  `layout` is a string or one level of a masked layout."""
     coords = np.asarray(coords, np.float32)
     cx, cx1, wx = locate(coords[:, 0], R[0])
     cy, cy1, wy = locate(coords[:, 1], R[1])
@@ -72,7 +88,7 @@ def level_corners(coords, R, base, layout="linear"):
             for j, (yy, wj) in enumerate(((cy, 1.0 - wy), (cy1, wy))):
                 for i, (xx, wi) in enumerate(((cx, 1.0 - wx), (cx1, wx))):
                     c = i + 2 * j + 4 * k + 8 * s
-                    rows[:, c] = base + fhash(tt, xx, yy, zz, R, layout)
+                    rows[:, c] = _rows(tt, xx, yy, zz, R, base, layout)
                     wts[:, c] = ws * wk * wj * wi
     return rows, wts
 
@@ -91,7 +107,9 @@ def interpolate_level(coords, R, base, table, layout="linear"):
         for i, xx in ((0, cx), (1, cx1)):
             for j, yy in ((0, cy), (1, cy1)):
                 for k, zz in ((0, cz), (1, cz1)):
-                    Vijk = np.asarray(table[base + fhash(tt, xx, yy, zz, R, layout)], np.float64)
+                    r = _rows(tt, xx, yy, zz, R, base, layout)
+                    Vijk = np.asarray(table[np.maximum(r, 0)], np.float64)
+                    Vijk = np.where((r >= 0)[:, None], Vijk, 0.0)        # inactive corner reads 0
                     acc = acc + Vijk * (x ** i * (1 - x) ** (1 - i)) * (y ** j * (1 - y) ** (1 - j)) \
                         * (z ** k * (1 - z) ** (1 - k))
         return acc
@@ -102,7 +120,8 @@ def interpolate_level(coords, R, base, table, layout="linear"):
 def encode(levels, level_bases, coords, table, layout="linear"):
     """Concatenated encoding [N][L*F] float64; `table` is indexable by int64 row arrays and
     returns [n][F] values (a dense [rows][F] array, or any lazy equivalent)."""
-    parts = [interpolate_level(coords, R, b, table, layout) for R, b in zip(levels, level_bases)]
+    parts = [interpolate_level(coords, R, b, table, _level_layout(layout, l))
+             for l, (R, b) in enumerate(zip(levels, level_bases))]
     return np.concatenate(parts, axis=1)
 
 
@@ -112,12 +131,14 @@ def encode_backward(levels, level_bases, coords, d_enc, F, layout="linear"):
     Returns (unique rows int64, gradient [n_rows][F] float64)."""
     all_rows, all_vals = [], []
     for l, (R, b) in enumerate(zip(levels, level_bases)):
-        rows, wts = level_corners(coords, R, b, layout)
+        rows, wts = level_corners(coords, R, b, _level_layout(layout, l))
         g = np.asarray(d_enc, np.float64)[:, l * F:(l + 1) * F]
         all_rows.append(rows.reshape(-1))
         all_vals.append((wts[:, :, None] * g[:, None, :]).reshape(-1, F))
     rows = np.concatenate(all_rows)
     vals = np.concatenate(all_vals)
+    keep = rows >= 0                                     # inactive corners take no gradient
+    rows, vals = rows[keep], vals[keep]
     # per-row sums of the contributions: sort by row, then sum each run of equal rows
     order = np.argsort(rows, kind="stable")
     rs = rows[order]
