@@ -419,6 +419,65 @@ def suite_coreset(args):
     print(json.dumps(res))
 
 
+def suite_masked(args):
+    """Masked compact tables (FHASH_LAYOUT_MASKED, Section 3.1's feature-only grids) against the default
+    brick layout, both trained on the coreset of advect-256^3x64 (10 key frames, batch 2^21): table size,
+    directory build time, coreset-training samples/s, float32 forward samples/s on 4M held-out coreset
+    points and PSNR there."""
+    import torch
+    import paper_2507_03836_gb300 as fh
+    from synth import workloads
+    w = dict(workloads.LARGE, batch=1 << 21)
+    keys = [int(round(k * (w["dims"][3] - 1) / 9)) for k in range(10)]
+    field, mask = workloads.make_field_and_mask(w)
+    hp = w["adam"]
+    B, K, W0 = w["batch"], args.steps, 3
+    res = {"suite": "masked", "workload": w["name"], "key_frames": keys, "batch": B, "steps": K}
+    st = torch.cuda.current_stream()
+    for name, layout in (("brick", fh.LAYOUT_BRICK), ("masked", fh.LAYOUT_MASKED)):
+        torch.cuda.synchronize()
+        t0 = time.time()
+        model, info = _build(w, fh.FP32, 5, mask, layout)
+        build_s = time.time() - t0
+        N = fh.fhash_coreset_build(model, field, keys)
+        per_epoch = (N + B - 1) // B
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for i in range(K + W0):
+            if i == W0:
+                torch.cuda.synchronize()
+                e0.record(st)
+            fh.fhash_coreset_train_step(model, 1, i // per_epoch, i % per_epoch, B, hp)
+        e1.record(st)
+        torch.cuda.synchronize()
+        fh.fhash_check(model)
+        ms = e0.elapsed_time(e1) / K
+        n_h = 1 << 22
+        hc = torch.empty((n_h, 4), dtype=torch.float32, device="cuda")
+        ht = torch.empty(n_h, dtype=torch.float32, device="cuda")
+        n_h = fh.fhash_coreset_batch(model, 4242, 0, 0, n_h, hc, ht)
+        hc, ht = hc[:n_h], ht[:n_h]
+        o = torch.empty(n_h, dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            fh.fhash_forward(model, hc, o)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(10):
+            fh.fhash_forward(model, hc, o)
+        e1.record(st)
+        torch.cuda.synchronize()
+        fwd_ms = e0.elapsed_time(e1) / 10
+        pred, lab = o.cpu().numpy().astype(np.float64), ht.cpu().numpy().astype(np.float64)
+        psnr = float(10 * np.log10((lab.max() - lab.min()) ** 2 / np.mean((pred - lab) ** 2)))
+        res[name] = {"table_rows": info["total_rows"], "table_params": info["n_table_params"],
+                     "device_bytes": info["device_bytes"], "build_s": build_s, "coreset_samples": N,
+                     "train_ms_per_step": ms, "train_samples_s": B / ms * 1e3,
+                     "forward_samples_s": n_h / fwd_ms * 1e3, "psnr_feature_db": psnr}
+        del model, hc, ht, o
+        torch.cuda.empty_cache()
+    res["table_fraction"] = res["masked"]["table_rows"] / res["brick"]["table_rows"]
+    print(json.dumps(res))
+
+
 def suite_forward(args):
     """The two evaluation paths of the precision form on uniform points: the fused kernel and the split
     pair (bf16 encoding rows, then the TMA-fed tensor-core MLP).  --workload picks the model (random
@@ -623,7 +682,8 @@ def main():
                          "linearisation on this GPU), or Eq. 9")
     ap.add_argument("--forward-points", type=int, default=1 << 22, help="--suite forward: points per call")
     ap.add_argument("--forward-paths", default="fused,split", help="--suite forward: paths to time")
-    ap.add_argument("--suite", default="train", choices=["train", "precision", "serve", "mixed", "coreset", "forward", "peaks"],
+    ap.add_argument("--suite", default="train", choices=["train", "precision", "serve", "mixed", "coreset", "masked", "forward",
+                                                    "peaks"],
                     help="train: the default line; precision / serve / mixed: the other workloads")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -632,7 +692,8 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         return {"precision": suite_precision, "serve": suite_serve, "mixed": suite_mixed,
-                "coreset": suite_coreset, "forward": suite_forward, "peaks": suite_peaks}[args.suite](args)
+                "coreset": suite_coreset, "masked": suite_masked, "forward": suite_forward,
+                "peaks": suite_peaks}[args.suite](args)
 
     import torch
     import synth

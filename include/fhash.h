@@ -111,8 +111,27 @@ typedef struct {
  * i = v % 4 and w(b) = min(4, R - 4b) per axis the row is
  *   t*Rx*Ry*Rz + 4*bz*Rx*Ry + wz*4*by*Rx + wz*wy*4*bx + (iz*wy + iy)*wx + ix,
  * a bijection onto [0, Rx*Ry*Rz*Rt) like Eq. 9.  The 16 corners of a cell then lie in 1 to 8 bricks
- * per time slice, which cuts the random memory accesses of the gathers at HBM-resident levels. */
-enum { FHASH_LAYOUT_LINEAR = 0, FHASH_LAYOUT_BRICK = 1 };
+ * per time slice, which cuts the random memory accesses of the gathers at HBM-resident levels.
+ *
+ * MASKED keeps rows only for the vertices near the features: the irregular multi-resolution grids
+ * that Section 3.1 describes as a smaller-model variant of the coreset.  Active vertices come from the
+ * dilated mask of every time step:
+ *   - Footprint of dilated voxel v (FBB-relative) on a spatial axis of S voxels: u*(S-1) in
+ *     [v - 1/2, v + 1/2], the points whose nearest voxel is v.  On the time axis (nt steps), step k
+ *     covers t*(nt-1) in [k - 1, k + 1].  In level units p = u*(R-1) the footprint is widened by
+ *     1/64 on each side.
+ *   - A vertex is active when it is a corner of a cell that the float32 cell step assigns to a point
+ *     of some footprint.  Per axis these are the vertices clamp(floor(p_lo), 0, R-2) ..
+ *     clamp(floor(p_hi), 0, R-2) + 1, in exact integer arithmetic.  An axis whose FBB has one voxel
+ *     keeps all its vertices.
+ *   - A level's rows are its active vertices in Eq. 9 order; base[l] adds up the active counts of the
+ *     coarser levels.
+ * An inactive corner contributes 0 to the encoding and receives no gradient.  Every sample whose
+ * nearest voxel is in the dilated feature (coreset samples, rendered samples at occupied voxels) sees
+ * only active corners.  There its encoding equals that of the rectangular table with the same vertex
+ * values.  MASKED needs dtype FHASH_FP32 and a mask; the allocation-free gradient entry point does not
+ * take it. */
+enum { FHASH_LAYOUT_LINEAR = 0, FHASH_LAYOUT_BRICK = 1, FHASH_LAYOUT_MASKED = 2 };
 
 typedef struct {
     int64_t nx, ny, nz, nt;
@@ -124,7 +143,7 @@ typedef struct {
     int32_t mlp_width;
     uint64_t seed;
     float init_range;
-    int32_t layout;  /* FHASH_LAYOUT_LINEAR (Eq. 9, the default) or FHASH_LAYOUT_BRICK */
+    int32_t layout;  /* FHASH_LAYOUT_LINEAR (Eq. 9, the default), _BRICK or _MASKED */
 } fhash_build_desc;
 
 /* Read-only description of a built model. */
@@ -133,7 +152,7 @@ typedef struct {
     int32_t mlp_dims[FHASH_MAX_HIDDEN + 2];  /* L*F, width, ..., width, 1 */
     int32_t res[FHASH_MAX_LEVELS][4];        /* (Rx, Ry, Rz, Rt), coarse -> fine */
     uint64_t base[FHASH_MAX_LEVELS];         /* first row of each level */
-    uint64_t total_rows;                     /* sum of Rx*Ry*Rz*Rt */
+    uint64_t total_rows;                     /* sum of Rx*Ry*Rz*Rt (MASKED: of the active counts) */
     uint64_t n_table_params;                 /* total_rows * F */
     uint64_t n_mlp_params;
     int64_t fbb_lo[3], fbb_size[3];          /* Feature Bounding Box, vertices, (x, y, z) */
@@ -188,7 +207,8 @@ fhash_status fhash_set_params(fhash_model* model, const float* tables, const flo
 /*
  * Encoding steps 1-3 of Section 3.2.4 for inspection: per sample and level, the 16 corner rows
  * through Eq. 9 (with level base) and their quadrilinear weights (Eqs. 10-12), corner index
- * c = i + 2j + 4k + 8s (i, j, k: upper corner on x, y, z; s = 1 for t_Next).
+ * c = i + 2j + 4k + 8s (i, j, k: upper corner on x, y, z; s = 1 for t_Next).  In a
+ * FHASH_LAYOUT_MASKED model an inactive corner's row is UINT64_MAX.
  *  coords: device [n][4]; rows: device [n][L][16] uint64; weights: device [n][L][16] float or NULL.
  */
 fhash_status fhash_lookup(fhash_model* model, const float* coords, int64_t n, uint64_t* rows, float* weights,
@@ -291,6 +311,13 @@ fhash_status fhash_write_state(fhash_model* model, int32_t which, uint64_t offse
  * out: host or device [Sz][Sy][Sx]. */
 fhash_status fhash_read_occupancy(fhash_model* model, int64_t t, uint8_t* out, fhash_stream stream);
 
+/* Active-vertex bits of level l of a FHASH_LAYOUT_MASKED model: word w holds the vertices with Eq. 9
+ * rows 64w .. 64w+63 of the level (bit i = row 64w + i), words [word0, word0 + n_words) into `bits`
+ * (host or device).  Synchronous for host buffers.  FHASH_EINVAL for another layout, a level out of
+ * range or words past ceil(Rx*Ry*Rz*Rt / 64). */
+fhash_status fhash_read_active(fhash_model* model, int32_t level, uint64_t word0, uint64_t n_words, uint64_t* bits,
+                               fhash_stream stream);
+
 /*
  * Checkpoints (the paper pretrains the INR before visualisation, Section 3.3).  fhash_save writes the
  * model description, level schedule, Feature Bounding Box, Adam step count, every state vector
@@ -383,7 +410,8 @@ fhash_status fhash_decode(fhash_model* model, float t_norm, int32_t upsample, fl
  *  - It evaluates the float32 form (float32 master tables and MLP on the CUDA cores), also for
  *    FHASH_BF16 models.
  *  - n must be in 1..FHASH_NOALLOC_MAX_SAMPLES; a model/n combination whose working set exceeds the
- *    array is rejected with FHASH_EINVAL before anything is launched.
+ *    array is rejected with FHASH_EINVAL before anything is launched.  FHASH_LAYOUT_MASKED models are
+ *    rejected with FHASH_EINVAL (they take fhash_compute_grads).
  *  - The first call on a device, made with that device current, looks up the array's device address
  *    (cudaGetSymbolAddress) once; make that first call before any stream capture.
  *  - Every call shares the one array, which keeps the previous call's contents: every scratch byte

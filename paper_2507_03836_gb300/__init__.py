@@ -102,6 +102,7 @@ _SIGS = {
     "fhash_level_info": [_vp, ctypes.POINTER(_i32), _vp, _vp, _vp],
     "fhash_write_state": [_vp, _i32, _u64, _u64, _vp, _vp],
     "fhash_read_occupancy": [_vp, _i64, _vp, _vp],
+    "fhash_read_active": [_vp, _i32, _u64, _u64, _vp, _vp],
     "fhash_check": [_vp, _vp],
     "fhash_save": [_vp, ctypes.c_char_p],
     "fhash_diag_wait_timeout": [_vp, _u64, _vp],
@@ -193,7 +194,7 @@ def make_schedule(mode="explicit", res=None, fold=2, levels_rule=LEVELS_MAX, n_l
     return s
 
 
-LAYOUT_LINEAR, LAYOUT_BRICK = 0, 1
+LAYOUT_LINEAR, LAYOUT_BRICK, LAYOUT_MASKED = 0, 1, 2
 
 
 def fhash_build(nx, ny, nz, nt, mask=None, schedule=None, F=2, dtype=FP32, mlp_hidden_layers=2, mlp_width=64,
@@ -326,6 +327,12 @@ def fhash_write_state(model, which, offset, buf, stream=None):
 
 def fhash_read_occupancy(model, t, out, stream=None):
     _ok(_lib.fhash_read_occupancy(model.handle, int(t), _ptr(out), _stream(stream)))
+
+
+def fhash_read_active(model, level, word0, out, stream=None):
+    """Active-vertex bit words [word0, word0 + len(out)) of a masked level into `out` (uint64)."""
+    n = out.numel() if hasattr(out, "numel") else out.size
+    _ok(_lib.fhash_read_active(model.handle, int(level), int(word0), int(n), _ptr(out), _stream(stream)))
 
 
 def fhash_compute_grads_noalloc(model, coords, target, loss=None, stream=None):

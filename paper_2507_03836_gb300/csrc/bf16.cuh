@@ -42,7 +42,7 @@ __device__ __forceinline__ void load_row_bf16(const __nv_bfloat16* __restrict__ 
 template <int F, int LAYOUT = -1>
 __device__ __forceinline__ void interp_level_bf16(const __nv_bfloat16* __restrict__ T, const Corners& k, float* out) {
     float v[16][F];
-    if (LAYOUT < 0 ? k.brick != 0 : LAYOUT == 1) {
+    if (LAYOUT < 0 ? k.layout == 1u : LAYOUT == 1) {  // masked levels never reach the bf16 form
 #pragma unroll
         for (int c = 0; c < 16; ++c) load_row_bf16<F>(T, corner_row<1>(k, c), v[c]);
     } else {

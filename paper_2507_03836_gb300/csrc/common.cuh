@@ -32,7 +32,9 @@ struct Level {
     uint32_t sy, sz;  // Rx, Rx*Ry
     uint64_t st;      // Rx*Ry*Rz
     uint64_t base;    // first row of the level
-    int32_t brick;    // row order inside a time slice: 0 = Eq. 9, 1 = 4x4x4 bricks (FHASH_LAYOUT_BRICK)
+    uint64_t nrows;   // rows of the level: Rx*Ry*Rz*Rt, or its active vertices (FHASH_LAYOUT_MASKED)
+    const uint4* dir; // masked levels: per 64 Eq. 9 rows {active bits lo, hi, active rows before lo, hi}
+    int32_t layout;   // FHASH_LAYOUT_LINEAR (Eq. 9), _BRICK (4x4x4 bricks per time slice) or _MASKED
 };
 
 struct Levels {
@@ -76,6 +78,10 @@ struct fhash_model {
     uint32_t* occ = nullptr;
     uint8_t* occ_any = nullptr;  // per brick: any bit set
     int64_t nbx = 0, nby = 0, nbz = 0;
+
+    // FHASH_LAYOUT_MASKED: the active-vertex directories of all levels, one record per 64 Eq. 9 rows
+    uint4* dir = nullptr;
+    uint64_t dir_words = 0;
 
     int* err_word = nullptr;  // device error word (0 = ok)
 
@@ -128,8 +134,24 @@ struct Corners {
     uint32_t ox, oy, oz;
     uint64_t ot;
     float wx, wy, wz, wt;
-    uint32_t brick, cx, cy, cz, Rx, Ry, Rz;
+    uint32_t layout, cx, cy, cz, Rx, Ry, Rz;
+    const uint4* dir;  // masked levels: r0 is the Eq. 9 row within the level, mapped through dir
+    uint64_t mbase;
 };
+
+// Row returned for an inactive corner of a masked level: it reads 0 and takes no gradient.
+constexpr uint64_t kInactiveRow = ~0ull;
+
+// Row of the vertex with Eq. 9 row r (within a masked level): the level's base plus the number of
+// active rows before r (the record's prefix count and a popcount inside its 64-row word), or
+// kInactiveRow when the vertex is not active.
+__device__ __forceinline__ uint64_t masked_row(const uint4* __restrict__ dir, uint64_t base, uint64_t r) {
+    const uint4 d = __ldg(dir + (r >> 6));
+    const uint64_t bits = ((uint64_t)d.y << 32) | d.x;
+    const uint32_t i = (uint32_t)r & 63u;
+    if (!((bits >> i) & 1ull)) return kInactiveRow;
+    return base + ((((uint64_t)d.w) << 32) | d.z) + (uint64_t)__popcll(bits & ((1ull << i) - 1ull));
+}
 
 // Row of vertex (x, y, z) inside a time slice in the brick layout (Section 3.2.3 allows other
 // linearisations than Eq. 9): 4x4x4 bricks in (bz, by, bx) order, vertices in (iz, iy, ix) order
@@ -141,9 +163,9 @@ __device__ __forceinline__ uint32_t brick_row3(uint32_t x, uint32_t y, uint32_t 
     return 4u * bz * Rx * Ry + wz * (4u * by * Rx + wy * 4u * bx) + ((z & 3u) * wy + (y & 3u)) * wx + (x & 3u);
 }
 
-// LAYOUT: 0 = Eq. 9, 1 = bricks, -1 = read from the level (kernels over one level per thread take the
-// runtime form; kernels that walk all levels of a sample are instantiated per layout, so that no
-// branch sits between the gathers of consecutive levels).
+// LAYOUT: 0 = Eq. 9, 1 = bricks, 2 = masked, -1 = read from the level (kernels over one level per thread
+// take the runtime form; kernels that walk all levels of a sample are instantiated per layout, so that
+// no branch sits between the gathers of consecutive levels).
 template <int LAYOUT = -1>
 __device__ __forceinline__ Corners corners(const Level& L, float4 u) {
     int cx, cy, cz, ct, dx, dy, dz, dt;
@@ -153,15 +175,17 @@ __device__ __forceinline__ Corners corners(const Level& L, float4 u) {
     cell(u.z, L.R[2], L.Rm1[2], cz, dz, k.wz);
     cell(u.w, L.R[3], L.Rm1[3], ct, dt, k.wt);
     k.ot = dt ? L.st : 0ull;
-    const bool brick = LAYOUT < 0 ? L.brick != 0 : LAYOUT == 1;
-    k.brick = brick ? 1u : 0u;
-    if (brick) {
+    const int lay = LAYOUT < 0 ? L.layout : LAYOUT;
+    k.layout = (uint32_t)lay;
+    k.dir = L.dir;
+    k.mbase = L.base;
+    if (lay == 1) {
         k.r0 = L.base + (uint64_t)ct * L.st;
         k.ox = dx; k.oy = dy; k.oz = dz;
         k.cx = cx; k.cy = cy; k.cz = cz;
         k.Rx = L.R[0]; k.Ry = L.R[1]; k.Rz = L.R[2];
     } else {
-        k.r0 = L.base + (uint64_t)ct * L.st + (uint64_t)cz * L.sz + (uint64_t)cy * L.sy + (uint64_t)cx;
+        k.r0 = (lay == 2 ? 0ull : L.base) + (uint64_t)ct * L.st + (uint64_t)cz * L.sz + (uint64_t)cy * L.sy + (uint64_t)cx;
         k.ox = dx;
         k.oy = dy ? L.sy : 0u;
         k.oz = dz ? L.sz : 0u;
@@ -170,15 +194,18 @@ __device__ __forceinline__ Corners corners(const Level& L, float4 u) {
     return k;
 }
 
-// Row of corner c = i + 2j + 4k + 8s (i, j, k: upper corner on x, y, z; s = 1 for t_Next).
+// Row of corner c = i + 2j + 4k + 8s (i, j, k: upper corner on x, y, z; s = 1 for t_Next); kInactiveRow
+// for an inactive corner of a masked level.
 template <int LAYOUT = -1>
 __device__ __forceinline__ uint64_t corner_row(const Corners& k, int c) {
-    const bool brick = LAYOUT < 0 ? k.brick != 0 : LAYOUT == 1;
-    if (brick)
+    const int lay = LAYOUT < 0 ? (int)k.layout : LAYOUT;
+    if (lay == 1)
         return k.r0 + ((c & 8) ? k.ot : 0ull) +
                brick_row3(k.cx + ((c & 1) ? k.ox : 0u), k.cy + ((c & 2) ? k.oy : 0u), k.cz + ((c & 4) ? k.oz : 0u),
                           k.Rx, k.Ry, k.Rz);
-    return k.r0 + ((c & 8) ? k.ot : 0ull) + ((c & 4) ? k.oz : 0u) + ((c & 2) ? k.oy : 0u) + ((c & 1) ? k.ox : 0u);
+    const uint64_t r = k.r0 + ((c & 8) ? k.ot : 0ull) + ((c & 4) ? k.oz : 0u) + ((c & 2) ? k.oy : 0u) + ((c & 1) ? k.ox : 0u);
+    if (lay == 2) return masked_row(k.dir, k.mbase, r);
+    return r;
 }
 
 __device__ __forceinline__ void raise_error(int* word, int code) {

@@ -32,9 +32,21 @@ __device__ __forceinline__ void load_row(const float* __restrict__ T, uint64_t r
 template <int F, int LAYOUT = -1>
 __device__ __forceinline__ void interp_level(const float* __restrict__ T, const Corners& k, float* out) {
     float v[16][F];
-    if (LAYOUT < 0 ? k.brick != 0 : LAYOUT == 1) {
+    const int lay = LAYOUT < 0 ? (int)k.layout : LAYOUT;
+    if (lay == 1) {
 #pragma unroll
         for (int c = 0; c < 16; ++c) load_row<F>(T, corner_row<1>(k, c), v[c]);
+    } else if (lay == 2) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const uint64_t r = corner_row<2>(k, c);
+            if (r != kInactiveRow) {
+                load_row<F>(T, r, v[c]);
+            } else {
+#pragma unroll
+                for (int f = 0; f < F; ++f) v[c][f] = 0.0f;  // an inactive corner reads 0
+            }
+        }
     } else {
 #pragma unroll
         for (int c = 0; c < 16; c += 2) {
@@ -307,7 +319,9 @@ __device__ __forceinline__ void scatter_sample(const Levels& lv, float* __restri
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
             float w = corner_weight(k, c);
-            float* dst = G + corner_row<LAYOUT>(k, c) * F;
+            const uint64_t r = corner_row<LAYOUT>(k, c);
+            if (LAYOUT == 2 && r == kInactiveRow) continue;  // inactive corners take no gradient
+            float* dst = G + r * F;
             if constexpr (F == 2) {
                 red_add2(dst, w * g[0], w * g[1]);
             } else if constexpr (F == 4) {
@@ -402,7 +416,11 @@ cudaError_t run_fused_layout(int which, const FusedArgs& a) {
 // All levels of a model share one layout; the per-sample kernels are instantiated for each.
 template <int F>
 cudaError_t run_fused(int which, const FusedArgs& a) {
-    return a.lv->lv[0].brick ? run_fused_layout<F, 1>(which, a) : run_fused_layout<F, 0>(which, a);
+    switch (a.lv->lv[0].layout) {
+        case FHASH_LAYOUT_BRICK: return run_fused_layout<F, 1>(which, a);
+        case FHASH_LAYOUT_MASKED: return run_fused_layout<F, 2>(which, a);
+        default: return run_fused_layout<F, 0>(which, a);
+    }
 }
 
 }  // namespace fh

@@ -210,7 +210,7 @@ static cudaError_t run_tc(fhash_model* m, bool train, FusedArgs& a) {
 // All levels of a model share one layout; the kernel is instantiated for each.
 template <int F>
 static cudaError_t run_tc_f(fhash_model* m, bool train, FusedArgs& a) {
-    return m->lv.lv[0].brick ? run_tc<F, 1>(m, train, a) : run_tc<F, 0>(m, train, a);
+    return m->lv.lv[0].layout == FHASH_LAYOUT_BRICK ? run_tc<F, 1>(m, train, a) : run_tc<F, 0>(m, train, a);
 }
 
 cudaError_t run_tc_any(fhash_model* m, bool train, FusedArgs& a) {

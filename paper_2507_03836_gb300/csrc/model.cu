@@ -180,6 +180,176 @@ __global__ void k_occ_read(const uint32_t* __restrict__ words, int sx, int sy, i
     }
 }
 
+// ------------------------------------------------------------------ masked compact tables
+// FHASH_LAYOUT_MASKED keeps table rows only for the vertices near the features (the irregular grids
+// of Section 3.1's feature-only coreset).  The active vertices of a level are the corners of the cells
+// that the float32 cell step assigns to the footprint of some dilated-feature voxel.  Footprint and
+// cells are products over the axes, so the active grid is the dilated mask over the FBB resampled
+// axis by axis with OR over the voxels whose footprint reaches each vertex.
+
+// The dilated mask over the Feature Bounding Box, [nt][sz][sy][sx] bytes 0/1.
+__global__ void k_fbb_copy(const uint8_t* __restrict__ dil, int64_t nx, int64_t ny, int64_t nz, int64_t lx,
+                           int64_t ly, int64_t lz, int64_t sx, int64_t sy, int64_t sz, int64_t nt,
+                           uint8_t* __restrict__ out) {
+    const int64_t n = sx * sy * sz * nt;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = e % sx, y = (e / sx) % sy, z = (e / (sx * sy)) % sz, t = e / (sx * sy * sz);
+        out[e] = dil[((t * nz + lz + z) * ny + ly + y) * nx + lx + x] != 0 ? 1 : 0;
+    }
+}
+
+// out[o][X][i] = OR of in[o][v][i] over the voxels v in range[X] (one axis of the active grid);
+// range[X] lies inside [0, S) or is empty (x > y).
+__global__ void k_or_resample(const uint8_t* __restrict__ in, uint8_t* __restrict__ out, int64_t n_outer, int S,
+                              int R, int64_t n_inner, const int2* __restrict__ range) {
+    const int64_t n = n_outer * R * n_inner;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % n_inner, q = e / n_inner;
+        const int X = (int)(q % R);
+        const int64_t o = q / R;
+        const int2 ab = range[X];
+        const uint8_t* p = in + o * S * n_inner + i;
+        uint8_t a = 0;
+        for (int v = ab.x; v <= ab.y && !a; ++v) a = p[(int64_t)v * n_inner];
+        out[e] = a ? 1 : 0;
+    }
+}
+
+// Bit i of 64-bit word w = grid[64 w + i] (0 past n), one 32-bit ballot per warp.  The loop bound is a
+// multiple of 32, so the lanes of a warp stay in the loop together.
+__global__ void k_pack_active(const uint8_t* __restrict__ grid, uint64_t n, uint64_t nwords, uint32_t* __restrict__ bits) {
+    const uint64_t total = nwords * 64;
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < total; r += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned b = __ballot_sync(0xffffffffu, r < n && grid[r] != 0);
+        if ((threadIdx.x & 31) == 0) bits[r >> 5] = b;
+    }
+}
+
+static int64_t floor_div(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Active vertices [lo, hi] of a level axis with R vertices for voxel v of the S voxels of the FBB on a
+// spatial axis (footprint u*(S-1) in [v - 1/2, v + 1/2]) or for step v of S on the time axis
+// (t*(S-1) in [v - 1, v + 1]); in level units p = u*(R-1), widened by 1/64, cells
+// clamp(floor(p), 0, R-2), vertices up to the last cell + 1.  Exact integer arithmetic.
+static void active_range(int64_t v, int64_t S, int64_t R, bool time, int64_t& lo, int64_t& hi) {
+    if (R == 1) { lo = hi = 0; return; }
+    if (S == 1) { lo = 0; hi = R - 1; return; }
+    const int64_t den = 64 * (S - 1);
+    const int64_t nlo = time ? (v - 1) * (R - 1) * 64 - (S - 1) : (2 * v - 1) * (R - 1) * 32 - (S - 1);
+    const int64_t nhi = time ? (v + 1) * (R - 1) * 64 + (S - 1) : (2 * v + 1) * (R - 1) * 32 + (S - 1);
+    lo = std::min(std::max(floor_div(nlo, den), (int64_t)0), R - 2);
+    hi = std::min(std::max(floor_div(nhi, den), (int64_t)0), R - 2) + 1;
+}
+
+// For every vertex X of an axis, the voxels whose active range holds X.  Both ends of the range grow
+// with v, so these voxels form an interval; an empty one is (1, 0).
+static std::vector<int2> inverse_ranges(int64_t S, int64_t R, bool time) {
+    std::vector<int2> r((size_t)R, make_int2(INT32_MAX, -1));
+    for (int64_t v = 0; v < S; ++v) {
+        int64_t lo, hi;
+        active_range(v, S, R, time, lo, hi);
+        for (int64_t X = lo; X <= hi; ++X) {
+            r[X].x = std::min<int>(r[X].x, (int)v);
+            r[X].y = std::max<int>(r[X].y, (int)v);
+        }
+    }
+    for (auto& e : r)
+        if (e.y < 0) e = make_int2(1, 0);
+    return r;
+}
+
+static uint64_t level_dense_rows(const Level& v) { return v.st * (uint64_t)v.R[3]; }
+
+// Points each masked level at its directory inside m->dir (records of the levels back to back).
+static void link_dirs(fhash_model* m) {
+    uint64_t off = 0;
+    for (int l = 0; l < m->lv.L; ++l) {
+        Level& v = m->lv.lv[l];
+        v.dir = m->dir ? m->dir + off : nullptr;
+        off += (level_dense_rows(v) + 63) / 64;
+    }
+}
+
+struct DevTmp {
+    void* p = nullptr;
+    ~DevTmp() { if (p) cudaFree(p); }
+};
+
+// Builds the active-vertex directories and the compact bases (levels' R, sy, sz, st already set).
+// dil: the dilated mask of the whole volume on the device, or null (no mask: every vertex active).
+static fhash_status build_masked(fhash_model* m, const uint8_t* dil, cudaStream_t st) {
+    const int L = m->lv.L;
+    const int64_t sx = m->fbb_size[0], sy = m->fbb_size[1], sz = m->fbb_size[2], T = m->nt;
+    uint64_t words = 0, max_words = 0;
+    size_t cap = 1;
+    int64_t max_axis = 1;
+    for (int l = 0; l < L; ++l) {
+        const Level& v = m->lv.lv[l];
+        const int64_t Rx = v.R[0], Ry = v.R[1], Rz = v.R[2], Rt = v.R[3];
+        const uint64_t nw = (level_dense_rows(v) + 63) / 64;
+        words += nw;
+        max_words = std::max(max_words, nw);
+        cap = std::max<size_t>(cap, (size_t)std::max({T * sz * sy * Rx, T * sz * Ry * Rx, T * Rz * Ry * Rx, Rt * Rz * Ry * Rx}));
+        max_axis = std::max({max_axis, Rx, Ry, Rz, Rt});
+    }
+    m->dir_words = words;
+    FH_TRY(dev_alloc(m, (void**)&m->dir, (size_t)words * sizeof(uint4)));
+    link_dirs(m);
+    DevTmp fbb, P, Q, bits, rng;
+    if (dil) {
+        FH_CUDA(cudaMalloc(&fbb.p, (size_t)(sx * sy * sz * T)));
+        k_fbb_copy<<<num_sms() * 8, 256, 0, st>>>(dil, m->desc.nx, m->desc.ny, m->desc.nz, m->fbb_lo[0], m->fbb_lo[1],
+                                                  m->fbb_lo[2], sx, sy, sz, T, (uint8_t*)fbb.p);
+        FH_CUDA(cudaGetLastError());
+        FH_CUDA(cudaMalloc(&P.p, cap));
+    }
+    FH_CUDA(cudaMalloc(&Q.p, cap));
+    FH_CUDA(cudaMalloc(&bits.p, (size_t)max_words * 8));
+    FH_CUDA(cudaMalloc(&rng.p, (size_t)max_axis * 4 * sizeof(int2)));
+    std::vector<uint64_t> hb((size_t)max_words);
+    std::vector<uint4> rec((size_t)max_words);
+    const unsigned grid = (unsigned)(num_sms() * 8);
+    uint64_t acc = 0;
+    for (int l = 0; l < L; ++l) {
+        Level& v = m->lv.lv[l];
+        const int64_t Rx = v.R[0], Ry = v.R[1], Rz = v.R[2], Rt = v.R[3];
+        const uint64_t n = level_dense_rows(v), nw = (n + 63) / 64;
+        uint8_t* g = (uint8_t*)Q.p;
+        if (dil) {
+            std::vector<int2> ax[4] = {inverse_ranges(sx, Rx, false), inverse_ranges(sy, Ry, false),
+                                       inverse_ranges(sz, Rz, false), inverse_ranges(T, Rt, true)};
+            int2* dr = (int2*)rng.p;
+            const int64_t off[4] = {0, max_axis, 2 * max_axis, 3 * max_axis};
+            for (int a = 0; a < 4; ++a)
+                FH_CUDA(cudaMemcpyAsync(dr + off[a], ax[a].data(), ax[a].size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+            uint8_t *A = (uint8_t*)fbb.p, *B = (uint8_t*)P.p, *C = (uint8_t*)Q.p;
+            k_or_resample<<<grid, 256, 0, st>>>(A, B, T * sz * sy, (int)sx, (int)Rx, 1, dr + off[0]);
+            k_or_resample<<<grid, 256, 0, st>>>(B, C, T * sz, (int)sy, (int)Ry, Rx, dr + off[1]);
+            k_or_resample<<<grid, 256, 0, st>>>(C, B, T, (int)sz, (int)Rz, Ry * Rx, dr + off[2]);
+            k_or_resample<<<grid, 256, 0, st>>>(B, C, 1, (int)T, (int)Rt, Rz * Ry * Rx, dr + off[3]);
+            FH_CUDA(cudaGetLastError());
+        } else {
+            FH_CUDA(cudaMemsetAsync(g, 1, (size_t)n, st));
+        }
+        k_pack_active<<<grid, 256, 0, st>>>(g, n, nw, (uint32_t*)bits.p);
+        FH_CUDA(cudaGetLastError());
+        FH_CUDA(cudaMemcpyAsync(hb.data(), bits.p, (size_t)nw * 8, cudaMemcpyDeviceToHost, st));
+        FH_CUDA(cudaStreamSynchronize(st));  // also retires the range uploads before ax goes away
+        uint64_t cnt = 0;
+        for (uint64_t w = 0; w < nw; ++w) {
+            rec[w] = make_uint4((uint32_t)hb[w], (uint32_t)(hb[w] >> 32), (uint32_t)cnt, (uint32_t)(cnt >> 32));
+            cnt += (uint64_t)__builtin_popcountll(hb[w]);
+        }
+        FH_CUDA(cudaMemcpyAsync((void*)v.dir, rec.data(), (size_t)nw * sizeof(uint4), cudaMemcpyHostToDevice, st));
+        FH_CUDA(cudaStreamSynchronize(st));
+        v.base = acc;
+        v.nrows = cnt;
+        acc += cnt;
+    }
+    m->total_rows = acc;
+    return FHASH_OK;
+}
+
 // ------------------------------------------------------------------ schedule (host)
 static int ceil_log(int f, int64_t s) {
     int L = 0;
@@ -234,7 +404,7 @@ static fhash_status make_schedule(const fhash_schedule& sc, const int64_t S[3], 
 static void destroy_model(fhash_model* m) {
     if (!m) return;
     cudaDeviceSynchronize();
-    void* ps[] = {m->param, m->grad, m->adam_m, m->adam_v, m->shadow, m->occ, m->occ_any, m->err_word,
+    void* ps[] = {m->param, m->grad, m->adam_m, m->adam_v, m->shadow, m->occ, m->occ_any, m->dir, m->err_word,
                   m->s_coords.p, m->s_target.p, m->s_out.p, m->s_acts.p, m->s_gacts.p, m->s_partial.p,
                   m->s_loss.p, m->s_misc.p, m->s_render.p, m->s_enc.p, m->s_cs_ent.p, m->s_cs_val.p};
     for (void* p : ps)
@@ -265,8 +435,11 @@ fhash_status fhash_build(const fhash_build_desc* d, fhash_stream stream, fhash_m
     if (d->mlp_width != 16 && d->mlp_width != 32 && d->mlp_width != 64)
         return set_error(FHASH_EINVAL, "mlp_width must be 16, 32 or 64");
     if (!(d->init_range >= 0.0f)) return set_error(FHASH_EINVAL, "init_range");
-    if (d->layout != FHASH_LAYOUT_LINEAR && d->layout != FHASH_LAYOUT_BRICK)
-        return set_error(FHASH_EINVAL, "layout must be FHASH_LAYOUT_LINEAR or FHASH_LAYOUT_BRICK");
+    if (d->layout != FHASH_LAYOUT_LINEAR && d->layout != FHASH_LAYOUT_BRICK && d->layout != FHASH_LAYOUT_MASKED)
+        return set_error(FHASH_EINVAL, "layout must be FHASH_LAYOUT_LINEAR, _BRICK or _MASKED");
+    if (d->layout == FHASH_LAYOUT_MASKED && d->dtype != FHASH_FP32)
+        return set_error(FHASH_EINVAL, "FHASH_LAYOUT_MASKED takes dtype FHASH_FP32");
+    const bool masked = d->layout == FHASH_LAYOUT_MASKED;
 
     fhash_model* m = new fhash_model();
     m->desc = *d;
@@ -283,15 +456,19 @@ fhash_status fhash_build(const fhash_build_desc* d, fhash_stream stream, fhash_m
 
     // ---- feature dilation, per-frame boxes, FBB (Section 3.1)
     const int64_t nx = d->nx, ny = d->ny, nz = d->nz, nt = d->nt, n3 = nx * ny * nz;
-    uint8_t* dil = nullptr;  // dilated mask, all frames
+    uint8_t* dil = nullptr;  // dilated mask, all frames (kept for the masked directories)
+    struct DilGuard {
+        uint8_t*& p;
+        ~DilGuard() { if (p) cudaFree(p); }
+    } dil_guard{dil};
     if (d->mask) {
         uint8_t* stage = nullptr;
         int* boxes = nullptr;
         FH_CUDA(cudaMalloc(&stage, n3));
         cudaError_t e = cudaMalloc(&dil, (size_t)(n3 * nt));
-        if (e != cudaSuccess) { cudaFree(stage); return cuda_error(e, "cudaMalloc(dilated mask)"); }
+        if (e != cudaSuccess) { dil = nullptr; cudaFree(stage); return cuda_error(e, "cudaMalloc(dilated mask)"); }
         e = cudaMalloc(&boxes, sizeof(int) * 6 * nt);
-        if (e != cudaSuccess) { cudaFree(stage); cudaFree(dil); return cuda_error(e, "cudaMalloc(boxes)"); }
+        if (e != cudaSuccess) { cudaFree(stage); return cuda_error(e, "cudaMalloc(boxes)"); }
         std::vector<int> hb(6 * nt);
         for (int64_t t = 0; t < nt; ++t) { hb[6 * t + 0] = hb[6 * t + 1] = hb[6 * t + 2] = INT32_MAX; hb[6 * t + 3] = hb[6 * t + 4] = hb[6 * t + 5] = -1; }
         cudaMemcpyAsync(boxes, hb.data(), sizeof(int) * 6 * nt, cudaMemcpyHostToDevice, st);
@@ -304,13 +481,13 @@ fhash_status fhash_build(const fhash_build_desc* d, fhash_stream stream, fhash_m
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         cudaFree(stage);
         cudaFree(boxes);
-        if (e != cudaSuccess) { cudaFree(dil); return cuda_error(e, "feature dilation"); }
+        if (e != cudaSuccess) return cuda_error(e, "feature dilation");
         int64_t lo[3] = {INT64_MAX, INT64_MAX, INT64_MAX}, hi[3] = {-1, -1, -1};
         for (int64_t t = 0; t < nt; ++t) {
             if (hb[6 * t + 3] < 0) continue;  // empty frame
             for (int a = 0; a < 3; ++a) { lo[a] = std::min<int64_t>(lo[a], hb[6 * t + a]); hi[a] = std::max<int64_t>(hi[a], hb[6 * t + 3 + a]); }
         }
-        if (hi[0] < 0) { cudaFree(dil); return set_error(FHASH_EINVAL, "feature mask is empty"); }
+        if (hi[0] < 0) return set_error(FHASH_EINVAL, "feature mask is empty");
         for (int a = 0; a < 3; ++a) { m->fbb_lo[a] = lo[a]; m->fbb_size[a] = hi[a] - lo[a] + 1; }
     } else {
         m->fbb_lo[0] = m->fbb_lo[1] = m->fbb_lo[2] = 0;
@@ -323,7 +500,7 @@ fhash_status fhash_build(const fhash_build_desc* d, fhash_stream stream, fhash_m
     const int64_t nbrick = m->nbx * m->nby * m->nbz;
     fhash_status s = dev_alloc(m, (void**)&m->occ, (size_t)(nbrick * 16 * 4 * nt));
     if (s == FHASH_OK) s = dev_alloc(m, (void**)&m->occ_any, (size_t)(nbrick * nt));
-    if (s != FHASH_OK) { if (dil) cudaFree(dil); return s; }
+    if (s != FHASH_OK) return s;
     if (dil) {
         for (int64_t t = 0; t < nt; ++t)
             k_occupancy<<<(unsigned)nbrick, 512, 0, st>>>(dil + t * n3, (int)nx, (int)ny, (int)m->fbb_lo[0], (int)m->fbb_lo[1],
@@ -331,8 +508,8 @@ fhash_status fhash_build(const fhash_build_desc* d, fhash_stream stream, fhash_m
                                                           m->occ + t * nbrick * 16, m->occ_any + t * nbrick);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        cudaFree(dil);
         if (e != cudaSuccess) return cuda_error(e, "occupancy");
+        if (!masked) { cudaFree(dil); dil = nullptr; }
     } else {
         // every voxel occupied; unused bits of partial bricks are never read
         FH_CUDA(cudaMemsetAsync(m->occ, 0xff, (size_t)(nbrick * 16 * 4 * nt), st));
@@ -358,11 +535,17 @@ fhash_status fhash_build(const fhash_build_desc* d, fhash_stream stream, fhash_m
         if (sxyz >= (1ull << 32)) return set_error(FHASH_EINVAL, "level %d: Rx*Ry*Rz too large", l);
         v.st = sxyz;
         v.base = acc;
-        v.brick = d->layout == FHASH_LAYOUT_BRICK ? 1 : 0;
-        acc += sxyz * (uint64_t)res[l][3];
+        v.nrows = sxyz * (uint64_t)res[l][3];
+        v.dir = nullptr;
+        v.layout = d->layout;
+        acc += v.nrows;
     }
     m->total_rows = acc;
-    m->n_table = acc * (uint64_t)d->F;
+    if (masked) {
+        FH_TRY(build_masked(m, dil, st));  // compact bases, row counts and directories
+        if (dil) { cudaFree(dil); dil = nullptr; }
+    }
+    m->n_table = m->total_rows * (uint64_t)d->F;
 
     MlpShape& sh = m->mlp;
     sh.in = L * d->F;
@@ -515,6 +698,23 @@ fhash_status fhash_read_occupancy(fhash_model* m, int64_t t, uint8_t* out, fhash
     return FHASH_OK;
 }
 
+fhash_status fhash_read_active(fhash_model* m, int32_t level, uint64_t word0, uint64_t n_words, uint64_t* bits,
+                               fhash_stream stream) {
+    if (!m || (!bits && n_words)) return set_error(FHASH_EINVAL, "fhash_read_active: null argument");
+    if (m->desc.layout != FHASH_LAYOUT_MASKED || !m->dir)
+        return set_error(FHASH_EINVAL, "fhash_read_active: the model does not use FHASH_LAYOUT_MASKED");
+    if (level < 0 || level >= m->lv.L) return set_error(FHASH_EINVAL, "fhash_read_active: level out of range");
+    const Level& v = m->lv.lv[level];
+    const uint64_t nw = (level_dense_rows(v) + 63) / 64;
+    if (word0 > nw || n_words > nw - word0) return set_error(FHASH_EINVAL, "fhash_read_active: words out of range");
+    if (!n_words) return FHASH_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the low 8 bytes of each 16-byte record are the bits
+    FH_CUDA(cudaMemcpy2DAsync(bits, 8, v.dir + word0, sizeof(uint4), 8, (size_t)n_words, cudaMemcpyDefault, st));
+    if (!is_device_ptr(bits)) FH_CUDA(cudaStreamSynchronize(st));
+    return FHASH_OK;
+}
+
 fhash_status fhash_check(fhash_model* m, fhash_stream stream) {
     if (!m) return set_error(FHASH_EINVAL, "fhash_check: null model");
     FH_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
@@ -540,6 +740,7 @@ struct CkptHeader {
     MlpShape mlp;
     uint64_t total_rows, n_table, n_params;
     int64_t fbb_lo[3], fbb_size[3], nt, step, nbx, nby, nbz;
+    uint64_t dir_words;  // masked layout: directory records after the occupancy grid
 };
 static const char kMagic[8] = {'F', 'H', 'A', 'S', 'H', 'C', 'K', '1'};
 
@@ -572,7 +773,7 @@ fhash_status fhash_save(const fhash_model* mc, const char* path) {
     CkptHeader h;
     memset(&h, 0, sizeof h);
     memcpy(h.magic, kMagic, 8);
-    h.version = 2;  // 2: levels carry their row layout
+    h.version = 3;  // 2: levels carry their row layout; 3: masked directories
     h.header_bytes = sizeof h;
     h.desc = m->desc;
     h.desc.mask = nullptr;
@@ -581,15 +782,19 @@ fhash_status fhash_save(const fhash_model* mc, const char* path) {
     h.total_rows = m->total_rows; h.n_table = m->n_table; h.n_params = m->n_params;
     for (int a = 0; a < 3; ++a) { h.fbb_lo[a] = m->fbb_lo[a]; h.fbb_size[a] = m->fbb_size[a]; }
     h.nt = m->nt; h.step = m->step; h.nbx = m->nbx; h.nby = m->nby; h.nbz = m->nbz;
+    h.dir_words = m->dir ? m->dir_words : 0;
+    for (int l = 0; l < h.lv.L; ++l) h.lv.lv[l].dir = nullptr;  // device addresses are not saved
     fhash_status rc = FHASH_OK;
     if (fwrite(&h, sizeof h, 1, f) != 1) rc = set_error(FHASH_EIO, "fhash_save: write failed");
     const size_t pin_bytes = 64u << 20;
     void* pin = nullptr;
     if (rc == FHASH_OK && cudaMallocHost(&pin, pin_bytes) != cudaSuccess) rc = set_error(FHASH_ENOMEM, "fhash_save: pinned buffer");
     const uint64_t nb = (uint64_t)(m->nbx * m->nby * m->nbz * m->nt);
-    void* arrays[] = {m->param, m->grad, m->adam_m, m->adam_v, m->occ, m->occ_any};
-    const uint64_t sizes[] = {m->n_params * 4, m->n_params * 4, m->n_params * 4, m->n_params * 4, nb * 64, nb};
-    for (int i = 0; i < 6 && rc == FHASH_OK; ++i) rc = stream_file(f, arrays[i], sizes[i], true, pin, pin_bytes);
+    void* arrays[] = {m->param, m->grad, m->adam_m, m->adam_v, m->occ, m->occ_any, m->dir};
+    const uint64_t sizes[] = {m->n_params * 4, m->n_params * 4, m->n_params * 4, m->n_params * 4, nb * 64, nb,
+                              h.dir_words * sizeof(uint4)};
+    for (int i = 0; i < 7 && rc == FHASH_OK; ++i)
+        if (sizes[i]) rc = stream_file(f, arrays[i], sizes[i], true, pin, pin_bytes);
     if (pin) cudaFreeHost(pin);
     if (fclose(f) != 0 && rc == FHASH_OK) rc = set_error(FHASH_EIO, "fhash_save: close failed");
     return rc;
@@ -601,7 +806,7 @@ fhash_status fhash_load(const char* path, fhash_stream stream, fhash_model** out
     FILE* f = fopen(path, "rb");
     if (!f) return set_error(FHASH_EIO, "fhash_load: cannot open %s", path);
     CkptHeader h;
-    if (fread(&h, sizeof h, 1, f) != 1 || memcmp(h.magic, kMagic, 8) != 0 || h.version != 2 ||
+    if (fread(&h, sizeof h, 1, f) != 1 || memcmp(h.magic, kMagic, 8) != 0 || h.version != 3 ||
         h.header_bytes != sizeof h || h.lv.L < 1 || h.lv.L > FHASH_MAX_LEVELS || h.n_params < h.n_table) {
         fclose(f);
         return set_error(FHASH_EIO, "fhash_load: %s is not an F-Hash checkpoint of this version", path);
@@ -630,13 +835,19 @@ fhash_status fhash_load(const char* path, fhash_stream stream, fhash_model** out
     if (m->desc.dtype == FHASH_BF16) FH_TRY(dev_alloc(m, (void**)&m->shadow, (size_t)m->n_params * 2));
     FH_TRY(dev_alloc(m, (void**)&m->occ, (size_t)nb * 64));
     FH_TRY(dev_alloc(m, (void**)&m->occ_any, (size_t)nb));
+    if (h.dir_words) {
+        m->dir_words = h.dir_words;
+        FH_TRY(dev_alloc(m, (void**)&m->dir, (size_t)h.dir_words * sizeof(uint4)));
+    }
+    link_dirs(m);
     const size_t pin_bytes = 64u << 20;
     void* pin = nullptr;
     if (cudaMallocHost(&pin, pin_bytes) != cudaSuccess) return set_error(FHASH_ENOMEM, "fhash_load: pinned buffer");
-    void* arrays[] = {m->param, m->grad, m->adam_m, m->adam_v, m->occ, m->occ_any};
-    const uint64_t sizes[] = {bytes, bytes, bytes, bytes, nb * 64, nb};
+    void* arrays[] = {m->param, m->grad, m->adam_m, m->adam_v, m->occ, m->occ_any, m->dir};
+    const uint64_t sizes[] = {bytes, bytes, bytes, bytes, nb * 64, nb, h.dir_words * sizeof(uint4)};
     fhash_status rc = FHASH_OK;
-    for (int i = 0; i < 6 && rc == FHASH_OK; ++i) rc = stream_file(f, arrays[i], sizes[i], false, pin, pin_bytes);
+    for (int i = 0; i < 7 && rc == FHASH_OK; ++i)
+        if (sizes[i]) rc = stream_file(f, arrays[i], sizes[i], false, pin, pin_bytes);
     cudaFreeHost(pin);
     if (rc != FHASH_OK) return rc;
     FH_TRY(refresh_shadow(m, 0, m->n_params, (cudaStream_t)stream));

@@ -45,6 +45,8 @@ using namespace fh;
 extern "C" fhash_status fhash_compute_grads_noalloc(fhash_model* m, const float* coords, const float* target, int64_t n,
                                                     double* loss, fhash_stream stream) {
     if (!m) return set_error(FHASH_EINVAL, "fhash_compute_grads_noalloc: null model");
+    if (m->desc.layout == FHASH_LAYOUT_MASKED)
+        return set_error(FHASH_EINVAL, "fhash_compute_grads_noalloc: FHASH_LAYOUT_MASKED models take fhash_compute_grads");
     if (n < 1 || n > FHASH_NOALLOC_MAX_SAMPLES || !coords || !target)
         return set_error(FHASH_EINVAL, "fhash_compute_grads_noalloc: need 1 <= n <= %d, coords and target",
                          FHASH_NOALLOC_MAX_SAMPLES);

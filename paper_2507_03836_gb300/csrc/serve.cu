@@ -88,7 +88,7 @@ static uint64_t render_scratch(int64_t NR) {
 
 static uint64_t serving_bytes(const fhash_model* m) {
     const int64_t nbrick = m->nbx * m->nby * m->nbz;
-    return m->n_params * 4 + (m->shadow ? m->n_params * 2 : 0) + (uint64_t)(nbrick * 17 * m->nt);
+    return m->n_params * 4 + (m->shadow ? m->n_params * 2 : 0) + (uint64_t)(nbrick * 17 * m->nt) + m->dir_words * 16;
 }
 
 }  // namespace fh

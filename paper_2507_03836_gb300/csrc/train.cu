@@ -18,16 +18,17 @@
 namespace fh {
 
 // ------------------------------------------------------------------ gathers / scatters (level-major)
-template <int F>
+// LAYOUT: the model's row layout (all levels share it), fixed per instantiation.
+template <int F, int LAYOUT>
 __global__ void __launch_bounds__(256) k_encode_cols(const __grid_constant__ Levels lv, const float* __restrict__ T,
                                                      const float* __restrict__ coords, int64_t n, float* __restrict__ enc) {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= n * lv.L) return;
     const int l = (int)(idx / n);
     const int64_t s = idx - (int64_t)l * n;
-    Corners k = corners(lv.lv[l], load_coord(coords, s));
+    Corners k = corners<LAYOUT>(lv.lv[l], load_coord(coords, s));
     float o[F];
-    interp_level<F>(T, k, o);
+    interp_level<F, LAYOUT>(T, k, o);
 #pragma unroll
     for (int f = 0; f < F; ++f) enc[(int64_t)(l * F + f) * n + s] = o[f];
 }
@@ -55,7 +56,7 @@ struct ScatterPlan {
     int32_t priv[FHASH_MAX_LEVELS];
 };
 
-template <int F>
+template <int F, int LAYOUT>
 __global__ void __launch_bounds__(256) k_scatter_cols(const __grid_constant__ Levels lv, const __grid_constant__ ScatterPlan P,
                                                       float* __restrict__ G, const float* __restrict__ coords, int64_t n,
                                                       const float* __restrict__ denc, int64_t dsf, int64_t dss) {
@@ -66,18 +67,20 @@ __global__ void __launch_bounds__(256) k_scatter_cols(const __grid_constant__ Le
     const int64_t s1 = min(n, s0 + P.per[l]);
     const Level& L = lv.lv[l];
     if (P.priv[l]) {
-        const int64_t nrow = (int64_t)L.st * L.R[3];
+        const int64_t nrow = (int64_t)L.nrows;
         for (int64_t e = threadIdx.x; e < nrow * F; e += blockDim.x) acc[e] = 0.0f;
         __syncthreads();
         for (int64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
-            Corners k = corners(L, load_coord(coords, s));
+            Corners k = corners<LAYOUT>(L, load_coord(coords, s));
             float g[F];
 #pragma unroll
             for (int f = 0; f < F; ++f) g[f] = denc[(int64_t)(l * F + f) * dsf + s * dss];
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
                 const float w = corner_weight(k, c);
-                float* dst = acc + (corner_row(k, c) - L.base) * F;
+                const uint64_t r = corner_row<LAYOUT>(k, c);
+                if (LAYOUT == 2 && r == kInactiveRow) continue;  // masked: inactive corners take no gradient
+                float* dst = acc + (r - L.base) * F;
 #pragma unroll
                 for (int f = 0; f < F; ++f) atomicAdd(dst + f, w * g[f]);
             }
@@ -89,7 +92,7 @@ __global__ void __launch_bounds__(256) k_scatter_cols(const __grid_constant__ Le
     } else {
         const int64_t s = s0 + threadIdx.x;
         if (s >= s1) return;
-        Corners k = corners(L, load_coord(coords, s));
+        Corners k = corners<LAYOUT>(L, load_coord(coords, s));
         float g[F];
 #pragma unroll
         for (int f = 0; f < F; ++f) g[f] = denc[(int64_t)(l * F + f) * dsf + s * dss];
@@ -98,18 +101,22 @@ __global__ void __launch_bounds__(256) k_scatter_cols(const __grid_constant__ Le
             // reduction instead of two 8-byte ones (fewer L2 atomic operations)
 #pragma unroll
             for (int c = 0; c < 16; c += 2) {
-                const uint64_t r = corner_row(k, c), r1 = corner_row(k, c + 1);
+                const uint64_t r = corner_row<LAYOUT>(k, c), r1 = corner_row<LAYOUT>(k, c + 1);
                 const float w0 = corner_weight(k, c), w1 = corner_weight(k, c + 1);
+                // (kInactiveRow is odd, so an inactive lower row never takes the paired form)
                 if (r1 == r + 1 && (r & 1u) == 0u) {
                     red_add4(G + r * 2, w0 * g[0], w0 * g[1], w1 * g[0], w1 * g[1]);
                 } else {
-                    red_add2(G + r * 2, w0 * g[0], w0 * g[1]);
-                    red_add2(G + r1 * 2, w1 * g[0], w1 * g[1]);
+                    if (LAYOUT != 2 || r != kInactiveRow) red_add2(G + r * 2, w0 * g[0], w0 * g[1]);
+                    if (LAYOUT != 2 || r1 != kInactiveRow) red_add2(G + r1 * 2, w1 * g[0], w1 * g[1]);
                 }
             }
         } else {
 #pragma unroll
-            for (int c = 0; c < 16; ++c) red_row<F>(G + corner_row(k, c) * F, corner_weight(k, c), g);
+            for (int c = 0; c < 16; ++c) {
+                const uint64_t r = corner_row<LAYOUT>(k, c);
+                if (LAYOUT != 2 || r != kInactiveRow) red_row<F>(G + r * F, corner_weight(k, c), g);
+            }
         }
     }
 }
@@ -417,6 +424,22 @@ cudaError_t run_tc_any(fhash_model* m, bool train, FusedArgs& a);
 bool launch_dw_tc(fhash_model* m, const float* acts, const float* dl, int64_t n, float* wpart, size_t wpart_bytes,
                   cudaStream_t st, cudaError_t* err);
 
+template <int F, int LAYOUT>
+static cudaError_t scatter_run(fhash_model* m, const ScatterPlan& Pp, const ScatterPlan& Pf, int bp, int bf,
+                               int64_t priv_floats, const float* coords, int64_t n, const float* denc, int64_t dsf,
+                               int64_t dss, cudaStream_t st) {
+    if (bp > 0) {
+        const int smem = (int)(priv_floats * 4);
+        cudaError_t e = cudaFuncSetAttribute((const void*)k_scatter_cols<F, LAYOUT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, std::max(smem, 1));
+        if (e != cudaSuccess) return e;
+        k_scatter_cols<F, LAYOUT><<<bp, 256, smem, st>>>(m->lv, Pp, m->grad, coords, n, denc, dsf, dss);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (bf > 0) k_scatter_cols<F, LAYOUT><<<bf, 256, 0, st>>>(m->lv, Pf, m->grad, coords, n, denc, dsf, dss);
+    return cudaGetLastError();
+}
+
 template <int F>
 static cudaError_t scatter_launch(fhash_model* m, const float* coords, int64_t n, const float* denc, int64_t dsf,
                                   int64_t dss, cudaStream_t st) {
@@ -428,7 +451,7 @@ static cudaError_t scatter_launch(fhash_model* m, const float* coords, int64_t n
     int64_t priv_floats = 0;
     for (int l = 0; l < m->lv.L; ++l) {
         const Level& L = m->lv.lv[l];
-        const int64_t fl = (int64_t)L.st * L.R[3] * F;
+        const int64_t fl = (int64_t)L.nrows * F;
         Pp.first[l] = bp;
         Pf.first[l] = bf;
         if (fl <= kPrivMax) {
@@ -444,16 +467,20 @@ static cudaError_t scatter_launch(fhash_model* m, const float* coords, int64_t n
     }
     Pp.first[m->lv.L] = bp;
     Pf.first[m->lv.L] = bf;
-    if (bp > 0) {
-        const int smem = (int)(priv_floats * 4);
-        cudaError_t e = cudaFuncSetAttribute((const void*)k_scatter_cols<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             std::max(smem, 1));
-        if (e != cudaSuccess) return e;
-        k_scatter_cols<F><<<bp, 256, smem, st>>>(m->lv, Pp, m->grad, coords, n, denc, dsf, dss);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    switch (m->lv.lv[0].layout) {
+        case FHASH_LAYOUT_BRICK: return scatter_run<F, 1>(m, Pp, Pf, bp, bf, priv_floats, coords, n, denc, dsf, dss, st);
+        case FHASH_LAYOUT_MASKED: return scatter_run<F, 2>(m, Pp, Pf, bp, bf, priv_floats, coords, n, denc, dsf, dss, st);
+        default: return scatter_run<F, 0>(m, Pp, Pf, bp, bf, priv_floats, coords, n, denc, dsf, dss, st);
     }
-    if (bf > 0) k_scatter_cols<F><<<bf, 256, 0, st>>>(m->lv, Pf, m->grad, coords, n, denc, dsf, dss);
-    return cudaGetLastError();
+}
+
+template <int F>
+static void encode_cols(fhash_model* m, unsigned grid, const float* coords, int64_t n, float* acts, cudaStream_t st) {
+    switch (m->lv.lv[0].layout) {
+        case FHASH_LAYOUT_BRICK: k_encode_cols<F, 1><<<grid, 256, 0, st>>>(m->lv, m->param, coords, n, acts); break;
+        case FHASH_LAYOUT_MASKED: k_encode_cols<F, 2><<<grid, 256, 0, st>>>(m->lv, m->param, coords, n, acts); break;
+        default: k_encode_cols<F, 0><<<grid, 256, 0, st>>>(m->lv, m->param, coords, n, acts); break;
+    }
 }
 
 // Backward of the encoding alone: d(encoding) given row-major [n][L*F] (the layout of fhash_encode).
@@ -506,10 +533,10 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
     } else {
         const unsigned eg = (unsigned)((n * m->lv.L + 255) / 256);
         switch (F) {
-            case 1: k_encode_cols<1><<<eg, 256, 0, st>>>(m->lv, m->param, coords, n, acts); break;
-            case 2: k_encode_cols<2><<<eg, 256, 0, st>>>(m->lv, m->param, coords, n, acts); break;
-            case 4: k_encode_cols<4><<<eg, 256, 0, st>>>(m->lv, m->param, coords, n, acts); break;
-            case 8: k_encode_cols<8><<<eg, 256, 0, st>>>(m->lv, m->param, coords, n, acts); break;
+            case 1: encode_cols<1>(m, eg, coords, n, acts, st); break;
+            case 2: encode_cols<2>(m, eg, coords, n, acts, st); break;
+            case 4: encode_cols<4>(m, eg, coords, n, acts, st); break;
+            case 8: encode_cols<8>(m, eg, coords, n, acts, st); break;
             default: return set_error(FHASH_EINVAL, "F=%d unsupported", F);
         }
         FH_CUDA(cudaGetLastError());
