@@ -163,6 +163,26 @@ __device__ __forceinline__ uint32_t brick_row3(uint32_t x, uint32_t y, uint32_t 
     return 4u * bz * Rx * Ry + wz * (4u * by * Rx + wy * 4u * bx) + ((z & 3u) * wy + (y & 3u)) * wx + (x & 3u);
 }
 
+// Rows of the x-neighbours with Eq. 9 rows r and r + ox (ox = 0 or 1) of a masked level, from one
+// directory record unless r + 1 starts the next 64-row word.  The rank of r + 1 is that of r plus one
+// when r is active.
+__device__ __forceinline__ void masked_pair(const uint4* __restrict__ dir, uint64_t base, uint64_t r, uint32_t ox,
+                                            uint64_t& a, uint64_t& b) {
+    const uint4 d = __ldg(dir + (r >> 6));
+    const uint64_t bits = ((uint64_t)d.y << 32) | d.x;
+    const uint32_t i = (uint32_t)r & 63u;
+    const uint64_t at = base + ((((uint64_t)d.w) << 32) | d.z) + (uint64_t)__popcll(bits & ((1ull << i) - 1ull));
+    const bool act0 = (bits >> i) & 1ull;
+    a = act0 ? at : kInactiveRow;
+    if (ox == 0u) {
+        b = a;
+    } else if (i < 63u) {
+        b = ((bits >> (i + 1u)) & 1ull) ? at + (act0 ? 1ull : 0ull) : kInactiveRow;
+    } else {
+        b = masked_row(dir, base, r + 1);
+    }
+}
+
 // LAYOUT: 0 = Eq. 9, 1 = bricks, 2 = masked, -1 = read from the level (kernels over one level per thread
 // take the runtime form; kernels that walk all levels of a sample are instantiated per layout, so that
 // no branch sits between the gathers of consecutive levels).
@@ -206,6 +226,12 @@ __device__ __forceinline__ uint64_t corner_row(const Corners& k, int c) {
     const uint64_t r = k.r0 + ((c & 8) ? k.ot : 0ull) + ((c & 4) ? k.oz : 0u) + ((c & 2) ? k.oy : 0u) + ((c & 1) ? k.ox : 0u);
     if (lay == 2) return masked_row(k.dir, k.mbase, r);
     return r;
+}
+
+// Rows of corners c (even: lower x) and c + 1 (upper x) of a masked level: one directory record per pair.
+__device__ __forceinline__ void masked_corner_pair(const Corners& k, int c, uint64_t& a, uint64_t& b) {
+    const uint64_t r = k.r0 + ((c & 8) ? k.ot : 0ull) + ((c & 4) ? k.oz : 0u) + ((c & 2) ? k.oy : 0u);
+    masked_pair(k.dir, k.mbase, r, k.ox, a, b);
 }
 
 __device__ __forceinline__ void raise_error(int* word, int code) {

@@ -38,13 +38,17 @@ __device__ __forceinline__ void interp_level(const float* __restrict__ T, const 
         for (int c = 0; c < 16; ++c) load_row<F>(T, corner_row<1>(k, c), v[c]);
     } else if (lay == 2) {
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-            const uint64_t r = corner_row<2>(k, c);
-            if (r != kInactiveRow) {
-                load_row<F>(T, r, v[c]);
-            } else {
+        for (int c = 0; c < 16; c += 2) {
+            uint64_t r[2];
+            masked_corner_pair(k, c, r[0], r[1]);
 #pragma unroll
-                for (int f = 0; f < F; ++f) v[c][f] = 0.0f;  // an inactive corner reads 0
+            for (int h = 0; h < 2; ++h) {
+                if (r[h] != kInactiveRow) {
+                    load_row<F>(T, r[h], v[c + h]);
+                } else {
+#pragma unroll
+                    for (int f = 0; f < F; ++f) v[c + h][f] = 0.0f;  // an inactive corner reads 0
+                }
             }
         }
     } else {

@@ -101,7 +101,13 @@ __global__ void __launch_bounds__(256) k_scatter_cols(const __grid_constant__ Le
             // reduction instead of two 8-byte ones (fewer L2 atomic operations)
 #pragma unroll
             for (int c = 0; c < 16; c += 2) {
-                const uint64_t r = corner_row<LAYOUT>(k, c), r1 = corner_row<LAYOUT>(k, c + 1);
+                uint64_t r, r1;
+                if constexpr (LAYOUT == 2) {
+                    masked_corner_pair(k, c, r, r1);
+                } else {
+                    r = corner_row<LAYOUT>(k, c);
+                    r1 = corner_row<LAYOUT>(k, c + 1);
+                }
                 const float w0 = corner_weight(k, c), w1 = corner_weight(k, c + 1);
                 // (kInactiveRow is odd, so an inactive lower row never takes the paired form)
                 if (r1 == r + 1 && (r & 1u) == 0u) {
@@ -113,9 +119,17 @@ __global__ void __launch_bounds__(256) k_scatter_cols(const __grid_constant__ Le
             }
         } else {
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                const uint64_t r = corner_row<LAYOUT>(k, c);
-                if (LAYOUT != 2 || r != kInactiveRow) red_row<F>(G + r * F, corner_weight(k, c), g);
+            for (int c = 0; c < 16; c += 2) {
+                uint64_t r[2];
+                if constexpr (LAYOUT == 2) {
+                    masked_corner_pair(k, c, r[0], r[1]);
+                } else {
+                    r[0] = corner_row<LAYOUT>(k, c);
+                    r[1] = corner_row<LAYOUT>(k, c + 1);
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    if (LAYOUT != 2 || r[h] != kInactiveRow) red_row<F>(G + r[h] * F, corner_weight(k, c + h), g);
             }
         }
     }
