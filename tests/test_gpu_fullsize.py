@@ -8,14 +8,18 @@ SplitMix64 (the library's documented initialisation), the seeded field and mask 
 - the full-batch loss of one training step, within 1e-5 relative;
 - MLP gradients and the table gradient on 20000 sampled touched rows, within 1e-4 x the sum of
   the magnitudes of their terms; 2000 sampled untouched rows exactly zero;
-- the Adam update of the same rows, fed the same gradient, within 1e-6 x lr + 3e-7 x |p|.
+- the Adam update of the same rows, fed the same gradient, within 1e-6 x lr + 3e-7 x |p|;
+- masked compact tables at this size: the active bit of 20000 sampled vertices on each of four levels
+  against the definition (a box query over the dilated mask), level bases equal to the running
+  popcount of the bits, and the rows of all corners of 4096 footprint points active and equal to the
+  level base plus the rank of their Eq. 9 row among the active ones.
 """
 import numpy as np
 import pytest
 
 import synth
 from synth import workloads
-from oracle import adam, encode, index, mlp, rng, schedule, train
+from oracle import adam, encode, index, masked, mlp, rng, schedule, train
 
 from _util import fh, to_dev, torch
 
@@ -228,5 +232,66 @@ def test_fullsize_render_and_decode(large):
     refd = ev(u[pick])
     tol = 1e-4 * np.maximum(np.abs(refd), np.sqrt(np.mean(refd ** 2)))
     assert (np.abs(got[pick] - refd) <= tol).all(), np.abs(got[pick] - refd).max()
+    fh().fhash_check(model)
+    del model
+
+
+def test_fullsize_masked_directory(large):
+    nx, ny, nz, nt = W["dims"]
+    model = fh().fhash_build(nx, ny, nz, nt, mask=large["mask"], schedule=fh().make_schedule(**W["schedule"]),
+                             F=W["F"], mlp_hidden_layers=W["hidden"], mlp_width=W["width"], seed=SEED,
+                             init_range=W["init_range"], layout=fh().LAYOUT_MASKED)
+    info = fh().fhash_get_info(model)
+    lv, base = info["res"], info["base"]
+    d = index.dilate(large["mask"])
+    lo, size = index.fbb(d)
+    dil = masked.fbb_mask(d, lo, size)
+    del d
+    T, Sz, Sy, Sx = dil.shape
+    pop = np.array([bin(i).count("1") for i in range(256)], np.uint8)
+    rs = np.random.default_rng(12)
+    bits, cum = [], []
+    for l, R in enumerate(lv):
+        nw = (int(np.prod(R, dtype=np.int64)) + 63) // 64
+        b = np.empty(nw, np.uint64)
+        fh().fhash_read_active(model, l, 0, b)
+        per_word = pop[b.view(np.uint8)].reshape(-1, 8).sum(1, dtype=np.int64)
+        bits.append(b)
+        cum.append(np.concatenate([[0], np.cumsum(per_word)]))
+        nxt = base[l + 1] if l + 1 < len(lv) else info["total_rows"]
+        assert cum[l][-1] == nxt - base[l], l
+    for l in (0, 8, 12, len(lv) - 1):
+        Rx, Ry, Rz, Rt = lv[l]
+        ranges = [np.array([masked.vertex_range(v, S, R) for v in range(S)]) for S, R in ((Sx, Rx), (Sy, Ry), (Sz, Rz))]
+        ranges.append(np.array([masked.time_range(k, T, Rt) for k in range(T)]))
+        for _ in range(20000):
+            X = [int(rs.integers(0, r)) for r in (Rx, Ry, Rz, Rt)]
+            vs = [np.flatnonzero((rg[:, 0] <= x) & (x <= rg[:, 1])) for rg, x in zip(ranges, X)]
+            want = bool(dil[np.ix_(vs[3], vs[2], vs[1], vs[0])].any()) if all(v.size for v in vs) else False
+            r = int(encode.fhash(X[3], X[0], X[1], X[2], lv[l]))
+            got = bool((int(bits[l][r >> 6]) >> (r & 63)) & 1)
+            assert got == want, (l, X)
+    # footprint points: random occupied voxels, offsets inside their footprints
+    pts = []
+    while sum(len(p) for p in pts) < 4096:
+        v = np.stack([rs.integers(0, n, 100000) for n in (T, Sz, Sy, Sx)], 1)
+        pts.append(v[dil[v[:, 0], v[:, 1], v[:, 2], v[:, 3]]])
+    v = np.concatenate(pts)[:4096]
+    u = np.empty((4096, 4))
+    for a, (col, S) in enumerate(((3, Sx), (2, Sy), (1, Sz))):
+        u[:, a] = (v[:, col] + rs.uniform(-0.5, 0.5, 4096)) / (S - 1)
+    u[:, 3] = (v[:, 0] + rs.uniform(-1.0, 1.0, 4096)) / (T - 1)
+    u = np.clip(u, 0, 1).astype(np.float32)
+    rows = torch().empty((4096, len(lv), 16), dtype=torch().int64, device="cuda")
+    fh().fhash_lookup(model, to_dev(u), rows)
+    rows = rows.cpu().numpy().view(np.uint64)
+    for l, R in enumerate(lv):
+        r_lin, _ = encode.level_corners(u, R, 0)
+        w, i = r_lin >> 6, (r_lin & 63).astype(np.uint64)
+        word = bits[l][w]
+        assert ((word >> i) & np.uint64(1) == 1).all(), l
+        below = word & ((np.uint64(1) << i) - np.uint64(1))
+        rank = cum[l][w] + pop[below.view(np.uint8).reshape(below.shape + (8,))].sum(-1, dtype=np.int64)
+        assert np.array_equal(rows[:, l, :], (base[l] + rank).astype(np.uint64)), l
     fh().fhash_check(model)
     del model
