@@ -1,7 +1,8 @@
 """GPU tests of the continuous-batching serving loop (include/fhash_serve.h).
 
 Each request's result in a mix - renders of different sizes, cameras and fractional times, and
-decodes at different upsampling and times, over an FP32 and a bf16 model, interleaved across many
+decodes at different upsampling and times, over an FP32, a bf16 and an FP32 masked-table model
+(FHASH_LAYOUT_MASKED), interleaved across many
 ticks of a small packed buffer - must be bit-identical to the same request run alone through
 fhash_render / fhash_decode (per-sample arithmetic does not depend on batch position, and the image
 does not depend on the ARM pace).  Admission follows the memory budget; cancellation releases memory.
@@ -22,8 +23,14 @@ W1 = workloads.SMALL
 def models():
     f, m = workloads.make_field_and_mask(W1)
     out = []
-    for dt in (fh().FP32, fh().BF16):
-        model = build(W1, mask=m, dtype=dt, seed=17)
+    nx, ny, nz, nt = W1["dims"]
+    for dt in (fh().FP32, fh().BF16, "masked"):
+        if dt == "masked":
+            model = fh().fhash_build(nx, ny, nz, nt, mask=m, schedule=fh().make_schedule(**W1["schedule"]), F=W1["F"],
+                                     mlp_hidden_layers=W1["hidden"], mlp_width=W1["width"], seed=17,
+                                     init_range=W1["init_range"], layout=fh().LAYOUT_MASKED)
+        else:
+            model = build(W1, mask=m, dtype=dt, seed=17)
         info = fh().fhash_get_info(model)
         table = synth.uniform(51, 50, info["n_table_params"], -0.6, 0.6)
         p = synth.init_mlp(51, info["mlp_dims"])
@@ -59,7 +66,8 @@ def test_mix_equals_alone(models):
     tf = to_dev(synth.transfer_function(0.5))
     srv = fh().fhash_server_create(models, budget_bytes=1 << 30, max_live=8, tick_samples=8192)
     specs = [("r", 0, 0.0, 40, 30, 0), ("d", 1, 0.37, 2), ("r", 1, 0.55, 64, 48, 1), ("d", 0, 1.0, 1),
-             ("r", 0, 0.9, 24, 24, 2), ("r", 1, 0.2, 72, 40, 3), ("d", 0, 0.5, 2)]
+             ("r", 2, 0.45, 48, 36, 4), ("r", 0, 0.9, 24, 24, 2), ("r", 1, 0.2, 72, 40, 3), ("d", 2, 0.6, 1),
+             ("d", 0, 0.5, 2)]
     subs = []
     for sp in specs:
         if sp[0] == "r":
