@@ -264,7 +264,9 @@ def test_fullsize_masked_directory(large):
         Rx, Ry, Rz, Rt = lv[l]
         ranges = [np.array([masked.vertex_range(v, S, R) for v in range(S)]) for S, R in ((Sx, Rx), (Sy, Ry), (Sz, Rz))]
         ranges.append(np.array([masked.time_range(k, T, Rt) for k in range(T)]))
-        for _ in range(20000):
+        # a box query reads about prod(S/R + 3) voxels: coarse levels get fewer samples
+        box = np.prod([S / R + 3 for S, R in ((Sx, Rx), (Sy, Ry), (Sz, Rz), (T, Rt))])
+        for _ in range(int(min(20000, max(20, 4e7 / box)))):
             X = [int(rs.integers(0, r)) for r in (Rx, Ry, Rz, Rt)]
             vs = [np.flatnonzero((rg[:, 0] <= x) & (x <= rg[:, 1])) for rg, x in zip(ranges, X)]
             want = bool(dil[np.ix_(vs[3], vs[2], vs[1], vs[0])].any()) if all(v.size for v in vs) else False
