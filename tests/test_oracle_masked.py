@@ -11,6 +11,7 @@
 - Equivalence: a masked table holding a rectangular table's vertex values encodes footprint points
   exactly like it; at any point the masked encoding equals the rectangular one with the inactive rows
   set to 0, and the gradients of the active rows agree.
+- Product structure: OR-resampling the dilated mask one axis at a time gives the same active grid.
 """
 from fractions import Fraction
 
@@ -153,3 +154,32 @@ def test_equivalence_with_the_rectangular_table():
     got = np.zeros_like(T_m)
     got[rm] = gm
     assert np.allclose(got, want, rtol=1e-12, atol=1e-12)
+
+
+def test_active_grid_is_separable():
+    """The definition marks, for every occupied voxel, the product of its per-axis vertex ranges.  The
+    same grid comes out of OR-resampling the dilated mask one axis at a time, each vertex taking the OR
+    over the voxels whose range holds it (the form a parallel build can use): a product structure the
+    definition must have."""
+    dil = _small_mask(8)
+    T, Sz, Sy, Sx = dil.shape
+
+    def resample(a, axis, S, R, time):
+        rng = [masked.time_range(v, S, R) if time else masked.vertex_range(v, S, R) for v in range(S)]
+        out_shape = list(a.shape)
+        out_shape[axis] = R
+        out = np.zeros(out_shape, bool)
+        for X in range(R):
+            vs = [v for v in range(S) if rng[v][0] <= X <= rng[v][1]]
+            if vs:
+                idx = [slice(None)] * a.ndim
+                idx[axis] = X
+                out[tuple(idx)] = np.take(a, vs, axis=axis).any(axis=axis)
+        return out
+
+    for R in LEVELS + [[40, 3, 50, 12]]:
+        g = resample(dil, 3, Sx, R[0], False)
+        g = resample(g, 2, Sy, R[1], False)
+        g = resample(g, 1, Sz, R[2], False)
+        g = resample(g, 0, T, R[3], True)
+        assert np.array_equal(g, masked.active_grid(dil, R)), R
