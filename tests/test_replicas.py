@@ -61,3 +61,17 @@ def test_two_gloo_replicas():
     assert [o[1] for o in out] == [2.5, 2.5]
     assert all(abs(o[2] - 2 * 1000 / 2.5) < 1e-9 for o in out)
     assert out[1][3] == ""  # rank 1 printed nothing
+
+
+def test_oracle_pool_on_host_cores():
+    """The CPU baseline's all-cores leg: spawned single-threaded processes time the oracle together and
+    the step time is extrapolated from the slowest one."""
+    sys.path.insert(0, ROOT)
+    import bench
+    pool = bench.OraclePool(procs=2)
+    try:
+        w = bench._workload("small")
+        t, desc = pool.step(w, 256, 4096, seed=1)
+    finally:
+        pool.close()
+    assert pool.procs == 2 and t > 0 and "2 single-threaded processes" in desc
