@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <string>
 #include <vector>
@@ -9,6 +10,17 @@
 #include "fhash.h"
 
 namespace fh {
+
+// NVTX range around an entry point (header-only NVTX 3): visible to Nsight Systems and to
+// `ncu --nvtx --nvtx-include`; without a tool attached each push and pop is a no-op call.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define FH_RANGE(name) ::fh::NvtxRange fh_nvtx_range_(name)
+
 
 // ------------------------------------------------------------------ errors
 fhash_status set_error(fhash_status s, const char* fmt, ...);

@@ -254,12 +254,14 @@ extern "C" {
 
 fhash_status fhash_coreset_build(fhash_model* m, const float* volume, const int32_t* key_frames, int32_t n_key,
                                  int64_t* count, fhash_stream stream) {
+    FH_RANGE("fhash_coreset_build");
     if (!m) return set_error(FHASH_EINVAL, "fhash_coreset_build: null model");
     return coreset_build(m, volume, key_frames, n_key, count, (cudaStream_t)stream);
 }
 
 fhash_status fhash_coreset_batch(fhash_model* m, uint64_t seed, int64_t epoch, int64_t batch, int64_t batch_size,
                                  float* coords, float* target, int64_t* n_out, fhash_stream stream) {
+    FH_RANGE("fhash_coreset_batch");
     if (!m || !coords || !target) return set_error(FHASH_EINVAL, "fhash_coreset_batch: null argument");
     if (!is_device_ptr(coords) || !is_device_ptr(target))
         return set_error(FHASH_EINVAL, "fhash_coreset_batch: buffers must be device memory");
@@ -268,6 +270,7 @@ fhash_status fhash_coreset_batch(fhash_model* m, uint64_t seed, int64_t epoch, i
 
 fhash_status fhash_coreset_train_step(fhash_model* m, uint64_t seed, int64_t epoch, int64_t batch, int64_t batch_size,
                                       const fhash_adam* adam, double* loss, fhash_stream stream) {
+    FH_RANGE("fhash_coreset_train_step");
     if (!m || !adam) return set_error(FHASH_EINVAL, "fhash_coreset_train_step: null argument");
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t want = std::max<int64_t>(1, std::min(batch_size, m->cs_n));

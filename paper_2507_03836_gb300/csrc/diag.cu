@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(256) k_diag_gather(const uint8_t* __restrict__
 
 extern "C" fhash_status fhash_diag_random_gather(const void* table, uint64_t bytes, int32_t width, int64_t n,
                                                  uint64_t seed, float* sum, fhash_stream stream) {
+    FH_RANGE("fhash_diag_random_gather");
     if (!table || !sum || n < 0 || (width != 4 && width != 8 && width != 16) || bytes < (uint64_t)width ||
         (reinterpret_cast<uintptr_t>(table) % 16) != 0 || !fh::is_device_ptr(table) || !fh::is_device_ptr(sum))
         return fh::set_error(FHASH_EINVAL, "fhash_diag_random_gather: bad arguments");

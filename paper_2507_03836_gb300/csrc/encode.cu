@@ -249,6 +249,7 @@ static fhash_status check_model(fhash_model* m, const char* fn) {
 extern "C" {
 
 fhash_status fhash_lookup(fhash_model* m, const float* coords, int64_t n, uint64_t* rows, float* w, fhash_stream stream) {
+    FH_RANGE("fhash_lookup");
     FH_TRY(check_model(m, "fhash_lookup"));
     if (n < 0 || (n && (!coords || !rows))) return set_error(FHASH_EINVAL, "fhash_lookup: bad arguments");
     if (n == 0) return FHASH_OK;
@@ -258,6 +259,7 @@ fhash_status fhash_lookup(fhash_model* m, const float* coords, int64_t n, uint64
 }
 
 fhash_status fhash_encode(fhash_model* m, const float* coords, int64_t n, float* enc, fhash_stream stream) {
+    FH_RANGE("fhash_encode");
     FH_TRY(check_model(m, "fhash_encode"));
     if (n < 0 || (n && (!coords || !enc))) return set_error(FHASH_EINVAL, "fhash_encode: bad arguments");
     if (n == 0) return FHASH_OK;
@@ -267,6 +269,7 @@ fhash_status fhash_encode(fhash_model* m, const float* coords, int64_t n, float*
 
 fhash_status fhash_encode_backward(fhash_model* m, const float* coords, const float* d_enc, int64_t n,
                                    fhash_stream stream) {
+    FH_RANGE("fhash_encode_backward");
     FH_TRY(check_model(m, "fhash_encode_backward"));
     if (n < 0 || (n && (!coords || !d_enc))) return set_error(FHASH_EINVAL, "fhash_encode_backward: bad arguments");
     if (n == 0) return FHASH_OK;
@@ -284,6 +287,7 @@ fhash_status fhash_set_forward_path(fhash_model* m, int32_t path) {
 }
 
 fhash_status fhash_forward(fhash_model* m, const float* coords, int64_t n, float* out, fhash_stream stream) {
+    FH_RANGE("fhash_forward");
     FH_TRY(check_model(m, "fhash_forward"));
     if (n < 0 || (n && (!coords || !out))) return set_error(FHASH_EINVAL, "fhash_forward: bad arguments");
     if (n == 0) return FHASH_OK;
@@ -303,6 +307,7 @@ fhash_status fhash_forward(fhash_model* m, const float* coords, int64_t n, float
 
 fhash_status fhash_compute_grads(fhash_model* m, const float* coords, const float* target, int64_t n, double* loss,
                                  fhash_stream stream) {
+    FH_RANGE("fhash_compute_grads");
     FH_TRY(check_model(m, "fhash_compute_grads"));
     if (n <= 0 || !coords || !target) return set_error(FHASH_EINVAL, "fhash_compute_grads: need n > 0, coords and target");
     cudaStream_t st = (cudaStream_t)stream;
@@ -320,6 +325,7 @@ fhash_status fhash_compute_grads(fhash_model* m, const float* coords, const floa
 }
 
 fhash_status fhash_apply_adam(fhash_model* m, const fhash_adam* a, fhash_stream stream) {
+    FH_RANGE("fhash_apply_adam");
     FH_TRY(check_model(m, "fhash_apply_adam"));
     if (!a || !(a->lr >= 0.0f) || !(a->beta1 >= 0.0f && a->beta1 < 1.0f) || !(a->beta2 >= 0.0f && a->beta2 < 1.0f) ||
         !(a->eps > 0.0f))
@@ -329,6 +335,7 @@ fhash_status fhash_apply_adam(fhash_model* m, const fhash_adam* a, fhash_stream 
 
 fhash_status fhash_train_step(fhash_model* m, const float* coords, const float* target, int64_t n, const fhash_adam* a,
                               double* loss, fhash_stream stream) {
+    FH_RANGE("fhash_train_step");
     FH_TRY(check_model(m, "fhash_train_step"));
     if (!a) return set_error(FHASH_EINVAL, "fhash_train_step: null adam");
     if (n <= 0 || !coords || !target) return set_error(FHASH_EINVAL, "fhash_train_step: need n > 0, coords and target");

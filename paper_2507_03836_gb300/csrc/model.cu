@@ -423,6 +423,7 @@ const char* fhash_last_error(void) { return g_err.c_str(); }
 void fhash_destroy(fhash_model* m) { destroy_model(m); }
 
 fhash_status fhash_build(const fhash_build_desc* d, fhash_stream stream, fhash_model** out) {
+    FH_RANGE("fhash_build");
     if (!d || !out) return set_error(FHASH_EINVAL, "fhash_build: null argument");
     *out = nullptr;
     cudaStream_t st = (cudaStream_t)stream;
@@ -765,6 +766,7 @@ static fhash_status stream_file(FILE* f, void* dev, uint64_t bytes, bool write, 
 extern "C" {
 
 fhash_status fhash_save(const fhash_model* mc, const char* path) {
+    FH_RANGE("fhash_save");
     fhash_model* m = const_cast<fhash_model*>(mc);
     if (!m || !path) return set_error(FHASH_EINVAL, "fhash_save: null argument");
     FH_CUDA(cudaDeviceSynchronize());
@@ -801,6 +803,7 @@ fhash_status fhash_save(const fhash_model* mc, const char* path) {
 }
 
 fhash_status fhash_load(const char* path, fhash_stream stream, fhash_model** out) {
+    FH_RANGE("fhash_load");
     if (!path || !out) return set_error(FHASH_EINVAL, "fhash_load: null argument");
     *out = nullptr;
     FILE* f = fopen(path, "rb");

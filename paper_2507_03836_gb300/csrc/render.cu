@@ -277,6 +277,7 @@ fhash_status fhash_decode_dims(const fhash_model* m, int32_t upsample, int64_t d
 }
 
 fhash_status fhash_decode(fhash_model* m, float t_norm, int32_t upsample, float* out, fhash_stream stream) {
+    FH_RANGE("fhash_decode");
     if (!m || !out || upsample < 1 || upsample > 8 || !(t_norm >= 0.0f && t_norm <= 1.0f))
         return set_error(FHASH_EINVAL, "fhash_decode: bad arguments (upsample 1..8, t_norm in [0,1])");
     if (!is_device_ptr(out)) return set_error(FHASH_EINVAL, "fhash_decode: out must be device memory");
@@ -311,6 +312,7 @@ fhash_status fhash_decode(fhash_model* m, float t_norm, int32_t upsample, float*
 fhash_status fhash_render(fhash_model* m, const fhash_camera* cam, float t_norm, const float* tf, int32_t w, int32_t h,
                           int32_t max_pace, float* rgba, int32_t* counts, fhash_render_stats* stats,
                           fhash_stream stream) {
+    FH_RANGE("fhash_render");
     if (!m || !cam || !tf || !rgba || w < 1 || h < 1 || (int64_t)w * h > (1 << 26) || max_pace < 1 ||
         !(t_norm >= 0.0f && t_norm <= 1.0f))
         return set_error(FHASH_EINVAL, "fhash_render: bad arguments");

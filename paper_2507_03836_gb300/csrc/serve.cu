@@ -256,6 +256,7 @@ static void finish(fhash_server* s, Req* q, int state) {
 }
 
 fhash_status fhash_server_tick(fhash_server* s, fhash_stream stream, int32_t* n_completed) {
+    FH_RANGE("fhash_server_tick");
     if (!s) return set_error(FHASH_EINVAL, "fhash_server_tick: null server");
     std::lock_guard<std::mutex> lock(s->mu);
     cudaStream_t st = (cudaStream_t)stream;
