@@ -177,6 +177,23 @@ typedef struct {
  */
 fhash_status fhash_build(const fhash_build_desc* desc, fhash_stream stream, fhash_model** out);
 
+/*
+ * Capacity planning without a build (host only: no CUDA call, so it also runs on a machine without a
+ * GPU).  For a Feature Bounding Box of fbb[3] = (Sx, Sy, Sz) vertices and nt time steps it returns what
+ * fhash_build would use with the same schedule, F, dtype and MLP shape in the rectangular layouts
+ * (Eq. 9 or bricks; a masked layout keeps a subset of these rows):
+ *  - *n_levels and res[0 .. *n_levels - 1] = (Rx, Ry, Rz, Rt), coarse -> fine (res may hold
+ *    FHASH_MAX_LEVELS rows);
+ *  - *table_rows = sum of Rx*Ry*Rz*Rt and *n_params = table_rows * F + the MLP's weights and biases;
+ *  - *state_bytes = 16 bytes per parameter (parameter, gradient, two Adam moments), plus 2 more for
+ *    the bf16 shadow of FHASH_BF16.
+ * Any output pointer may be NULL.  Errors (FHASH_EINVAL) as fhash_build reports them for the same
+ * arguments: bad schedule, F, dtype, MLP shape, L*F above 64, or a level too large to index.
+ */
+fhash_status fhash_plan(const fhash_schedule* sched, const int64_t fbb[3], int64_t nt, int32_t F, int32_t dtype,
+                        int32_t mlp_hidden_layers, int32_t mlp_width, int32_t* n_levels, int32_t (*res)[4],
+                        uint64_t* table_rows, uint64_t* n_params, uint64_t* state_bytes);
+
 /* Release every device and host resource of the model (synchronises the device first). */
 void fhash_destroy(fhash_model* model);
 

@@ -103,6 +103,8 @@ _SIGS = {
     "fhash_write_state": [_vp, _i32, _u64, _u64, _vp, _vp],
     "fhash_read_occupancy": [_vp, _i64, _vp, _vp],
     "fhash_read_active": [_vp, _i32, _u64, _u64, _vp, _vp],
+    "fhash_plan": [ctypes.POINTER(fhash_schedule), _vp, _i64, _i32, _i32, _i32, _i32, ctypes.POINTER(_i32), _vp,
+                   ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
     "fhash_check": [_vp, _vp],
     "fhash_save": [_vp, ctypes.c_char_p],
     "fhash_diag_wait_timeout": [_vp, _u64, _vp],
@@ -195,6 +197,20 @@ def make_schedule(mode="explicit", res=None, fold=2, levels_rule=LEVELS_MAX, n_l
 
 
 LAYOUT_LINEAR, LAYOUT_BRICK, LAYOUT_MASKED = 0, 1, 2
+
+
+def fhash_plan(fbb, nt, schedule=None, F=2, dtype=FP32, mlp_hidden_layers=2, mlp_width=64):
+    """Levels, table rows, parameters and device state bytes fhash_build would use (host only)."""
+    sched = schedule if schedule is not None else make_schedule()
+    fb = (ctypes.c_int64 * 3)(*[int(x) for x in fbb])
+    L = _i32()
+    res = ((ctypes.c_int32 * 4) * MAX_LEVELS)()
+    rows, npar, nbytes = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _ok(_lib.fhash_plan(ctypes.byref(sched), ctypes.cast(fb, _vp), int(nt), int(F), int(dtype), int(mlp_hidden_layers),
+                        int(mlp_width), ctypes.byref(L), ctypes.cast(res, _vp), ctypes.byref(rows), ctypes.byref(npar),
+                        ctypes.byref(nbytes)))
+    return dict(res=[list(res[l]) for l in range(L.value)], table_rows=rows.value, n_params=npar.value,
+                state_bytes=nbytes.value)
 
 
 def fhash_build(nx, ny, nz, nt, mask=None, schedule=None, F=2, dtype=FP32, mlp_hidden_layers=2, mlp_width=64,

@@ -593,6 +593,44 @@ fhash_status fhash_build(const fhash_build_desc* d, fhash_stream stream, fhash_m
     return FHASH_OK;
 }
 
+fhash_status fhash_plan(const fhash_schedule* sched, const int64_t fbb[3], int64_t nt, int32_t F, int32_t dtype,
+                        int32_t nh, int32_t width, int32_t* n_levels, int32_t (*res)[4], uint64_t* table_rows,
+                        uint64_t* n_params, uint64_t* state_bytes) {
+    if (!sched || !fbb) return set_error(FHASH_EINVAL, "fhash_plan: null argument");
+    for (int a = 0; a < 3; ++a)
+        if (fbb[a] < 1 || fbb[a] > (1 << 20)) return set_error(FHASH_EINVAL, "fhash_plan: FBB size out of range");
+    if (nt < 1) return set_error(FHASH_EINVAL, "fhash_plan: nt must be >= 1");
+    if (F != 1 && F != 2 && F != 4 && F != 8) return set_error(FHASH_EINVAL, "F must be 1, 2, 4 or 8");
+    if (dtype != FHASH_FP32 && dtype != FHASH_BF16) return set_error(FHASH_EINVAL, "dtype");
+    if (nh < 1 || nh > FHASH_MAX_HIDDEN) return set_error(FHASH_EINVAL, "mlp_hidden_layers must be in 1..%d", FHASH_MAX_HIDDEN);
+    if (width != 16 && width != 32 && width != 64) return set_error(FHASH_EINVAL, "mlp_width must be 16, 32 or 64");
+    std::vector<std::array<int64_t, 4>> lv;
+    FH_TRY(make_schedule(*sched, fbb, nt, lv));
+    const int L = (int)lv.size();
+    if (L * F > 64) return set_error(FHASH_EINVAL, "L*F = %d exceeds 64 (MLP input width)", L * F);
+    uint64_t rows = 0;
+    for (int l = 0; l < L; ++l) {
+        const uint64_t sxy = (uint64_t)lv[l][0] * lv[l][1];
+        if (sxy >= (1ull << 32)) return set_error(FHASH_EINVAL, "level %d: Rx*Ry too large", l);
+        const uint64_t sxyz = sxy * lv[l][2];
+        if (sxyz >= (1ull << 32)) return set_error(FHASH_EINVAL, "level %d: Rx*Ry*Rz too large", l);
+        rows += sxyz * (uint64_t)lv[l][3];
+        if (res)
+            for (int a = 0; a < 4; ++a) res[l][a] = (int32_t)lv[l][a];
+    }
+    uint64_t mlp = 0;
+    for (int k = 0; k <= nh; ++k) {
+        const uint64_t fi = (k == 0) ? (uint64_t)(L * F) : (uint64_t)width, fo = (k == nh) ? 1 : (uint64_t)width;
+        mlp += fi * fo + fo;
+    }
+    const uint64_t np = rows * (uint64_t)F + mlp;
+    if (n_levels) *n_levels = L;
+    if (table_rows) *table_rows = rows;
+    if (n_params) *n_params = np;
+    if (state_bytes) *state_bytes = np * 16 + (dtype == FHASH_BF16 ? np * 2 : 0);
+    return FHASH_OK;
+}
+
 fhash_status fhash_get_info(const fhash_model* m, fhash_info* o) {
     if (!m || !o) return set_error(FHASH_EINVAL, "fhash_get_info: null argument");
     memset(o, 0, sizeof *o);
