@@ -328,6 +328,12 @@ fhash_status fhash_write_state(fhash_model* model, int32_t which, uint64_t offse
  * out: host or device [Sz][Sy][Sx]. */
 fhash_status fhash_read_occupancy(fhash_model* model, int64_t t, uint8_t* out, fhash_stream stream);
 
+/* The rule FHASH_LAYOUT_MASKED builds with, for inspection (host only, no CUDA call): the vertices
+ * [*lo, *hi] of a level axis with R vertices that the footprint of voxel v of the S voxels of the FBB
+ * on that axis makes active (is_time = 0), or that time step v of S makes active (is_time = 1); see
+ * the layout description above.  FHASH_EINVAL unless 0 <= v < S, 1 <= S <= 2^24 and 1 <= R <= 2^24. */
+fhash_status fhash_active_range(int64_t v, int64_t S, int64_t R, int32_t is_time, int64_t* lo, int64_t* hi);
+
 /* Active-vertex bits of level l of a FHASH_LAYOUT_MASKED model: word w holds the vertices with Eq. 9
  * rows 64w .. 64w+63 of the level (bit i = row 64w + i), words [word0, word0 + n_words) into `bits`
  * (host or device).  Synchronous for host buffers.  FHASH_EINVAL for another layout, a level out of

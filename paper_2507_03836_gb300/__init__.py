@@ -103,6 +103,7 @@ _SIGS = {
     "fhash_write_state": [_vp, _i32, _u64, _u64, _vp, _vp],
     "fhash_read_occupancy": [_vp, _i64, _vp, _vp],
     "fhash_read_active": [_vp, _i32, _u64, _u64, _vp, _vp],
+    "fhash_active_range": [_i64, _i64, _i64, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64)],
     "fhash_plan": [ctypes.POINTER(fhash_schedule), _vp, _i64, _i32, _i32, _i32, _i32, ctypes.POINTER(_i32), _vp,
                    ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
     "fhash_check": [_vp, _vp],
@@ -197,6 +198,13 @@ def make_schedule(mode="explicit", res=None, fold=2, levels_rule=LEVELS_MAX, n_l
 
 
 LAYOUT_LINEAR, LAYOUT_BRICK, LAYOUT_MASKED = 0, 1, 2
+
+
+def fhash_active_range(v, S, R, is_time=False):
+    """Vertices [lo, hi] of a level axis that voxel (or time step) v makes active in a masked model."""
+    lo, hi = ctypes.c_int64(), ctypes.c_int64()
+    _ok(_lib.fhash_active_range(int(v), int(S), int(R), 1 if is_time else 0, ctypes.byref(lo), ctypes.byref(hi)))
+    return lo.value, hi.value
 
 
 def fhash_plan(fbb, nt, schedule=None, F=2, dtype=FP32, mlp_hidden_layers=2, mlp_width=64):

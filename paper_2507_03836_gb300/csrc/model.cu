@@ -593,6 +593,14 @@ fhash_status fhash_build(const fhash_build_desc* d, fhash_stream stream, fhash_m
     return FHASH_OK;
 }
 
+fhash_status fhash_active_range(int64_t v, int64_t S, int64_t R, int32_t is_time, int64_t* lo, int64_t* hi) {
+    if (!lo || !hi) return set_error(FHASH_EINVAL, "fhash_active_range: null argument");
+    if (S < 1 || S > (1 << 24) || R < 1 || R > (1 << 24) || v < 0 || v >= S)
+        return set_error(FHASH_EINVAL, "fhash_active_range: need 0 <= v < S <= 2^24 and 1 <= R <= 2^24");
+    active_range(v, S, R, is_time != 0, *lo, *hi);
+    return FHASH_OK;
+}
+
 fhash_status fhash_plan(const fhash_schedule* sched, const int64_t fbb[3], int64_t nt, int32_t F, int32_t dtype,
                         int32_t nh, int32_t width, int32_t* n_levels, int32_t (*res)[4], uint64_t* table_rows,
                         uint64_t* n_params, uint64_t* state_bytes) {

@@ -8,6 +8,7 @@ against the oracle's schedules and the parameter counts Table 3 prints.
   (16 B per parameter, 18 B with the bf16 shadow) equal to the oracle's counts; the bench workload
   has 3,557,118,770 table parameters.
 - Refusals: L*F above 64, fold < 2, bad F, MLP width or FBB size.
+- The masked layout's per-axis active-vertex rule (fhash_active_range) equals the oracle's.
 """
 import os
 
@@ -86,3 +87,17 @@ def test_plan_refusals():
     with pytest.raises(f.FHashError):
         f.fhash_plan((0, 8, 8), 2, f.make_schedule(mode="fold", fold=2))
     assert np.isfinite(f.fhash_plan((8, 8, 8), 1, f.make_schedule(mode="fold", fold=2))["state_bytes"])
+
+
+def test_masked_active_range_matches_oracle():
+    """The library's per-axis rule of the masked layout (the host arithmetic its GPU build uses) equals
+    the oracle's, exhaustively over small axes and on bench-sized ones."""
+    from oracle import masked
+    f = fh()
+    for S in list(range(1, 14)) + [256, 431]:
+        for R in list(range(1, 16)) + [64, 256, 432]:
+            for v in (range(S) if S < 20 else (0, 1, S // 3, S - 2, S - 1)):
+                assert f.fhash_active_range(v, S, R) == masked.vertex_range(v, S, R), (S, R, v)
+                assert f.fhash_active_range(v, S, R, is_time=True) == masked.time_range(v, S, R), (S, R, v)
+    with pytest.raises(f.FHashError):
+        f.fhash_active_range(5, 5, 3)
