@@ -40,7 +40,8 @@ def _digest(paths):
 
 def build(force=False, verbose=False, extra=()):
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    deps = srcs + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
+    deps = (srcs + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) +
+            glob.glob(os.path.join(ROOT, "include", "*.h")))
     tag = _digest(deps) + ("|" + " ".join(extra) if extra else "")
     stamp = OUT + ".stamp"
     if not force and os.path.exists(OUT) and os.path.exists(stamp) and open(stamp).read() == tag:
