@@ -6,6 +6,13 @@ output layer included, with accumulation in float32 on the GPU.  This module rou
 quantities to bf16 and then computes in float64, so the remaining difference to the GPU is its
 float32 accumulation (and, rarely, a value on a bf16 rounding boundary that float32 and float64
 round to neighbouring bf16 values).  Biases stay float32, as on the GPU.
+
+Pins (tests/test_oracle_precision.py): bf16_round equals torch's bf16 conversion; with every table
+value, weight, bias and activation already a bf16 value the emulation equals the float64 MLP exactly;
+hand-worked single-neuron cases on rounding ties fix each rounding point (table values, the
+interpolated layer-1 input, each weight matrix, each hidden activation before the next layer) and
+that biases are not rounded; grads_bf16 equals torch float64 autograd of the same forward with the
+roundings passed straight through and the float32 master weights in the backward.
 """
 import numpy as np
 
@@ -33,12 +40,12 @@ def forward_bf16(levels, level_bases, table, params, dims, coords, layout="linea
     return (bf16_round(x) @ bf16_round(Wo).T + bo)[:, 0]
 
 
-def grads_bf16(levels, level_bases, table, params, dims, coords, targets):
+def grads_bf16(levels, level_bases, table, params, dims, coords, targets, layout="linear"):
     """Loss and MLP gradient of one training step in the precision form: the forward of forward_bf16
     (activations kept as computed), the MSE, and the backward in float64 with the float32 master
     weights (the GPU's backward reads those, and forms the weight gradients from the stored
     activations and deltas).  Also returns the sum of |terms| of each gradient entry."""
-    enc = encode.encode(levels, level_bases, coords, bf16_round(np.asarray(table, np.float32)))
+    enc = encode.encode(levels, level_bases, coords, bf16_round(np.asarray(table, np.float32)), layout)
     layers = mlp.unpack(params, dims)
     acts, pre = [enc], []
     x = enc
