@@ -27,8 +27,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "train samples/s (enc+MLP fwd+bwd); render p50/p99 ms; BF16 vs FP32 @PSNR"
-# DRAM traffic of k_adam from one ncu capture of the current kernel on advect-128^3x32
-# (profiles/ncu_k_adam_advect-128^3x32.md): 4.106 GB read + 3.323 GB written for 256,431,321
+# DRAM traffic of k_adam from one ncu capture of the kernel on advect-128^3x32: 4.106 GB read + 3.323 GB written for 256,431,321
 # parameters, 28.97 B/param, when 21% of the 4-parameter gradient groups were non-zero (algorithmic
 # 28 + 4 x 0.21 = 28.84 B/param).  The written part depends on that fraction, so the capture does not
 # scale to the full launch in proportion; the bench reports it as a small-case ratio instead.
@@ -249,6 +248,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w["name"], "global_batch": w["batch"]},
+        "extrapolated": True,
+        "sample": "ms_per_step extrapolated from bounded samples: " + desc,
         "cpu_baseline": {"value": v, "unit": "samples/s", "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 

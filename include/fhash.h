@@ -421,8 +421,9 @@ fhash_status fhash_decode(fhash_model* model, float t_norm, int32_t upsample, fl
 /*
  * Gradient computation that allocates nothing (the paper has no counterpart to this call).
  *
- * Same result as fhash_compute_grads (forward, MSE loss, backward, gradients added to the model's
- * gradient buffer), but its working memory is a fixed array of FHASH_NOALLOC_SCRATCH_BYTES that the
+ * Same result as fhash_compute_grads on float32 models (forward, MSE loss, backward, gradients added
+ * to the model's gradient buffer); for FHASH_BF16 models, the float32-form loss and gradients of the
+ * float32 master weights (fhash_compute_grads evaluates those models' bf16 forward).  Its working memory is a fixed array of FHASH_NOALLOC_SCRATCH_BYTES that the
  * library holds in device global memory from load to exit, on every GPU that loads it.  For callers
  * that cannot call cudaMalloc: for example an application that has handed all device memory to its
  * own pool, or a latency-critical loop that cannot afford the implicit device synchronisation of
@@ -430,13 +431,13 @@ fhash_status fhash_decode(fhash_model* model, float t_norm, int32_t upsample, fl
  * cudaMalloc, cudaFree or other allocating call.
  *  - coords [n][4] and target [n] must be DEVICE memory (they are not staged); loss is host or
  *    device double* or NULL.
- *  - It evaluates the float32 form (float32 master tables and MLP on the CUDA cores), also for
- *    FHASH_BF16 models.
  *  - n must be in 1..FHASH_NOALLOC_MAX_SAMPLES; a model/n combination whose working set exceeds the
  *    array is rejected with FHASH_EINVAL before anything is launched.  FHASH_LAYOUT_MASKED models are
  *    rejected with FHASH_EINVAL (they take fhash_compute_grads).
  *  - The first call on a device, made with that device current, looks up the array's device address
- *    (cudaGetSymbolAddress) once; make that first call before any stream capture.
+ *    (cudaGetSymbolAddress) once and keeps it for the life of the process; make that first call
+ *    before any stream capture.  cudaDeviceReset invalidates the kept address (the array may be
+ *    reloaded elsewhere): do not call this entry point on a device after resetting it.
  *  - Every call shares the one array, which keeps the previous call's contents: every scratch byte
  *    this call reads it has written earlier in the same call, so nothing needs clearing, but calls
  *    that overlap on the GPU (other streams, other threads, other models) race and must be ordered

@@ -22,7 +22,7 @@ Every routine follows the paper's definitions in its own notation and order:
   Section 3.3) and the time-slice decode.
 
 Where the paper is silent or garbled the reading taken is stated beside the
-code (and listed in the design notes); the one FP32 step (cell location) is done
+code; the one FP32 step (cell location) is done
 in float32 on purpose, because it decides integer table rows and both sides must
 take that decision in the same precision.
 """

@@ -28,10 +28,27 @@ def bf16_round(x):
     return np.where(np.isnan(f), np.nan, out)
 
 
+class _RoundedRows:
+    """A lazy table (indexable by row arrays, like oracle.rng.InitTable) read through bf16_round."""
+
+    def __init__(self, table):
+        self.table = table
+
+    def __getitem__(self, rows):
+        return bf16_round(np.asarray(self.table[rows], np.float32))
+
+
+def _bf16_table(table):
+    if isinstance(table, np.ndarray):
+        return bf16_round(np.asarray(table, np.float32))
+    return _RoundedRows(table)
+
+
 def forward_bf16(levels, level_bases, table, params, dims, coords, layout="linear"):
     """y [N] of the precision form: bf16 table values, quadrilinear interpolation (float64), then every
-    layer on bf16 inputs and bf16 weights with float32 biases (ReLU after the hidden layers)."""
-    enc = encode.encode(levels, level_bases, coords, bf16_round(np.asarray(table, np.float32)), layout)
+    layer on bf16 inputs and bf16 weights with float32 biases (ReLU after the hidden layers).  `table`
+    is a dense [rows][F] array or a lazy row-indexable table."""
+    enc = encode.encode(levels, level_bases, coords, _bf16_table(table), layout)
     layers = mlp.unpack(params, dims)
     x = enc
     for k, (W, b) in enumerate(layers[:-1]):
@@ -44,8 +61,10 @@ def grads_bf16(levels, level_bases, table, params, dims, coords, targets, layout
     """Loss and MLP gradient of one training step in the precision form: the forward of forward_bf16
     (activations kept as computed), the MSE, and the backward in float64 with the float32 master
     weights (the GPU's backward reads those, and forms the weight gradients from the stored
-    activations and deltas).  Also returns the sum of |terms| of each gradient entry."""
-    enc = encode.encode(levels, level_bases, coords, bf16_round(np.asarray(table, np.float32)), layout)
+    activations and deltas).  Also returns the sum of |terms| of each gradient entry, and the gradient
+    of the loss with respect to the encoding, d_enc [N][L*F], with the sum of |terms| of each entry
+    (encode.encode_backward turns both into table gradients)."""
+    enc = encode.encode(levels, level_bases, coords, _bf16_table(table), layout)
     layers = mlp.unpack(params, dims)
     acts, pre = [enc], []
     x = enc
@@ -57,7 +76,7 @@ def grads_bf16(levels, level_bases, table, params, dims, coords, targets, layout
     Wo, bo = layers[-1]
     y = (bf16_round(x) @ bf16_round(Wo).T + bo)[:, 0]
     L, gy = mlp.mse(y, targets)
-    g, _ = mlp.backward(params, dims, acts, pre + [None], gy)
-    gabs, _ = mlp.backward(np.abs(params), dims, [np.abs(a) for a in acts],
-                           [np.where(z > 0, 1.0, -1.0) for z in pre] + [None], np.abs(gy))
-    return L, g, gabs
+    g, d_enc = mlp.backward(params, dims, acts, pre + [None], gy)
+    gabs, d_enc_abs = mlp.backward(np.abs(params), dims, [np.abs(a) for a in acts],
+                                   [np.where(z > 0, 1.0, -1.0) for z in pre] + [None], np.abs(gy))
+    return L, g, gabs, d_enc, d_enc_abs

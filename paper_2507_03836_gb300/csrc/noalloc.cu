@@ -44,6 +44,7 @@ using namespace fh;
 
 extern "C" fhash_status fhash_compute_grads_noalloc(fhash_model* m, const float* coords, const float* target, int64_t n,
                                                     double* loss, fhash_stream stream) {
+    FH_RANGE("fhash_compute_grads_noalloc");
     if (!m) return set_error(FHASH_EINVAL, "fhash_compute_grads_noalloc: null model");
     if (m->desc.layout == FHASH_LAYOUT_MASKED)
         return set_error(FHASH_EINVAL, "fhash_compute_grads_noalloc: FHASH_LAYOUT_MASKED models take fhash_compute_grads");

@@ -9,6 +9,9 @@ SplitMix64 (the library's documented initialisation), the seeded field and mask 
 - MLP gradients and the table gradient on 20000 sampled touched rows, within 1e-4 x the sum of
   the magnitudes of their terms; 2000 sampled untouched rows exactly zero;
 - the Adam update of the same rows, fed the same gradient, within 1e-6 x lr + 3e-7 x |p|;
+- the bf16 precision form at this size (brick rows, tables U(-0.5, 0.5)): forward on 4096 points
+  against the bf16 emulation, and the loss, MLP gradients and 20000 sampled table-row gradients of
+  one full-batch step against the emulation's backward (bounds of the small-workload bf16 tests);
 - masked compact tables at this size: the active bit of 20000 sampled vertices on each of four levels
   against the definition (a box query over the dilated mask), level bases equal to the running
   popcount of the bits, and the rows of all corners of 4096 footprint points active and equal to the
@@ -19,7 +22,7 @@ import pytest
 
 import synth
 from synth import workloads
-from oracle import adam, encode, index, masked, mlp, rng, schedule, train
+from oracle import adam, encode, index, masked, mlp, precision, rng, schedule, train
 
 from _util import fh, to_dev, torch
 
@@ -126,6 +129,54 @@ def _forward_train_step(model, info, field, layout):
         got[k] = one
     assert (np.abs(got - p1) <= 1e-6 * HP32[0] + 3e-7 * np.abs(p1)).all()
     fh().fhash_check(model)
+
+
+def test_fullsize_bf16_forward_and_gradients(large):
+    """The precision form at the bench size, in the launch configuration the bench uses (brick rows,
+    persistent tensor-core forward, tensor-core weight gradients).  Forward: every output within
+    4e-3 x max(|o|, RMS(o)) of the bf16 emulation and 99% within 5e-4.  One step at batch 2^18: loss
+    within 2e-3 relative, MLP gradients and the gradients of 20000 sampled touched table rows within
+    3e-3 x the sum of the magnitudes of their terms."""
+    nx, ny, nz, nt = W["dims"]
+    seed, r = 29, float(np.float32(0.5))
+    model = fh().fhash_build(nx, ny, nz, nt, mask=large["mask"], schedule=fh().make_schedule(**W["schedule"]),
+                             F=W["F"], dtype=fh().BF16, mlp_hidden_layers=W["hidden"], mlp_width=W["width"],
+                             seed=seed, init_range=0.5, layout=fh().LAYOUT_BRICK)
+    info = fh().fhash_get_info(model)
+    lv, b, F, dims = info["res"], info["base"], info["F"], info["mlp_dims"]
+    table = rng.InitTable(seed, F, r)
+    p = rng.init_mlp(seed, dims).astype(np.float64)
+
+    c = synth.coords(41, 4096)
+    c[:3] = [[0, 0, 0, 0], [1, 1, 1, 1], [np.nan, 2.0, -1.0, 0.5]]
+    out = torch().empty(c.shape[0], dtype=torch().float32, device="cuda")
+    fh().fhash_forward(model, to_dev(c), out)
+    ref = precision.forward_bf16(lv, b, table, p, dims, c, "brick")
+    err = np.abs(out.cpu().numpy() - ref) / np.maximum(np.abs(ref), np.sqrt(np.mean(ref ** 2)))
+    assert err.max() <= 4e-3 and np.mean(err <= 5e-4) >= 0.99, (err.max(), np.mean(err <= 5e-4))
+
+    B = W["batch"]
+    c = synth.coords(12_000, B)
+    tgt = synth.sample(large["field"], info["fbb_lo"], info["fbb_size"], c)
+    loss = np.zeros(1, np.float64)
+    fh().fhash_compute_grads(model, to_dev(c), to_dev(tgt), loss)
+    L, g_mlp, g_abs, d_enc, d_abs = precision.grads_bf16(lv, b, table, p, dims, c, tgt.astype(np.float64), "brick")
+    assert abs(loss[0] - L) <= 2e-3 * L, (loss[0], L)
+    g_dev = np.empty(info["n_mlp_params"], np.float32)
+    fh().fhash_read_state(model, fh().STATE_GRAD, info["n_table_params"], g_dev)
+    assert (np.abs(g_dev - g_mlp) <= 3e-3 * g_abs + 1e-9).all(), np.max(np.abs(g_dev - g_mlp) / (g_abs + 1e-9))
+    rows, g_rows = encode.encode_backward(lv, b, c, d_enc, F, "brick")
+    r_abs, g_rows_abs = encode.encode_backward(lv, b, c, d_abs, F, "brick")
+    assert np.array_equal(rows, r_abs)
+    pick = np.random.default_rng(3).choice(rows.size, 20000, replace=False)
+    got = np.empty((pick.size, F), np.float32)
+    one = np.empty(F, np.float32)
+    for k, rr in enumerate(rows[pick]):
+        fh().fhash_read_state(model, fh().STATE_GRAD, int(rr) * F, one)
+        got[k] = one
+    assert (np.abs(got - g_rows[pick]) <= 3e-3 * g_rows_abs[pick] + 1e-9).all()
+    fh().fhash_check(model)
+    del model
 
 
 def test_fullsize_finite_differences(large):

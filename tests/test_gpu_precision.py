@@ -5,7 +5,8 @@ remains is the GPU's float32 accumulation, plus a rare layer input that sits on 
 boundary, where float32 and float64 round to neighbouring bf16 values (one bf16 ulp, 2^-8 relative,
 on one input of one layer).  Tolerance: every output within 4e-3 x max(|o|, RMS(o)), and 99% of
 outputs within 5e-4 x max(|o|, RMS(o)).  PSNR against the field: serving the same trained weights in
-the precision form loses at most 0.5 dB, and training in it lands within 1 dB of float32 training
+the precision form loses at most 0.1 dB (deterministic: the rounding of tables, weights and
+activations is all that changes), and training in it lands within 1 dB of float32 training
 (atomic scatter order makes single trainings differ by tenths of a dB, so a tighter bound is not
 stable on one run; the bench reports the measured drops).
 """
@@ -141,7 +142,7 @@ def test_bf16_psnr_against_fp32(mask, capsys):
     with capsys.disabled():
         print("\nPSNR fp32 %.3f dB | bf16 serving of fp32 weights %.3f dB | bf16-trained %.3f dB" % (p32, p16_serve, p16_train))
     assert p32 > 25, p32
-    assert p16_serve >= p32 - 0.5, (p32, p16_serve)
+    assert p16_serve >= p32 - 0.1, (p32, p16_serve)
     assert p16_train >= p32 - 1.0, (p32, p16_train)
 
 
@@ -185,7 +186,7 @@ def test_bf16_gradients_parity(mask, n):
     tgt = synth.sample(f, info["fbb_lo"], info["fbb_size"], c)
     loss = np.zeros(1, np.float64)
     fh().fhash_compute_grads(model, to_dev(c), to_dev(tgt), loss)
-    L, g_ref, g_abs = precision.grads_bf16(info["res"], info["base"], table.reshape(-1, info["F"]),
+    L, g_ref, g_abs, _, _ = precision.grads_bf16(info["res"], info["base"], table.reshape(-1, info["F"]),
                                            p.astype(np.float64), info["mlp_dims"], c, tgt.astype(np.float64))
     assert abs(loss[0] - L) <= 2e-3 * L
     g = read(model, fh().STATE_GRAD, info["n_table_params"], info["n_mlp_params"]).astype(np.float64)

@@ -5,13 +5,18 @@ decodes at different upsampling and times, over an FP32, a bf16 and an FP32 mask
 (FHASH_LAYOUT_MASKED), interleaved across many
 ticks of a small packed buffer - must be bit-identical to the same request run alone through
 fhash_render / fhash_decode (per-sample arithmetic does not depend on batch position, and the image
-does not depend on the ARM pace).  Admission follows the memory budget; cancellation releases memory.
+does not depend on the ARM pace).  Served results are also checked against the oracle directly:
+renders and decodes of the float32 model against oracle/render.py with the tolerances of the
+standalone render and decode tests, the masked model against the oracle's masked layout, and the bf16
+model against oracle/render.py evaluated through the bf16 emulation (oracle/precision.py).  Admission
+follows the memory budget; cancellation releases memory.
 """
 import numpy as np
 import pytest
 
 import synth
 from synth import workloads
+from oracle import encode, index, masked, mlp, precision, render
 
 from _util import build, fh, set_params, to_dev, torch
 
@@ -137,3 +142,84 @@ def test_invalid_requests(models):
         with pytest.raises(fh().FHashError) as e:
             fh().fhash_server_submit(srv, r)
         assert e.value.status == 1
+
+
+def _oracle_eval(model, kind, m):
+    """The oracle's float64 evaluation of a served model: (function of u [n][4], FBB size, occupancy)."""
+    info = fh().fhash_get_info(model)
+    table = synth.uniform(51, 50, info["n_table_params"], -0.6, 0.6)
+    p = synth.init_mlp(51, info["mlp_dims"])
+    p[-1] = 0.45
+    d = index.dilate(m)
+    occ = index.occupancy(d, info["fbb_lo"], info["fbb_size"])
+    T = table.reshape(-1, info["F"])
+    res, dims = info["res"], info["mlp_dims"]
+    if kind == "bf16":
+        return (lambda u: precision.forward_bf16(res, info["base"], T, p.astype(np.float64), dims, u)), info, occ
+    if kind == "masked":
+        lo, size = index.fbb(d)
+        lay = masked.MaskedLayout(res, masked.fbb_mask(d, lo, size))
+        assert list(info["base"][:len(res)]) == lay.bases
+        return (lambda u: mlp.forward(p.astype(np.float64), dims,
+                                      encode.encode(res, lay.bases, u, T.astype(np.float64), lay))[0]), info, occ
+    return render.model_eval_fn(res, info["base"], T.astype(np.float64), p.astype(np.float64), dims), info, occ
+
+
+def test_served_results_match_oracle(models, capsys):
+    """Renders and decodes of all three models, served together, against the oracle.  float32 and masked:
+    composited-sample counts equal on >= 99.9% of pixels, matched pixels within 2e-4, image PSNR >= 60 dB;
+    decodes within 1e-4 x max(|o|, RMS).  bf16 against the bf16 emulation (float32 accumulation against
+    float64, and the rare layer input on a bf16 rounding tie): counts equal on >= 99.5% of pixels, 99% of
+    matched pixels within 2e-4, image PSNR >= 50 dB; decodes within 4e-3 x max(|o|, RMS), 99% within 5e-4."""
+    f, m = workloads.make_field_and_mask(W1)
+    tf_host = synth.transfer_function(0.5)
+    tf = to_dev(tf_host)
+    srv = fh().fhash_server_create(models, budget_bytes=1 << 30, max_live=8, tick_samples=4096)
+    subs = []
+    for mi in range(3):
+        w, h, t = 48, 36, 0.45 + 0.1 * mi
+        cam = synth.camera(synth.sphere_eye(6, mi), w, h)
+        out = torch().empty((h, w, 4), dtype=torch().float32, device="cuda")
+        cnt = torch().empty((h, w), dtype=torch().int32, device="cuda")
+        rid = fh().fhash_server_submit(srv, fh().make_request(fh().REQ_RENDER, mi, t, cam, w, h, 64, tf, out=out,
+                                                              counts=cnt))
+        subs.append(("r", mi, rid, out, cnt, (cam, w, h, t)))
+        d = fh().fhash_decode_dims(models[mi], 2)
+        dout = torch().empty((d[2], d[1], d[0]), dtype=torch().float32, device="cuda")
+        rid = fh().fhash_server_submit(srv, fh().make_request(fh().REQ_DECODE, mi, 0.37, upsample=2, out=dout))
+        subs.append(("d", mi, rid, dout, None, (0.37, 2)))
+        fh().fhash_server_tick(srv)
+    _run(srv, [s[2] for s in subs])
+    kinds = ["fp32", "bf16", "masked"]
+    for kind, mi, rid, out, cnt, arg in subs:
+        assert fh().fhash_server_poll(srv, rid)[0] == fh().REQ_DONE
+        ev, info, occ = _oracle_eval(models[mi], kinds[mi], m)
+        name = kinds[mi]
+        if kind == "r":
+            cam, w, h, t = arg
+            img, c = out.cpu().numpy(), cnt.cpu().numpy()
+            ref, rc = render.render(ev, cam, w, h, info["fbb_size"], occ, np.float32(t), tf_host)
+            same = c == rc
+            assert rc.sum() > 0
+            err = np.abs(img[same] - ref[same]).max(axis=-1)
+            mse = np.mean((img - ref) ** 2)
+            psnr = np.inf if mse == 0 else 10 * np.log10(1.0 / mse)
+            with capsys.disabled():
+                print("\nserved render %s: counts equal %.5f, matched max err %.3g, PSNR %.1f dB"
+                      % (name, same.mean(), err.max(), psnr))
+            if name == "bf16":
+                assert same.mean() >= 0.995 and np.mean(err <= 2e-4) >= 0.99 and psnr >= 50, name
+            else:
+                assert same.mean() >= 0.999 and err.max() <= 2e-4 and psnr >= 60, name
+        else:
+            t, up = arg
+            u, shape = render.decode_coords(info["fbb_size"], up, np.float32(t))
+            ref = ev(u).reshape(shape)
+            got = out.cpu().numpy()
+            e = np.abs(got - ref) / np.maximum(np.abs(ref), np.sqrt(np.mean(ref ** 2)))
+            with capsys.disabled():
+                print("served decode %s: max rel err %.3g" % (name, e.max()))
+            if name == "bf16":
+                assert e.max() <= 4e-3 and np.mean(e <= 5e-4) >= 0.99, name
+            else:
+                assert e.max() <= 1e-4, name

@@ -103,11 +103,11 @@ def test_exact_when_every_value_is_bf16():
     got = precision.forward_bf16(levels, bases, table, params, dims, c)
     assert np.array_equal(got, ref)
     tgt = r.standard_normal(500)
-    L, g, _ = precision.grads_bf16(levels, bases, table, params, dims, c, tgt)
+    L, g, _, d_enc, _ = precision.grads_bf16(levels, bases, table, params, dims, c, tgt)
     y, a, z = mlp.forward(params, dims, encode.encode(levels, bases, c, table.astype(np.float64)))
     L0, gy = mlp.mse(y, tgt)
-    g0, _ = mlp.backward(params, dims, a, z, gy)
-    assert L == L0 and np.array_equal(g, g0)
+    g0, d0 = mlp.backward(params, dims, a, z, gy)
+    assert L == L0 and np.array_equal(g, g0) and np.array_equal(d_enc, d0)
 
 
 def test_grads_match_straight_through_autograd():
@@ -124,11 +124,12 @@ def test_grads_match_straight_through_autograd():
     params = (r.standard_normal(mlp.n_params(dims)) * 0.4).astype(np.float32).astype(np.float64)
     c = r.random((300, 4)).astype(np.float32)
     tgt = r.standard_normal(300)
-    L, g, _ = precision.grads_bf16(levels, bases, table, params, dims, c, tgt)
+    L, g, _, d_enc, _ = precision.grads_bf16(levels, bases, table, params, dims, c, tgt)
 
-    enc = torch.from_numpy(encode.encode(levels, bases, c, precision.bf16_round(table)))
+    enc = torch.from_numpy(encode.encode(levels, bases, c, precision.bf16_round(table))).requires_grad_(True)
     bf = lambda t: t.detach().to(torch.bfloat16).to(torch.float64)   # noqa: E731
     leaves, x, o = [], enc, 0
+    # (the encoding leaf's gradient is d(loss)/d(encoding): straight through the layer-1 rounding too)
     for k in range(len(dims) - 1):
         fi, fo = dims[k], dims[k + 1]
         W = torch.tensor(params[o:o + fo * fi].reshape(fo, fi), requires_grad=True)
@@ -144,6 +145,7 @@ def test_grads_match_straight_through_autograd():
     g_ref = torch.cat([t.grad.reshape(-1) for t in leaves]).numpy()
     assert abs(L - loss.item()) <= 1e-14 * L
     assert np.allclose(g, g_ref, rtol=1e-12, atol=1e-15)
+    assert np.allclose(d_enc, enc.grad.numpy(), rtol=1e-12, atol=1e-15)
     # and the emulation's rounding matters here: the plain float64 gradient is measurably different
     y, a, z = mlp.forward(params, dims, encode.encode(levels, bases, c, table.astype(np.float64)))
     g_plain, _ = mlp.backward(params, dims, a, z, mlp.mse(y, tgt)[1])

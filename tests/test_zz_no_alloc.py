@@ -5,7 +5,10 @@ given all device memory to its own pool, or a loop that cannot take the implicit
 synchronisation of cudaMalloc/cudaFree).  It must give the same loss and gradients as the regular
 entry point: checked here on two calls in a row (gradients accumulate), within the tolerance of the
 gradient parity test (1e-4 relative to the magnitude of the entries; the atomic scatter order differs
-between runs).  This file is collected last so that a first-failure stop has run every other test.
+between runs), for both rectangular row layouts, embedding sizes F = 1, 2, 4 and 8, and a model built
+in the bf16 precision form (whose float32 form this call evaluates: it is compared with a float32
+model holding the same parameters).  The call must also leave the device's free memory unchanged.
+This file is collected last so that a first-failure stop has run every other test.
 """
 import numpy as np
 import pytest
@@ -13,7 +16,7 @@ import pytest
 import synth
 from synth import workloads
 
-from _util import build, fh, read, set_params, to_dev, torch
+from _util import fh, read, set_params, to_dev, torch
 
 pytestmark = pytest.mark.gpu
 W1 = workloads.SMALL
@@ -24,10 +27,26 @@ def _close(a, b):
     return (np.abs(a - b) <= 1e-4 * scale).all()
 
 
-def test_noalloc_matches_regular_entry_point():
-    f, m = workloads.make_field_and_mask(W1)
-    ref = build(W1, mask=m, seed=4)
-    alt = build(W1, mask=m, seed=4)
+def _build(m, F, dtype, layout, seed=4):
+    nx, ny, nz, nt = W1["dims"]
+    return fh().fhash_build(nx, ny, nz, nt, mask=m, schedule=fh().make_schedule(**W1["schedule"]), F=F, dtype=dtype,
+                            mlp_hidden_layers=W1["hidden"], mlp_width=W1["width"], seed=seed,
+                            init_range=W1["init_range"], layout=layout)
+
+
+@pytest.fixture(scope="module")
+def field_mask():
+    return workloads.make_field_and_mask(W1)
+
+
+@pytest.mark.parametrize("layout,F,dtype", [("linear", 2, "fp32"), ("brick", 2, "fp32"), ("linear", 4, "fp32"),
+                                            ("brick", 1, "fp32"), ("brick", 8, "fp32"), ("brick", 2, "bf16"),
+                                            ("linear", 4, "bf16")])
+def test_noalloc_matches_regular_entry_point(field_mask, layout, F, dtype):
+    f, m = field_mask
+    lay = fh().LAYOUT_BRICK if layout == "brick" else fh().LAYOUT_LINEAR
+    ref = _build(m, F, fh().FP32, lay)
+    alt = _build(m, F, fh().BF16 if dtype == "bf16" else fh().FP32, lay)
     info = fh().fhash_get_info(ref)
     table = synth.uniform(8, 50, info["n_table_params"], -0.5, 0.5)
     p = synth.init_mlp(8, info["mlp_dims"])
@@ -51,9 +70,28 @@ def test_noalloc_matches_regular_entry_point():
     fh().fhash_check(alt)
 
 
-def test_noalloc_rejects_oversized_batch():
-    f, m = workloads.make_field_and_mask(W1)
-    model = build(W1, mask=m)
+def test_noalloc_leaves_free_memory_unchanged(field_mask):
+    f, m = field_mask
+    model = _build(m, 2, fh().FP32, fh().LAYOUT_BRICK, seed=9)
+    info = fh().fhash_get_info(model)
+    batches = []
+    for n in (fh().NOALLOC_MAX_SAMPLES, 1, 333, 2048):
+        c = synth.coords(90 + n, n)
+        batches.append((to_dev(c), to_dev(synth.sample(f, info["fbb_lo"], info["fbb_size"], c))))
+    loss = torch().zeros(1, dtype=torch().float64, device="cuda")
+    fh().fhash_compute_grads_noalloc(model, *batches[0], loss)  # loads the library's kernels and array
+    torch().cuda.synchronize()
+    free0 = torch().cuda.mem_get_info()[0]
+    for cd, td in batches:
+        fh().fhash_compute_grads_noalloc(model, cd, td, loss)
+    torch().cuda.synchronize()
+    assert torch().cuda.mem_get_info()[0] == free0
+    fh().fhash_check(model)
+
+
+def test_noalloc_rejects_oversized_batch(field_mask):
+    f, m = field_mask
+    model = _build(m, 2, fh().FP32, fh().LAYOUT_LINEAR)
     n = fh().NOALLOC_MAX_SAMPLES + 1
     c = to_dev(synth.coords(1, n))
     t = to_dev(np.zeros(n, np.float32))
