@@ -58,21 +58,28 @@ def job_rate(world, units_per_rank, seconds):
     return world * units_per_rank / seconds
 
 
-def _touched_fraction(fh, model, info, coords, tgt, hp, chunk=1 << 28):
+def _touched_fraction(fh, model, info, coords, tgt, hp, n_deferred=0, chunk=1 << 28):
     """One more training step, untimed: the fraction of 4-parameter gradient groups that are non-zero
-    before its Adam update."""
+    before its Adam update, over the parameters Adam updates densely (all but the n_deferred parameters of
+    the deferred levels, which end the table)."""
     import torch
     n = info["n_table_params"] + info["n_mlp_params"]
+    lo = info["n_table_params"] - n_deferred
+    lo -= lo % 8
+    ranges = [(0, lo), (lo + n_deferred, n)] if n_deferred else [(0, n)]
     fh.fhash_compute_grads(model, coords, tgt)
     buf = torch.empty(min(chunk, n), dtype=torch.float32, device="cuda")
-    hit = 0
-    for off in range(0, n - n % 4, chunk):
-        k = min(chunk, n - n % 4 - off)
-        fh.fhash_read_state(model, fh.STATE_GRAD, off, buf[:k])
-        hit += int(buf[:k].view(-1, 4).ne(0).any(1).sum())
+    hit = total = 0
+    for a, b in ranges:
+        b -= (b - a) % 4
+        for off in range(a, b, chunk):
+            k = min(chunk, b - off)
+            fh.fhash_read_state(model, fh.STATE_GRAD, off, buf[:k])
+            hit += int(buf[:k].view(-1, 4).ne(0).any(1).sum())
+            total += k // 4
     fh.fhash_apply_adam(model, hp)
     torch.cuda.synchronize()
-    return hit / max(1, n // 4)
+    return hit / max(1, total)
 
 
 def _peaks():
@@ -738,6 +745,11 @@ def main():
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"],
                     help="training form: float32, or the bf16 precision form (tensor-core MLP)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving and precision legs")
+    ap.add_argument("--age-steps", type=int, default=512,
+                    help="untimed training steps on fresh batches before the warm-up (steady-state Adam deferral)")
+    ap.add_argument("--adam-deferral", type=int, default=-1,
+                    help="levels with at least this many rows defer their Adam update (0: dense Adam every "
+                         "step; -1: the library default, 2^25)")
     ap.add_argument("--serve-requests", type=int, default=60)
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--layout", default="brick", choices=["linear", "brick"],
@@ -796,16 +808,26 @@ def main():
     st = torch.cuda.current_stream()
     hp = w["adam"]
 
+    if args.adam_deferral >= 0:
+        fh.fhash_set_adam_deferral(model, args.adam_deferral)
+    # aging (untimed): steps on fresh batches, so that the deferred Adam state (how many steps each table
+    # group is behind when a batch reads it) has the distribution of a long training run, not of a
+    # fresh model (a fresh model's first steps replay almost nothing)
+    t_age = time.time()
+    for k in range(args.age_steps):
+        c = synth.coords(50_000 + 1000 * rank + k, B)
+        fh.fhash_train_step(model, torch.from_numpy(c).cuda(),
+                            torch.from_numpy(synth.sample(field, info["fbb_lo"], info["fbb_size"], c)).cuda(), hp)
+    torch.cuda.synchronize()
+    age_s = time.time() - t_age
     for k in range(args.warmup):
-        fh.fhash_compute_grads(model, coords_d[k], tgt_d[k], loss_d[k:k + 1])
-        fh.fhash_apply_adam(model, hp)
+        fh.fhash_train_step(model, coords_d[k], tgt_d[k], hp, loss_d[k:k + 1])
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
 
     K = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = Clocks(local)
     clocks.start()
@@ -813,22 +835,35 @@ def main():
     e_start.record(st)
     for k in range(K):
         i = args.warmup + k
-        ev[k][0].record(st)
-        fh.fhash_compute_grads(model, coords_d[i], tgt_d[i], loss_d[i:i + 1])
-        ev[k][1].record(st)
-        fh.fhash_apply_adam(model, hp)
-        ev[k][2].record(st)
+        fh.fhash_train_step(model, coords_d[i], tgt_d[i], hp, loss_d[i:i + 1])
     e_end.record(st)
     torch.cuda.synchronize()
     clk = clocks.stop()
     elapsed = max_over_ranks(dist, e_start.elapsed_time(e_end) / 1e3)
-    grads_ms = float(np.mean([ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]))
-    adam_ms = float(np.mean([ev[k][1].elapsed_time(ev[k][2]) for k in range(K)]))
     losses = loss_d.cpu().numpy()
 
-    # fraction of 4-parameter groups with a non-zero gradient after one step (untimed): k_adam writes the
-    # cleared gradient back only there, so its algorithmic bytes are 28 B/param + 4 B x that fraction
-    touched = _touched_fraction(fh, model, info, coords_d[args.warmup], tgt_d[args.warmup], hp)
+    # phase breakdown (untimed for the headline): the same batches again with the library's events around
+    # the phases of fhash_train_step on its stream
+    fh.fhash_set_timing(model, True)
+    ph, groups, gsteps = [], [], []
+    for k in range(K):
+        i = args.warmup + k
+        fh.fhash_train_step(model, coords_d[i], tgt_d[i], hp)
+        a = fh.fhash_get_adam_stats(model)
+        ph.append(a["last_ms"])
+        groups.append(a["last_replayed_groups"])
+        gsteps.append(a["last_replayed_steps"])
+    fh.fhash_set_timing(model, False)
+    ph = np.mean(np.array(ph), 0)
+    adam_stats = fh.fhash_get_adam_stats(model)
+    claim_ms, replay_ms, encode_ms, mlp_ms, scatter_ms, dw_ms, dense_ms = (float(x) for x in ph)
+    replay_groups, replay_steps = float(np.mean(groups)), float(np.mean(gsteps))
+    n_deferred = int(adam_stats["deferred_params"])
+
+    # fraction of 4-parameter groups with a non-zero gradient after one step in the densely updated range
+    # (untimed): k_adam writes the cleared gradient back only there, so its algorithmic bytes are
+    # 28 B/param + 4 B x that fraction
+    touched = _touched_fraction(fh, model, info, coords_d[args.warmup], tgt_d[args.warmup], hp, n_deferred)
 
     # end to end through the public API: host (pinned) inputs copied in, loss read back, every step
     pin_c = [torch.from_numpy(c).pin_memory() for c in coords_h[:K]]
@@ -853,35 +888,77 @@ def main():
 
     n_params = info["n_table_params"] + info["n_mlp_params"]
     peaks, peak_kind = _peaks()
-    # read p, g, m, v; write p, m, v, the cleared g where it was not zero (+ the bf16 shadow of p in the
-    # precision form)
-    adam_bpp = (30.0 if args.dtype == "bf16" else 28.0) + 4.0 * touched
-    adam_bytes = adam_bpp * n_params
-    achieved = adam_bytes / (adam_ms / 1e3) / 1e9
+    hbm = peaks["hbm_gbs"]
+    L, F = len(info["res"]), info["F"]
+    bf16 = args.dtype == "bf16"
+    n_dense = n_params - n_deferred
+    # Algorithmic bytes per launch of each phase kernel (each phase below is one launch, except the MLP and
+    # weight-gradient phases):
+    #  k_adam (dense range): read p, g, m, v; write p, m, v, and the cleared g where it was not zero
+    #    (+ the bf16 shadow of p in the precision form);
+    #  k_defer_replay: per caught-up 8-float group, one 32-byte sector each of p, g, m, v read and of p,
+    #    m, v written (+16 bytes of bf16 shadow);
+    #  k_encode_cols: per sample 16 corner rows of F float32 per level, the 16-byte coordinates and the
+    #    L*F encoding values written;
+    #  k_scatter_cols (its two launches): the same corner rows reduced, coordinates, d(encoding) read.
+    adam_bpp = (30.0 if bf16 else 28.0) + 4.0 * touched
+    elem = 2 if bf16 else 4
+    kern = {
+        "k_adam": (adam_bpp * n_dense, dense_ms, "dense Adam over %d parameters (levels below the deferred ones "
+                                                 "and the MLP), %.2f B/param" % (n_dense, adam_bpp)),
+        "k_defer_replay": (replay_groups * (7 * 32 + (16 if bf16 else 0)), replay_ms,
+                           "%.0f caught-up 8-float groups per step, %.1f replayed steps each on average"
+                           % (replay_groups, replay_steps / max(replay_groups, 1))),
+        "k_encode_cols": (B * (16 * L * F * 4 + 16 + L * F * 4), encode_ms,
+                          "%d samples x (16 x %d levels x %d floats gathered + 16 B coordinates + %d floats written)"
+                          % (B, L, F, L * F)),
+        "k_scatter_cols": (B * (16 * L * F * 4 + 16 + L * F * 4), scatter_ms,
+                           "%d samples x (16 x %d levels x %d floats reduced + 16 B coordinates + %d floats read)"
+                           % (B, L, F, L * F)),
+    }
+    if bf16:  # the fused tensor-core forward replaces k_encode_cols in the precision form
+        kern["k_forward_tc"] = (B * (16 * L * F * elem + 16), encode_ms, "%d samples x (16 x %d levels x %d bf16 "
+                                "gathered + 16 B coordinates)" % (B, L, F))
+        del kern["k_encode_cols"]
+    phases = {}
+    for name, (by, ms, note) in kern.items():
+        ach = by / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+        phases[name] = {"ms": ms, "bytes_per_launch": by, "achieved": ach, "frac": ach / hbm, "unit": "GB/s",
+                        "bytes": note}
+    top = max(phases, key=lambda k: phases[k]["ms"])
     value = job_rate(world, B * K, elapsed)
+    nh = w["hidden"]
+    deferred = adam_stats["first_deferred_level"] >= 0
+    per_step = (8 if not bf16 else 6 + 3 * (nh + 1)) + (3 + 2 if deferred else 1)
 
     out = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": elapsed / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.dtype, "data": "synthetic",
-        "config": {"workload": w["name"], "global_batch": B * world, "levels": len(info["res"]), "F": info["F"],
+        "config": {"workload": w["name"], "global_batch": B * world, "levels": L, "F": F,
                    "layout": args.layout,
                    "mlp": info["mlp_dims"], "table_params": info["n_table_params"],
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (%.1f GB of training state streamed per step)" % (adam_bytes / 1e9)},
-        "phases_ms": {"encode_mlp_fwd_bwd_scatter": grads_ms, "adam": adam_ms},
-        # per step, float32: encode, MLP forward, loss, MLP backward, 2 scatters, weight gradients and
-        # their reduction, Adam; precision form: fused forward, loss, MLP backward, 2 scatters, the
-        # tensor-core weight gradients, 3 reductions per layer, Adam
-        "gpu_launches": K * (9 if args.dtype == "f32" else 7 + 3 * (w["hidden"] + 1)),
-        "roofline": {"kernel": "k_adam", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                     "traffic": None,
-                     "traffic_note": "the full launch exceeds the ncu capture size rule; the small-case capture of "
-                                     "the same kernel gives measured / algorithmic bytes in traffic_small_case",
-                     "traffic_small_case": ADAM_SMALL_CASE if args.dtype == "f32" else None,
-                     "peak_source": peak_kind, "bytes_per_launch": adam_bytes, "bytes_per_param": adam_bpp,
-                     "grad_groups_touched": touched},
+                   "adam": "deferred from level %d (%d of %d parameters), bit-identical to dense"
+                           % (adam_stats["first_deferred_level"], n_deferred, n_params) if deferred else "dense",
+                   "aged_steps": args.age_steps,
+                   "l2": "inputs larger than L2: %.1f GB of training state; every step's gathers, replays and "
+                         "scatters reach it at random" % (16.0 * n_params / 1e9)},
+        "phases_ms": {"catch_up_claim_sort": claim_ms, "catch_up_replay": replay_ms, "encode": encode_ms,
+                      "mlp_fwd_loss_bwd": mlp_ms, "scatter": scatter_ms, "weight_grads": dw_ms,
+                      "adam_dense": dense_ms},
+        "adam_deferral": {"replayed_groups_per_step": replay_groups, "replayed_group_steps_per_step": replay_steps,
+                          "first_deferred_level": adam_stats["first_deferred_level"],
+                          "deferred_params": n_deferred},
+        # per step, float32: encode, MLP forward, loss, MLP backward, 2 scatters, weight gradients and their
+        # reduction; precision form: fused forward, loss, MLP backward, 2 scatters, the tensor-core weight
+        # gradients and 3 reductions per layer; then the deferred catch-up (claim, sort, replay) and Adam over
+        # the dense ranges (2 launches), or one dense Adam launch
+        "gpu_launches": K * per_step,
+        "roofline": dict(kernel=top, bound="hbm", achieved=phases[top]["achieved"], peak=hbm, unit="GB/s",
+                         frac=phases[top]["frac"], traffic=None, peak_source=peak_kind,
+                         bytes_per_launch=phases[top]["bytes_per_launch"], bytes=phases[top]["bytes"],
+                         phases=phases),
         "clocks": clk,
         "e2e": {"value": job_rate(world, B * K, e2e_s), "unit": "samples/s", "h2d_bytes_per_step": B * 20,
                 "d2h_bytes_per_step": 8},

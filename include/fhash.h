@@ -275,12 +275,55 @@ fhash_status fhash_compute_grads(fhash_model* model, const float* coords, const 
                                  double* loss, fhash_stream stream);
 
 /* One Adam step (Section 5.1.3) over every parameter using the gradient buffer, which it then
- * clears to zero; increments the step count. */
+ * clears to zero; increments the step count.  Every operation is rounded to nearest in float32 with no
+ * fused multiply-add: m = b1 m + (1 - b1) g (one fma), v = b2 v + (1 - b2) g^2 (one fma),
+ * p -= (lr / bc1) * (m / (sqrt(v) / sqrt(bc2) + eps)), with lr / bc1 and sqrt(bc2) computed in double
+ * from the step count and rounded to float32. */
 fhash_status fhash_apply_adam(fhash_model* model, const fhash_adam* adam, fhash_stream stream);
 
-/* One full training step: fhash_compute_grads followed by fhash_apply_adam. */
+/* One full training step: the result of fhash_compute_grads followed by fhash_apply_adam, bit for bit.
+ * For models with deferred levels (fhash_set_adam_deferral) the Adam update of those levels' rows is
+ * deferred to the next step that reads them, or to the next call that reads or writes the model's
+ * state, whichever comes first; no call can observe the difference. */
 fhash_status fhash_train_step(fhash_model* model, const float* coords, const float* target, int64_t n,
                               const fhash_adam* adam, double* loss, fhash_stream stream);
+
+/*
+ * Deferred Adam (an implementation of Section 5.1.3's dense Adam, not a different optimiser).  A step
+ * whose gradient is zero moves every parameter by a fixed float32 map of (parameter, first moment,
+ * second moment) that depends only on that step's scalars.  In fhash_train_step the table levels with
+ * at least min_level_rows rows (and every finer level) do not take that map every step: each group of
+ * 8 consecutive parameters remembers the last step applied to it, and when a batch is about to read
+ * it (or any other call touches the state) it replays the missed steps, the first with its pending
+ * gradient and the others with a zero gradient, with the same float32 operations in the same order as
+ * the dense update.  Parameters, gradients and moments are therefore bit-identical to dense Adam at
+ * every point a caller can observe, while a step streams only the groups its batch touches instead of
+ * every parameter.  Coarser levels and the MLP take the dense update every step.
+ *  min_level_rows: 0 turns deferral off; the default is 2^25 (33,554,432 rows).  Changing it first
+ *  brings every group to the current step (a kernel on `stream`).  The state costs 4 bytes per 8
+ *  deferred parameters (allocated at the first deferred step) and 32 bytes per step taken.
+ */
+#define FHASH_ADAM_DEFER_DEFAULT_ROWS (1ull << 25)
+fhash_status fhash_set_adam_deferral(fhash_model* model, uint64_t min_level_rows, fhash_stream stream);
+
+/* Measurement aid (no counterpart in the paper): with enable != 0, fhash_train_step records CUDA events
+ * on its stream around its phases, read back by fhash_get_adam_stats. */
+fhash_status fhash_set_timing(fhash_model* model, int32_t enable);
+
+typedef struct {
+    int32_t first_deferred_level;    /* -1 when no level is deferred */
+    uint64_t deferred_params;        /* parameters in deferred groups */
+    int64_t step, clean_step;        /* Adam steps taken; every deferred group is current at least at clean_step */
+    uint64_t last_replayed_groups;   /* last training step: groups brought up to date before its gathers */
+    uint64_t last_replayed_steps;    /* ... and the group-steps replayed for them */
+    float last_ms[7];                /* with timing on, the last training step's phases (ms): claim and
+                                        sort of the catch-up, its replay, the gathers (bf16: the fused
+                                        forward), MLP forward + loss + backward, table scatter, weight
+                                        gradients, dense Adam */
+} fhash_adam_stats;
+
+/* Deferral state and the last training step's counters; synchronises with the last training step. */
+fhash_status fhash_get_adam_stats(fhash_model* model, fhash_adam_stats* out);
 
 /*
  * Feature-based coreset (Section 3.1).  The training samples are the vertices of the dilated feature

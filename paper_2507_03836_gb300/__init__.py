@@ -80,6 +80,14 @@ class fhash_server_stats(ctypes.Structure):
                 ("pool_used", ctypes.c_uint64)]
 
 
+class fhash_adam_stats(ctypes.Structure):
+    _fields_ = [("first_deferred_level", ctypes.c_int32), ("deferred_params", ctypes.c_uint64),
+                ("step", ctypes.c_int64), ("clean_step", ctypes.c_int64), ("last_replayed_groups", ctypes.c_uint64),
+                ("last_replayed_steps", ctypes.c_uint64), ("last_ms", ctypes.c_float * 7)]
+
+
+ADAM_DEFER_DEFAULT_ROWS = 1 << 25
+
 _vp, _i64, _u64, _i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32
 _SIGS = {
     "fhash_build": [ctypes.POINTER(fhash_build_desc), _vp, ctypes.POINTER(_vp)],
@@ -96,6 +104,9 @@ _SIGS = {
     "fhash_compute_grads": [_vp, _vp, _vp, _i64, _vp, _vp],
     "fhash_apply_adam": [_vp, ctypes.POINTER(fhash_adam), _vp],
     "fhash_train_step": [_vp, _vp, _vp, _i64, ctypes.POINTER(fhash_adam), _vp, _vp],
+    "fhash_set_adam_deferral": [_vp, _u64, _vp],
+    "fhash_set_timing": [_vp, _i32],
+    "fhash_get_adam_stats": [_vp, ctypes.POINTER(fhash_adam_stats)],
     "fhash_read_state": [_vp, _i32, _u64, _u64, _vp, _vp],
     "fhash_get_params": [_vp, _vp, _vp, _vp],
     "fhash_set_params": [_vp, _vp, _vp, _vp],
@@ -295,6 +306,22 @@ def fhash_train_step(model, coords, target, adam=None, loss=None, stream=None):
     a = _adam(adam)
     _ok(_lib.fhash_train_step(model.handle, _ptr(coords), _ptr(target), coords.shape[0], ctypes.byref(a),
                               _ptr(loss), _stream(stream)))
+
+
+def fhash_set_adam_deferral(model, min_level_rows, stream=None):
+    _ok(_lib.fhash_set_adam_deferral(model.handle, int(min_level_rows), _stream(stream)))
+
+
+def fhash_set_timing(model, enable=True):
+    _ok(_lib.fhash_set_timing(model.handle, 1 if enable else 0))
+
+
+def fhash_get_adam_stats(model):
+    st = fhash_adam_stats()
+    _ok(_lib.fhash_get_adam_stats(model.handle, ctypes.byref(st)))
+    return {"first_deferred_level": st.first_deferred_level, "deferred_params": st.deferred_params,
+            "step": st.step, "clean_step": st.clean_step, "last_replayed_groups": st.last_replayed_groups,
+            "last_replayed_steps": st.last_replayed_steps, "last_ms": list(st.last_ms)}
 
 
 def fhash_coreset_build(model, volume, key_frames, stream=None):

@@ -103,6 +103,25 @@ struct fhash_model {
     int64_t cs_n = 0;
     uint64_t device_bytes = 0;
     int32_t forward_path = 0;  // FHASH_FORWARD_* (precision form only)
+
+    // deferred Adam (csrc/adam.cu): levels from defer_level on (those with at least defer_min_rows
+    // rows) hold 8-float groups [defer_lo/8, defer_hi/8) of the flat vectors, each with a stamp: the
+    // step its p, m, v are current at; every group is at least clean_step-current; dirty when some
+    // group is behind `step`.
+    uint64_t defer_min_rows = 1ull << 25;
+    int32_t defer_level = -1;
+    uint64_t defer_lo = 0, defer_hi = 0;
+    uint32_t* stamp = nullptr;
+    uint64_t stamp_groups = 0;
+    int64_t clean_step = 0;
+    bool dirty = false;
+    void* adam_tab = nullptr;  // per-step Adam scalars, indexed by step
+    int64_t adam_tab_cap = 0;
+    fh::Scratch s_defer;       // counters, claim list and its bucket-sorted copy
+    void* last_ctr = nullptr;  // counters of the last step's catch-up (device), or null
+    // phase timing of fhash_train_step (fhash_set_timing): events at the phase boundaries fh::TEV_*
+    bool timing = false, tev_init = false;
+    cudaEvent_t tev[8]{};
 };
 
 namespace fh {
@@ -116,6 +135,15 @@ __host__ __device__ __forceinline__ uint64_t sm_mix(uint64_t z) {
     return z ^ (z >> 31);
 }
 __host__ __device__ __forceinline__ uint64_t sm_at(uint64_t seed, uint64_t i) { return sm_mix(seed + (i + 1) * FH_GAMMA); }
+
+// Phase boundaries of a training step, recorded on its stream when timing is on: start, after the
+// claim and sort of the deferred catch-up, after its replay, after the gathers (the fused forward in
+// the precision form), after the MLP forward, loss and backward, after the table scatter, after the
+// weight gradients, after Adam.
+enum { TEV_START = 0, TEV_CLAIM, TEV_REPLAY, TEV_ENCODE, TEV_MLP, TEV_SCATTER, TEV_DW, TEV_ADAM, TEV_N };
+inline void tev_record(fhash_model* m, int i, cudaStream_t st) {
+    if (m->timing) cudaEventRecord(m->tev[i], st);
+}
 
 fhash_status grow(fhash_model* m, Scratch& s, size_t bytes);
 bool is_device_ptr(const void* p);
@@ -285,6 +313,12 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
 // Table-gradient scatter of the encoding alone, d(encoding) row-major [n][L*F] (csrc/train.cu).
 fhash_status launch_encode_backward(fhash_model* m, const float* coords, int64_t n, const float* denc, cudaStream_t st);
 fhash_status launch_adam(fhash_model* m, const fhash_adam* a, cudaStream_t st);
+// Training step (forward, loss, backward, Adam), deferred where the model has deferred levels (csrc/adam.cu).
+fhash_status launch_train_step(fhash_model* m, const float* coords, const float* target, int64_t n,
+                               const fhash_adam* a, double* loss_dev, cudaStream_t st);
+// Brings every deferred group to the current step; a no-op unless a deferred training step left some
+// behind.  Every entry point that reads or writes the model's state outside fhash_train_step calls it.
+fhash_status settle_deferred(fhash_model* m, cudaStream_t st);
 fhash_status refresh_shadow(fhash_model* m, uint64_t off, uint64_t n, cudaStream_t st);
 
 }  // namespace fh

@@ -1,5 +1,5 @@
 // Host glue and small kernels of the float32 path: encode / lookup launches, MLP weight gradients,
-// loss reduction and Adam (Section 5.1.3), and the C-ABI entry points for encode, forward and training.
+// loss reduction, and the C-ABI entry points for encode, forward and training (Adam: csrc/adam.cu).
 #include <math.h>
 
 #include <algorithm>
@@ -92,57 +92,6 @@ __global__ void k_loss(const double* __restrict__ partial, int nb, int64_t n, do
     if (threadIdx.x == 0) *loss = red[0] / (double)n;
 }
 
-// Adam (PyTorch semantics, dense): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
-// p -= (lr / bc1) * m / (sqrt(v) / sqrt(bc2) + eps); the gradient is cleared for the next step.
-// Streams p, g, m, v once: 16 bytes read + 16 bytes written per parameter (+2 for the bf16 shadow).
-__device__ __forceinline__ void adam1(float& p, float& g, float& m, float& v, float b1, float b2, float step_size,
-                                      float sqrt_bc2, float eps) {
-    m = fmaf(b1, m, (1.0f - b1) * g);
-    v = fmaf(b2, v, (1.0f - b2) * (g * g));
-    float denom = __fdiv_rn(sqrtf(v), sqrt_bc2) + eps;
-    p = p - step_size * __fdiv_rn(m, denom);
-    g = 0.0f;
-}
-
-template <bool SHADOW>
-__global__ void __launch_bounds__(256) k_adam(float* __restrict__ P, float* __restrict__ G, float* __restrict__ M,
-                                              float* __restrict__ V, uint64_t n, float b1, float b2, float step_size,
-                                              float sqrt_bc2, float eps, __nv_bfloat16* __restrict__ shadow) {
-    const uint64_t n4 = n / 4;
-    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (i < n4) {
-        float4* P4 = reinterpret_cast<float4*>(P);
-        float4* G4 = reinterpret_cast<float4*>(G);
-        float4* M4 = reinterpret_cast<float4*>(M);
-        float4* V4 = reinterpret_cast<float4*>(V);
-        float4 p = __ldcs(P4 + i), g = __ldcs(G4 + i), m = __ldcs(M4 + i), v = __ldcs(V4 + i);
-        // The gradient is cleared by writing zeros only where it is not zero already: a step's
-        // scatter touches a small fraction of the table rows, and untouched sectors then cost no
-        // DRAM write.  The buffer ends all-zero either way.
-        const bool touched = (g.x != 0.0f) | (g.y != 0.0f) | (g.z != 0.0f) | (g.w != 0.0f);
-        adam1(p.x, g.x, m.x, v.x, b1, b2, step_size, sqrt_bc2, eps);
-        adam1(p.y, g.y, m.y, v.y, b1, b2, step_size, sqrt_bc2, eps);
-        adam1(p.z, g.z, m.z, v.z, b1, b2, step_size, sqrt_bc2, eps);
-        adam1(p.w, g.w, m.w, v.w, b1, b2, step_size, sqrt_bc2, eps);
-        __stcs(P4 + i, p);
-        if (touched) __stcs(G4 + i, g);
-        __stcs(M4 + i, m);
-        __stcs(V4 + i, v);
-        if (SHADOW) {
-            __nv_bfloat162* s2 = reinterpret_cast<__nv_bfloat162*>(shadow) + 2 * i;
-            s2[0] = __floats2bfloat162_rn(p.x, p.y);
-            s2[1] = __floats2bfloat162_rn(p.z, p.w);
-        }
-    } else if (i - n4 < n - 4 * n4) {  // the last n % 4 parameters, one per thread
-        const uint64_t e = 4 * n4 + (i - n4);
-        float p = P[e], g = G[e], m = M[e], v = V[e];
-        adam1(p, g, m, v, b1, b2, step_size, sqrt_bc2, eps);
-        P[e] = p; M[e] = m; V[e] = v;
-        G[e] = 0.0f;
-        if (SHADOW) shadow[e] = __float2bfloat16_rn(p);
-    }
-}
-
 cudaError_t run_fused_any(int F, int which, const FusedArgs& a);
 cudaError_t run_tc_any(fhash_model* m, bool train, FusedArgs& a);
 
@@ -218,25 +167,6 @@ fhash_status launch_forward_seg(fhash_model* m, const float* coords, float* out,
     return FHASH_OK;
 }
 
-fhash_status launch_adam(fhash_model* m, const fhash_adam* ad, cudaStream_t st) {
-    m->step += 1;
-    const double k = (double)m->step;
-    const double bc1 = 1.0 - pow((double)ad->beta1, k), bc2 = 1.0 - pow((double)ad->beta2, k);
-    // one thread per float4 (plus one per leftover parameter), no grid-stride loop: measured fastest on
-    // GB300 at this size (every thread issues its four 16-byte loads at once)
-    const uint64_t n4 = m->n_params / 4, threads = n4 + (m->n_params - 4 * n4);
-    const unsigned grid = (unsigned)std::max<uint64_t>(1, (threads + 255) / 256);
-    const float ss = (float)(ad->lr / bc1), sb = (float)sqrt(bc2);
-    if (m->shadow)
-        k_adam<true><<<grid, 256, 0, st>>>(m->param, m->grad, m->adam_m, m->adam_v, m->n_params, ad->beta1, ad->beta2,
-                                           ss, sb, ad->eps, m->shadow);
-    else
-        k_adam<false><<<grid, 256, 0, st>>>(m->param, m->grad, m->adam_m, m->adam_v, m->n_params, ad->beta1, ad->beta2,
-                                            ss, sb, ad->eps, nullptr);
-    FH_CUDA(cudaGetLastError());
-    return FHASH_OK;
-}
-
 }  // namespace fh
 
 using namespace fh;
@@ -264,6 +194,7 @@ fhash_status fhash_encode(fhash_model* m, const float* coords, int64_t n, float*
     if (n < 0 || (n && (!coords || !enc))) return set_error(FHASH_EINVAL, "fhash_encode: bad arguments");
     if (n == 0) return FHASH_OK;
     if (!is_device_ptr(coords) || !is_device_ptr(enc)) return set_error(FHASH_EINVAL, "fhash_encode: buffers must be device memory");
+    FH_TRY(settle_deferred(m, (cudaStream_t)stream));
     return launch_encode(m, coords, n, enc, (cudaStream_t)stream);
 }
 
@@ -275,6 +206,7 @@ fhash_status fhash_encode_backward(fhash_model* m, const float* coords, const fl
     if (n == 0) return FHASH_OK;
     if (!is_device_ptr(coords) || !is_device_ptr(d_enc))
         return set_error(FHASH_EINVAL, "fhash_encode_backward: buffers must be device memory");
+    FH_TRY(settle_deferred(m, (cudaStream_t)stream));
     return launch_encode_backward(m, coords, n, d_enc, (cudaStream_t)stream);
 }
 
@@ -292,6 +224,7 @@ fhash_status fhash_forward(fhash_model* m, const float* coords, int64_t n, float
     if (n < 0 || (n && (!coords || !out))) return set_error(FHASH_EINVAL, "fhash_forward: bad arguments");
     if (n == 0) return FHASH_OK;
     cudaStream_t st = (cudaStream_t)stream;
+    FH_TRY(settle_deferred(m, st));
     const void* dc;
     FH_TRY(stage_in(m, m->s_coords, coords, (size_t)n * 16, st, &dc));
     bool host_out = !is_device_ptr(out);
@@ -311,6 +244,7 @@ fhash_status fhash_compute_grads(fhash_model* m, const float* coords, const floa
     FH_TRY(check_model(m, "fhash_compute_grads"));
     if (n <= 0 || !coords || !target) return set_error(FHASH_EINVAL, "fhash_compute_grads: need n > 0, coords and target");
     cudaStream_t st = (cudaStream_t)stream;
+    FH_TRY(settle_deferred(m, st));
     const void *dc, *dt;
     FH_TRY(stage_in(m, m->s_coords, coords, (size_t)n * 16, st, &dc));
     FH_TRY(stage_in(m, m->s_target, target, (size_t)n * 4, st, &dt));
@@ -345,8 +279,10 @@ fhash_status fhash_train_step(fhash_model* m, const float* coords, const float* 
     FH_TRY(stage_in(m, m->s_target, target, (size_t)n * 4, st, &dt));
     FH_TRY(grow(m, m->s_loss, 64));
     bool dev_loss = loss && is_device_ptr(loss);
-    FH_TRY(launch_grads2(m, (const float*)dc, (const float*)dt, n, dev_loss ? loss : (double*)m->s_loss.p, st));
-    FH_TRY(fhash_apply_adam(m, a, stream));
+    if (!(a->lr >= 0.0f) || !(a->beta1 >= 0.0f && a->beta1 < 1.0f) || !(a->beta2 >= 0.0f && a->beta2 < 1.0f) ||
+        !(a->eps > 0.0f))
+        return set_error(FHASH_EINVAL, "fhash_train_step: bad hyper-parameters");
+    FH_TRY(launch_train_step(m, (const float*)dc, (const float*)dt, n, a, dev_loss ? loss : (double*)m->s_loss.p, st));
     if (loss && !dev_loss) {
         FH_CUDA(cudaMemcpyAsync(loss, m->s_loss.p, 8, cudaMemcpyDeviceToHost, st));
         FH_CUDA(cudaStreamSynchronize(st));

@@ -406,9 +406,12 @@ static void destroy_model(fhash_model* m) {
     cudaDeviceSynchronize();
     void* ps[] = {m->param, m->grad, m->adam_m, m->adam_v, m->shadow, m->occ, m->occ_any, m->dir, m->err_word,
                   m->s_coords.p, m->s_target.p, m->s_out.p, m->s_acts.p, m->s_gacts.p, m->s_partial.p,
-                  m->s_loss.p, m->s_misc.p, m->s_render.p, m->s_enc.p, m->s_cs_ent.p, m->s_cs_val.p};
+                  m->s_loss.p, m->s_misc.p, m->s_render.p, m->s_enc.p, m->s_cs_ent.p, m->s_cs_val.p,
+                  m->stamp, m->adam_tab, m->s_defer.p};
     for (void* p : ps)
         if (p) cudaFree(p);
+    if (m->tev_init)
+        for (cudaEvent_t e : m->tev) cudaEventDestroy(e);
     delete m;
 }
 
@@ -678,6 +681,7 @@ fhash_status fhash_read_state(fhash_model* m, int32_t which, uint64_t off, uint6
     float* p = state_ptr(m, which);
     if (!p) return set_error(FHASH_EINVAL, "fhash_read_state: unknown state %d", which);
     if (off > m->n_params || n > m->n_params - off) return set_error(FHASH_EINVAL, "fhash_read_state: range out of bounds");
+    FH_TRY(settle_deferred(m, (cudaStream_t)stream));
     if (n) FH_CUDA(cudaMemcpyAsync(buf, p + off, n * 4, cudaMemcpyDefault, (cudaStream_t)stream));
     return FHASH_OK;
 }
@@ -687,6 +691,7 @@ fhash_status fhash_write_state(fhash_model* m, int32_t which, uint64_t off, uint
     float* p = state_ptr(m, which);
     if (!p) return set_error(FHASH_EINVAL, "fhash_write_state: unknown state %d", which);
     if (off > m->n_params || n > m->n_params - off) return set_error(FHASH_EINVAL, "fhash_write_state: range out of bounds");
+    FH_TRY(settle_deferred(m, (cudaStream_t)stream));
     if (n) FH_CUDA(cudaMemcpyAsync(p + off, buf, n * 4, cudaMemcpyDefault, (cudaStream_t)stream));
     if (which == FHASH_STATE_PARAM) FH_TRY(refresh_shadow(m, off, n, (cudaStream_t)stream));
     return FHASH_OK;
@@ -815,6 +820,7 @@ fhash_status fhash_save(const fhash_model* mc, const char* path) {
     FH_RANGE("fhash_save");
     fhash_model* m = const_cast<fhash_model*>(mc);
     if (!m || !path) return set_error(FHASH_EINVAL, "fhash_save: null argument");
+    FH_TRY(settle_deferred(m, 0));
     FH_CUDA(cudaDeviceSynchronize());
     FILE* f = fopen(path, "wb");
     if (!f) return set_error(FHASH_EIO, "fhash_save: cannot open %s", path);
@@ -872,7 +878,7 @@ fhash_status fhash_load(const char* path, fhash_stream stream, fhash_model** out
     m->mlp = h.mlp;
     m->total_rows = h.total_rows; m->n_table = h.n_table; m->n_params = h.n_params;
     for (int a = 0; a < 3; ++a) { m->fbb_lo[a] = h.fbb_lo[a]; m->fbb_size[a] = h.fbb_size[a]; }
-    m->nt = h.nt; m->step = h.step; m->nbx = h.nbx; m->nby = h.nby; m->nbz = h.nbz;
+    m->nt = h.nt; m->step = h.step; m->clean_step = h.step; m->nbx = h.nbx; m->nby = h.nby; m->nbz = h.nbz;
     const uint64_t nb = (uint64_t)(m->nbx * m->nby * m->nbz * m->nt);
     const size_t bytes = (size_t)m->n_params * 4;
     FH_TRY(dev_alloc(m, (void**)&m->err_word, sizeof(int)));

@@ -54,6 +54,7 @@ extern "C" fhash_status fhash_compute_grads_noalloc(fhash_model* m, const float*
     if (!is_device_ptr(coords) || !is_device_ptr(target))
         return set_error(FHASH_EINVAL, "fhash_compute_grads_noalloc: coords and target must be device memory");
     cudaStream_t st = (cudaStream_t)stream;
+    FH_TRY(settle_deferred(m, st));  // a kernel launch over the model's own buffers: no allocation
     const MlpShape& sh = m->mlp;
     const int W = sh.width;
     const int64_t A = sh.in + (int64_t)sh.nh * W, D = (int64_t)sh.nh * W + 1;

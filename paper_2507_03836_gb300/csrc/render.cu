@@ -285,6 +285,7 @@ fhash_status fhash_decode(fhash_model* m, float t_norm, int32_t upsample, float*
     for (int a = 0; a < 3; ++a) d[a] = decode_points(m->fbb_size[a], upsample);
     if (d[0] * d[1] * d[2] >= (1ll << 40)) return set_error(FHASH_EINVAL, "fhash_decode: grid too large");
     cudaStream_t st = (cudaStream_t)stream;
+    FH_TRY(settle_deferred(m, st));
     if (m->shadow) {  // precision form: coordinates in chunks, then the tensor-core forward
         const int64_t total = d[0] * d[1] * d[2], chunk = 1 << 23;
         FH_TRY(grow(m, m->s_misc, (size_t)chunk * 16));
@@ -319,6 +320,7 @@ fhash_status fhash_render(fhash_model* m, const fhash_camera* cam, float t_norm,
     if (!is_device_ptr(tf) || !is_device_ptr(rgba) || (counts && !is_device_ptr(counts)))
         return set_error(FHASH_EINVAL, "fhash_render: tf, rgba and counts must be device memory");
     cudaStream_t st = (cudaStream_t)stream;
+    FH_TRY(settle_deferred(m, st));
     const RenderGeo g = make_geo(m, cam, t_norm, w, h);
     const int64_t NR = (int64_t)w * h;
     // scratch: ray states, two alive lists, sample coords and values, per-ray counts, counters

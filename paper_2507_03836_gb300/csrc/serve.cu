@@ -110,6 +110,7 @@ fhash_status fhash_server_create(fhash_model* const* models, int32_t n_models, u
     uint64_t fixed = (uint64_t)tick_samples * 20 + 4096;
     for (int i = 0; i < n_models; ++i) {
         if (!models[i]) return set_error(FHASH_EINVAL, "fhash_server_create: null model %d", i);
+        FH_TRY(settle_deferred(models[i], (cudaStream_t)stream));
         fixed += serving_bytes(models[i]);
     }
     if (fixed >= budget)
@@ -224,6 +225,7 @@ fhash_status fhash_server_tick(fhash_server* s, fhash_stream stream, int32_t* n_
     if (!s) return set_error(FHASH_EINVAL, "fhash_server_tick: null server");
     std::lock_guard<std::mutex> lock(s->mu);
     cudaStream_t st = (cudaStream_t)stream;
+    for (fhash_model* m : s->models) FH_TRY(settle_deferred(m, st));  // a model trained since the last tick
     int done = 0;
     // drop cancelled live requests (their last tick has completed: every tick ends synchronised)
     for (size_t i = 0; i < s->live.size();) {

@@ -544,6 +544,7 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
         a.coords = coords; a.target = target; a.n = n; a.acts = acts; a.gy = gy; a.partial = lpart; a.st = st;
         FH_CUDA(run_tc_any(m, true, a));
         nb = a.grid;  // at most one loss partial per CTA, never more than the buffer holds
+        tev_record(m, TEV_ENCODE, st);
     } else {
         const unsigned eg = (unsigned)((n * m->lv.L + 255) / 256);
         switch (F) {
@@ -554,6 +555,7 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
             default: return set_error(FHASH_EINVAL, "F=%d unsupported", F);
         }
         FH_CUDA(cudaGetLastError());
+        tev_record(m, TEV_ENCODE, st);
         FH_CUDA(cudaFuncSetAttribute((const void*)k_mlp_fwd_t, cudaFuncAttributeMaxDynamicSharedMemorySize, tsmem));
         nb = std::min(nb, tile_grid);  // one loss partial per block
         k_mlp_fwd_t<<<nb, 256, tsmem, st>>>(sh, Pm, target, n, 2.0f / (float)n, acts, gy, lpart);
@@ -566,18 +568,21 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
     FH_CUDA(cudaFuncSetAttribute((const void*)k_mlp_bwd_t, cudaFuncAttributeMaxDynamicSharedMemorySize, tsmem));
     k_mlp_bwd_t<<<bb, 256, tsmem, st>>>(sh, Pm, n, acts, gy, dl, denc);
     FH_CUDA(cudaGetLastError());
+    tev_record(m, TEV_MLP, st);
     switch (F) {
         case 1: FH_CUDA(scatter_launch<1>(m, coords, n, denc, n, 1, st)); break;
         case 2: FH_CUDA(scatter_launch<2>(m, coords, n, denc, n, 1, st)); break;
         case 4: FH_CUDA(scatter_launch<4>(m, coords, n, denc, n, 1, st)); break;
         case 8: FH_CUDA(scatter_launch<8>(m, coords, n, denc, n, 1, st)); break;
     }
+    tev_record(m, TEV_SCATTER, st);
     // weight gradients: tensor cores (TMA + tcgen05 kind::tf32) for the bf16 form, float32 SIMT tiles
     // otherwise (the float32 form keeps full float32 products)
     if (m->shadow) {
         cudaError_t e = cudaSuccess;
         if (launch_dw_tc(m, acts, dl, n, wpart, m->s_partial.bytes - wpart_off, st, &e)) {
             FH_CUDA(e);
+            tev_record(m, TEV_DW, st);
             return FHASH_OK;
         }
     }
@@ -592,6 +597,7 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
     FH_CUDA(cudaGetLastError());
     k_dw_reduce2<<<dim3((kDwStride + 255) / 256, nl), 256, 0, st>>>(wpart, nchunk, Ls, sh, m->grad + m->n_table);
     FH_CUDA(cudaGetLastError());
+    tev_record(m, TEV_DW, st);
     return FHASH_OK;
 }
 
