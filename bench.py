@@ -273,12 +273,9 @@ def _copy_params(src, dst, n, chunk=1 << 28):
     torch.cuda.synchronize()
 
 
-def serving_leg(args, w, model, info, field, mask, rank):
-    """Render serving of the trained model in FP32 and in the precision form (bf16 + tensor cores):
-    a Poisson stream of renders (sizes uniform in {256^2, 512^2, 1024^2}, cameras uniform on the
-    radius-2 sphere, t uniform in [0,1], 256-entry transfer function) through the continuous-batching
-    server; latency from arrival to completion.  Also PSNR / max error of both forms on 1M held-out
-    points against the field."""
+def precision_leg(args, w, model, info, field, mask, rank):
+    """The trained model served in FP32 and in the precision form (bf16 + tensor cores, the same weights):
+    PSNR and max error of both forms on 1M held-out points against the field."""
     import torch
     import synth
     import paper_2507_03836_gb300 as fh
@@ -304,59 +301,10 @@ def serving_leg(args, w, model, info, field, mask, rank):
         prec["max_abs_err_" + name] = float(np.abs(pred - truth).max())
     prec["psnr_drop_db"] = prec["psnr_fp32"] - prec["psnr_bf16"]
 
-    tf = torch.from_numpy(synth.transfer_function(0.5)).cuda()
-    rng = np.random.default_rng(1234)
-    n_req = args.serve_requests
-    arrivals = np.cumsum(rng.exponential(1.0 / args.serve_rate, n_req))
-    sizes = rng.choice([256, 512, 1024], n_req)
-    times = rng.random(n_req)
-    render = {"requests": n_req, "rate_req_s": args.serve_rate, "sizes": [256, 512, 1024],
-              "model": w["name"] + " after the timed training steps"}
-    outs = [torch.empty((int(s), int(s), 4), dtype=torch.float32, device="cuda") for s in sizes]
-    for name, mi in (("fp32", 0), ("bf16", 1)):
-        srv = fh.fhash_server_create([model, m16], budget_bytes=64 << 30, max_live=64, tick_samples=1 << 22)
-        # warm-up request (graph replays and kernels loaded)
-        cam = synth.camera(synth.sphere_eye(99, 0), 256, 256)
-        wid = fh.fhash_server_submit(srv, fh.make_request(fh.REQ_RENDER, mi, 0.5, cam, 256, 256, 64, tf, out=outs[0]))
-        while fh.fhash_server_poll(srv, wid)[0] != fh.REQ_DONE:
-            fh.fhash_server_tick(srv)
-        st0 = fh.fhash_server_get_stats(srv)
-        torch.cuda.synchronize()
-        lat = np.zeros(n_req)
-        done = np.zeros(n_req, bool)
-        ids = {}
-        nxt = 0
-        t0 = time.perf_counter()
-        while not done.all():
-            now = time.perf_counter() - t0
-            while nxt < n_req and arrivals[nxt] <= now:
-                s_ = int(sizes[nxt])
-                cam = synth.camera(synth.sphere_eye(7, nxt), s_, s_)
-                ids[nxt] = fh.fhash_server_submit(srv, fh.make_request(fh.REQ_RENDER, mi, float(times[nxt]), cam, s_, s_,
-                                                                       64, tf, out=outs[nxt]))
-                nxt += 1
-            if not ids or all(done[k] for k in ids):
-                time.sleep(max(0.0, min(arrivals[nxt] - (time.perf_counter() - t0), 0.01)) if nxt < n_req else 0)
-                continue
-            fh.fhash_server_tick(srv)
-            tnow = time.perf_counter() - t0
-            for k, rid in ids.items():
-                if not done[k] and fh.fhash_server_poll(srv, rid)[0] == fh.REQ_DONE:
-                    done[k] = True
-                    lat[k] = (tnow - arrivals[k]) * 1e3
-        elapsed = time.perf_counter() - t0
-        st = fh.fhash_server_get_stats(srv)
-        samples = st["samples"] - st0["samples"]
-        render[name] = {"p50_ms": float(np.percentile(lat, 50)), "p95_ms": float(np.percentile(lat, 95)),
-                        "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
-                        "throughput_samples_s": samples / elapsed, "requests_s": n_req / elapsed,
-                        "ticks": st["ticks"] - st0["ticks"], "graph_launches": st["model_launches"] - st0["model_launches"]}
-        del srv
     del m16
-    return {"render": render, "precision": prec}
+    return prec
 
 
-# ------------------------------------------------------------------ suites beyond the default line
 def _build(w, dtype, seed, mask, layout=0):
     import paper_2507_03836_gb300 as fh
     nx, ny, nz, nt = w["dims"]
@@ -406,7 +354,7 @@ def _psnr(model, info, field, n=1 << 20, seed=777):
     return float(10 * np.log10(rng ** 2 / np.mean((pred - truth) ** 2))), float(np.abs(pred - truth).max())
 
 
-def suite_precision(args):
+def leg_precision_front(args, steps):
     """Precision form against float32 on the Combustion-shaped front: both trained from the same start on the
     same batches; samples/s of each, and PSNR / max abs error on 1M held-out points against the field."""
     import paper_2507_03836_gb300 as fh
@@ -414,17 +362,25 @@ def suite_precision(args):
     w = workloads.FRONT
     t0 = time.time()
     field, mask = workloads.make_field_and_mask(w)
-    res = {"suite": "precision", "workload": w["name"], "steps": args.steps, "batch": w["batch"]}
+    res = {"workload": w["name"], "steps": steps, "batch": w["batch"],
+           "note": "both forms trained from the same fresh start; ms_per_step over all but 3 warm-up steps"}
     for name, dt in (("fp32", fh.FP32), ("bf16", fh.BF16)):
         model, info = _build(w, dt, 5, mask, _layout(args))
-        batches = _batches(w, info, field, args.steps + 3, 50_000)
+        batches = _batches(w, info, field, steps + 3, 50_000)
         ms = _train(model, batches, w["adam"])
         p, e = _psnr(model, info, field)
         res[name] = {"ms_per_step": ms, "samples_s": w["batch"] / ms * 1e3, "psnr_db": p, "max_abs_err": e,
                      "params": info["n_table_params"] + info["n_mlp_params"]}
         del model, batches
     res["psnr_drop_db"] = res["fp32"]["psnr_db"] - res["bf16"]["psnr_db"]
+    res["bf16_over_fp32_samples_s"] = res["bf16"]["samples_s"] / res["fp32"]["samples_s"]
     res["setup_s"] = time.time() - t0
+    return res
+
+
+def suite_precision(args):
+    res = leg_precision_front(args, args.steps)
+    res["suite"] = "precision"
     print(json.dumps(res))
 
 
@@ -619,12 +575,16 @@ def suite_peaks(args):
 
 def _serve(models, kinds, n_req, rate, budget, tf, seed=1234, decode_every=0):
     """Poisson stream through one server; kinds[i] = model index of request i; every `decode_every`-th
-    request (0: none) is a time-slice decode (upsample 1 or 2), the rest renders of 256^2/512^2/1024^2."""
+    request (0: none) is a time-slice decode (upsample 1 or 2), the rest renders of 256^2/512^2/1024^2.
+    rate None: closed loop, each request submitted when the previous one is done (service time alone)."""
     import torch
     import synth
     import paper_2507_03836_gb300 as fh
     rng = np.random.default_rng(seed)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    closed = rate is None
+    arrivals = np.cumsum(rng.exponential(1.0 / (rate or 1.0), n_req))
+    if closed:
+        arrivals[:] = np.inf
     sizes = rng.choice([256, 512, 1024], n_req)
     times = rng.random(n_req)
     ups = rng.choice([1, 2], n_req)
@@ -655,6 +615,8 @@ def _serve(models, kinds, n_req, rate, budget, tf, seed=1234, decode_every=0):
     t0 = time.perf_counter()
     while not done.all():
         now = time.perf_counter() - t0
+        if closed and nxt < n_req and all(done[k] for k in ids):  # one at a time: arrival = now
+            arrivals[nxt] = now
         while nxt < n_req and arrivals[nxt] <= now:
             ids[nxt] = fh.fhash_server_submit(srv, reqs[nxt])
             nxt += 1
@@ -684,9 +646,11 @@ def _serve(models, kinds, n_req, rate, budget, tf, seed=1234, decode_every=0):
     return out
 
 
-def suite_serve(args):
-    """Render serving on the Supernova-shaped shell model (trained as the default workload): Poisson stream,
-    FP32 form and the precision form (same weights), p50/p95/p99 and samples/s; PSNR of both forms."""
+def leg_serve_shell(args, steps, n_req, rate, alone=0):
+    """Render serving on the Supernova-shaped shell model (trained as the default workload for `steps`
+    steps): Poisson stream at `rate` req/s, FP32 form and the precision form (same weights), p50/p95/p99 and
+    samples/s; PSNR of both forms; with alone > 0 also the latency of the first `alone` requests served one
+    at a time (service time without queueing)."""
     import torch
     import synth
     import paper_2507_03836_gb300 as fh
@@ -695,16 +659,27 @@ def suite_serve(args):
     t0 = time.time()
     field, mask = workloads.make_field_and_mask(w)
     m32, info = _build(w, fh.FP32, 6, mask, _layout(args))
-    ms = _train(m32, _batches(w, info, field, args.steps + 3, 60_000), w["adam"])
+    ms = _train(m32, _batches(w, info, field, steps + 3, 60_000), w["adam"])
     m16, _ = _build(w, fh.BF16, 6, mask, _layout(args))
+    del mask
     _copy_params(m32, m16, info["n_table_params"] + info["n_mlp_params"])
     tf = torch.from_numpy(synth.transfer_function(0.5)).cuda()
-    res = {"suite": "serve", "workload": w["name"], "train_steps": args.steps + 3, "train_ms_per_step": ms,
-           "requests": args.serve_requests, "rate_req_s": args.serve_rate}
+    res = {"workload": w["name"], "model_params": info["n_table_params"] + info["n_mlp_params"],
+           "train_steps": steps + 3, "train_ms_per_step": ms, "requests": n_req, "rate_req_s": rate,
+           "images": "uniform in {256^2, 512^2, 1024^2}, cameras on the radius-2 sphere, t uniform in [0,1]"}
     for name, mi in (("fp32", 0), ("bf16", 1)):
-        res[name] = _serve([m32, m16], [mi] * args.serve_requests, args.serve_requests, args.serve_rate, 96 << 30, tf)
+        res[name] = _serve([m32, m16], [mi] * n_req, n_req, rate, 96 << 30, tf)
+        if alone:
+            res[name]["alone"] = _serve([m32, m16], [mi] * alone, alone, None, 96 << 30, tf)
         res[name]["psnr_db"], res[name]["max_abs_err"] = _psnr(m32 if mi == 0 else m16, info, field)
     res["setup_s"] = time.time() - t0
+    del m32, m16
+    return res
+
+
+def suite_serve(args):
+    res = leg_serve_shell(args, args.steps, args.serve_requests, args.serve_rate)
+    res["suite"] = "serve"
     print(json.dumps(res))
 
 
@@ -751,6 +726,10 @@ def main():
                     help="levels with at least this many rows defer their Adam update (0: dense Adam every "
                          "step; -1: the library default, 2^25)")
     ap.add_argument("--serve-requests", type=int, default=60)
+    ap.add_argument("--serve-alone", type=int, default=12, help="requests also served one at a time (no queueing)")
+    ap.add_argument("--serve-train-steps", type=int, default=40, help="training steps of the served shell model")
+    ap.add_argument("--precision-steps", type=int, default=20, help="training steps per form on the front model")
+    ap.add_argument("--no-precision-suite", action="store_true", help="skip the front-model bf16 vs fp32 leg")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--layout", default="brick", choices=["linear", "brick"],
                     help="table row layout: 4x4x4 bricks per time slice (the default: the faster F-Hash "
@@ -881,9 +860,9 @@ def main():
     e2e_s = max_over_ranks(dist, time.perf_counter() - t1)
     fh.fhash_check(model)
 
-    serve = None
+    prec = None
     if not args.no_serve:
-        serve = serving_leg(args, w, model, info, field, mask_for_bf16, rank)
+        prec = precision_leg(args, w, model, info, field, mask_for_bf16, rank)
     del mask_for_bf16
 
     n_params = info["n_table_params"] + info["n_mlp_params"]
@@ -965,9 +944,18 @@ def main():
         "loss_first_last": [float(losses[0]), float(losses[-1])],
         "setup_s": setup_s,
     }
-    if serve:
-        out["render"] = serve["render"]
-        out["precision"] = serve["precision"]
+    if prec:
+        out["precision"] = prec
+    if not args.no_serve:
+        # the other configurations, after the training model is released: renders served on the shell model
+        # (config 4: Poisson stream at 200 req/s, and the same requests one at a time), and bf16 against
+        # float32 training on the front model (config 3)
+        del model
+        torch.cuda.synchronize()
+        out["render"] = leg_serve_shell(args, args.serve_train_steps, args.serve_requests, args.serve_rate,
+                                        alone=args.serve_alone)
+        if not args.no_precision_suite:
+            out["precision_front"] = leg_precision_front(args, args.precision_steps)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t, desc = oracle_step_sample(w, 32768, adam_slice=1 << 25)
         one = {"value": B / t, "unit": "samples/s", "cores": 1, "kind": "oracle", "sample": desc}

@@ -144,6 +144,13 @@ typedef struct {
     uint64_t seed;
     float init_range;
     int32_t layout;  /* FHASH_LAYOUT_LINEAR (Eq. 9, the default), _BRICK or _MASKED */
+    /* Several features in one model (Section 3.1 merges the occupancy grids of several features for
+     * rendering): n_masks > 0 host masks of the same shape as `mask` (which must then be NULL).  Each is
+     * dilated on its own and the dilated regions are OR-merged: the Feature Bounding Box is the box of
+     * the union, the occupancy grid its bits, and the masked layout keeps the vertices near any of
+     * them.  0 means the single `mask` (or none). */
+    const uint8_t* const* masks;
+    int32_t n_masks;
 } fhash_build_desc;
 
 /* Read-only description of a built model. */
@@ -444,7 +451,9 @@ typedef struct {
  *      interpolation; alpha is per sample (already corrected for the spacing).
  *  rgba: device [h][w][4] float32 = (accumulated colour, opacity); rays missing the box give 0.
  *  counts: device [h][w] int32 composited samples per pixel, or NULL.  stats: host, or NULL.
- * Synchronous (the round loop reads the alive count back every round).
+ * Synchronous.  Each round's kernels read the alive count from device memory, so rounds are issued
+ * in batches of 1, 2, 4, ... up to 64 with one read-back of the alive count per batch instead of one
+ * per round.
  */
 fhash_status fhash_render(fhash_model* model, const fhash_camera* cam, float t_norm, const float* tf, int32_t w,
                           int32_t h, int32_t max_pace, float* rgba, int32_t* counts, fhash_render_stats* stats,

@@ -18,6 +18,9 @@
  *     device memory);
  *  4. composites render samples and copies decode values to the requests' outputs, then reads every
  *     request's progress back with one copy and one synchronisation.
+ * Steps 2 and 4 are one kernel launch each over all live requests (a per-tick work table gives every
+ * request its range of threads), and the rays of all renders admitted in a tick are set up by one more
+ * launch: a tick makes a number of launches that does not grow with the number of live requests.
  * A render's w*h may not exceed tick_samples (one round of all its rays must fit in a tick).
  * Requests that arrive while others are on the GPU join at the next tick.  Per-sample arithmetic does
  * not depend on where a sample sits in the packed buffer and the image does not depend on the pace,
@@ -66,6 +69,9 @@ typedef struct {
     int64_t live, queued;   /* current request counts */
     uint64_t pool_bytes;    /* request scratch pool */
     uint64_t pool_used;
+    int64_t packed_launches; /* the other kernel launches: one ray initialisation per admission tick,
+                                one sample generation and one compositing launch per tick, each over
+                                every live request */
 } fhash_server_stats;
 
 /*

@@ -22,6 +22,17 @@ def dilate(mask):
     return out
 
 
+def merge_features(masks):
+    """Several features in one model: Section 3.1 merges the occupancy grids of several features for
+    rendering.  Each feature mask is dilated on its own (as above) and the dilated regions are OR-ed;
+    the Feature Bounding Box and the occupancy grid are then those of the union."""
+    out = None
+    for m in masks:
+        d = dilate(m)
+        out = d if out is None else (out | d)
+    return out
+
+
 def frame_boxes(d):
     """Bounding box b_k of each frame's dilated feature (Section 3.1): inclusive [lo, hi] in
     (x, y, z) order, or None for an empty frame."""

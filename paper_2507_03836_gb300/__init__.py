@@ -42,7 +42,8 @@ class fhash_build_desc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64), ("nt", ctypes.c_int64),
                 ("mask", ctypes.c_void_p), ("sched", fhash_schedule), ("F", ctypes.c_int32), ("dtype", ctypes.c_int32),
                 ("mlp_hidden_layers", ctypes.c_int32), ("mlp_width", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("init_range", ctypes.c_float), ("layout", ctypes.c_int32)]
+                ("init_range", ctypes.c_float), ("layout", ctypes.c_int32), ("masks", ctypes.c_void_p),
+                ("n_masks", ctypes.c_int32)]
 
 
 class fhash_info(ctypes.Structure):
@@ -77,7 +78,7 @@ class fhash_request(ctypes.Structure):
 class fhash_server_stats(ctypes.Structure):
     _fields_ = [("ticks", ctypes.c_int64), ("samples", ctypes.c_int64), ("model_launches", ctypes.c_int64),
                 ("live", ctypes.c_int64), ("queued", ctypes.c_int64), ("pool_bytes", ctypes.c_uint64),
-                ("pool_used", ctypes.c_uint64)]
+                ("pool_used", ctypes.c_uint64), ("packed_launches", ctypes.c_int64)]
 
 
 class fhash_adam_stats(ctypes.Structure):
@@ -233,15 +234,26 @@ def fhash_plan(fbb, nt, schedule=None, F=2, dtype=FP32, mlp_hidden_layers=2, mlp
 
 
 def fhash_build(nx, ny, nz, nt, mask=None, schedule=None, F=2, dtype=FP32, mlp_hidden_layers=2, mlp_width=64,
-                seed=0, init_range=1e-4, layout=LAYOUT_LINEAR, stream=None):
-    """fhash_build: mask is a host numpy uint8 array [nt][nz][ny][nx] or None."""
+                seed=0, init_range=1e-4, layout=LAYOUT_LINEAR, stream=None, masks=None):
+    """fhash_build: mask is a host numpy uint8 array [nt][nz][ny][nx] or None; masks, a list of such arrays
+    (several features, merged), replaces it."""
     d = fhash_build_desc()
     d.nx, d.ny, d.nz, d.nt = int(nx), int(ny), int(nz), int(nt)
+
+    def _mask(a):
+        a = np.ascontiguousarray(a, np.uint8)
+        if a.shape != (nt, nz, ny, nx):
+            raise ValueError("mask shape %s != (nt, nz, ny, nx)" % (a.shape,))
+        return a
     if mask is not None:
-        mask = np.ascontiguousarray(mask, np.uint8)
-        if mask.shape != (nt, nz, ny, nx):
-            raise ValueError("mask shape %s != (nt, nz, ny, nx)" % (mask.shape,))
+        mask = _mask(mask)
     d.mask = _ptr(mask)
+    keep = []
+    if masks is not None:
+        keep = [_mask(a) for a in masks]
+        arr = (_vp * max(1, len(keep)))(*[a.ctypes.data for a in keep])
+        d.masks = ctypes.cast(arr, _vp)
+        d.n_masks = len(keep)
     d.sched = schedule if schedule is not None else make_schedule()
     d.F, d.dtype = int(F), int(dtype)
     d.mlp_hidden_layers, d.mlp_width = int(mlp_hidden_layers), int(mlp_width)

@@ -110,9 +110,12 @@ fhash_status refresh_shadow(fhash_model* m, uint64_t off, uint64_t n, cudaStream
 }
 
 // ------------------------------------------------------------------ feature dilation + boxes
-// d(v) = OR of f over the 3x3x3 spatial neighbourhood of v, clipped at the border (Section 3.1).
-// Also folds the per-frame bounding box of d into box[6] = (minx, miny, minz, maxx, maxy, maxz).
-__global__ void k_dilate(const uint8_t* __restrict__ f, uint8_t* __restrict__ d, int nx, int ny, int nz, int* box) {
+// d(v) = OR of f over the 3x3x3 spatial neighbourhood of v, clipped at the border (Section 3.1); with
+// merge, d(v) |= that instead (the union of several features' dilated regions, whose occupancy grids
+// Section 3.1 merges for rendering).  Also folds the per-frame bounding box of this feature's dilated
+// region into box[6] = (minx, miny, minz, maxx, maxy, maxz).
+__global__ void k_dilate(const uint8_t* __restrict__ f, uint8_t* __restrict__ d, int nx, int ny, int nz, int* box,
+                         int merge) {
     __shared__ int sb[6];
     if (threadIdx.x < 6) sb[threadIdx.x] = (threadIdx.x < 3) ? INT32_MAX : -1;
     __syncthreads();
@@ -134,7 +137,7 @@ __global__ void k_dilate(const uint8_t* __restrict__ f, uint8_t* __restrict__ d,
                 }
             }
         }
-        d[i] = v;
+        d[i] = merge ? (uint8_t)(d[i] | v) : v;
         if (v) {
             atomicMin(&sb[0], x); atomicMin(&sb[1], y); atomicMin(&sb[2], z);
             atomicMax(&sb[3], x); atomicMax(&sb[4], y); atomicMax(&sb[5], z);
@@ -444,10 +447,16 @@ fhash_status fhash_build(const fhash_build_desc* d, fhash_stream stream, fhash_m
     if (d->layout == FHASH_LAYOUT_MASKED && d->dtype != FHASH_FP32)
         return set_error(FHASH_EINVAL, "FHASH_LAYOUT_MASKED takes dtype FHASH_FP32");
     const bool masked = d->layout == FHASH_LAYOUT_MASKED;
+    if (d->n_masks < 0 || d->n_masks > 64 || (d->n_masks > 0 && (!d->masks || d->mask)))
+        return set_error(FHASH_EINVAL, "n_masks must be 0..64; with n_masks > 0 give masks[] and leave mask NULL");
+    for (int k = 0; k < d->n_masks; ++k)
+        if (!d->masks[k]) return set_error(FHASH_EINVAL, "masks[%d] is NULL", k);
+    const int n_feat = d->n_masks > 0 ? d->n_masks : (d->mask ? 1 : 0);
 
     fhash_model* m = new fhash_model();
     m->desc = *d;
     m->desc.mask = nullptr;
+    m->desc.masks = nullptr;
     cudaGetDevice(&m->device);
     m->nt = d->nt;
     struct Guard {
@@ -465,7 +474,7 @@ fhash_status fhash_build(const fhash_build_desc* d, fhash_stream stream, fhash_m
         uint8_t*& p;
         ~DilGuard() { if (p) cudaFree(p); }
     } dil_guard{dil};
-    if (d->mask) {
+    if (n_feat > 0) {
         uint8_t* stage = nullptr;
         int* boxes = nullptr;
         FH_CUDA(cudaMalloc(&stage, n3));
@@ -476,11 +485,14 @@ fhash_status fhash_build(const fhash_build_desc* d, fhash_stream stream, fhash_m
         std::vector<int> hb(6 * nt);
         for (int64_t t = 0; t < nt; ++t) { hb[6 * t + 0] = hb[6 * t + 1] = hb[6 * t + 2] = INT32_MAX; hb[6 * t + 3] = hb[6 * t + 4] = hb[6 * t + 5] = -1; }
         cudaMemcpyAsync(boxes, hb.data(), sizeof(int) * 6 * nt, cudaMemcpyHostToDevice, st);
-        for (int64_t t = 0; t < nt && e == cudaSuccess; ++t) {
-            e = cudaMemcpyAsync(stage, d->mask + t * n3, n3, cudaMemcpyHostToDevice, st);
-            k_dilate<<<(unsigned)((n3 + 255) / 256), 256, 0, st>>>(stage, dil + t * n3, (int)nx, (int)ny, (int)nz, boxes + 6 * t);
-            if (e == cudaSuccess) e = cudaGetLastError();
-        }
+        for (int64_t t = 0; t < nt && e == cudaSuccess; ++t)
+            for (int k = 0; k < n_feat && e == cudaSuccess; ++k) {  // each feature dilated, then OR-merged
+                const uint8_t* src = d->n_masks > 0 ? d->masks[k] : d->mask;
+                e = cudaMemcpyAsync(stage, src + t * n3, n3, cudaMemcpyHostToDevice, st);
+                k_dilate<<<(unsigned)((n3 + 255) / 256), 256, 0, st>>>(stage, dil + t * n3, (int)nx, (int)ny, (int)nz,
+                                                                      boxes + 6 * t, k > 0);
+                if (e == cudaSuccess) e = cudaGetLastError();
+            }
         if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), boxes, sizeof(int) * 6 * nt, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         cudaFree(stage);

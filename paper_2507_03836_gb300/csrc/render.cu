@@ -20,175 +20,63 @@ namespace fh {
 
 cudaError_t run_fused_any(int F, int which, const FusedArgs& a);
 
-__device__ __forceinline__ bool occ_bit(const RenderGeo& g, int t, int x, int y, int z) {
-    int64_t b = ((int64_t)(z >> 3) * g.nby + (y >> 3)) * g.nbx + (x >> 3);
-    if (!g.occ_any[(int64_t)t * g.nbrick + b]) return false;
-    int lx = x & 7, ly = y & 7, lz = z & 7;
-    int mi = (lx & 1) | ((ly & 1) << 1) | ((lz & 1) << 2) | ((lx & 2) << 2) | ((ly & 2) << 3) | ((lz & 2) << 4) |
-             ((lx & 4) << 4) | ((ly & 4) << 5) | ((lz & 4) << 6);
-    return (g.occ[((int64_t)t * g.nbrick + b) * 16 + (mi >> 5)] >> (mi & 31)) & 1u;
-}
-
-// Occupancy of the sample at model coordinate u (nearest voxel), at t_norm.
-__device__ __forceinline__ bool sample_occupied(const RenderGeo& g, const float u[3]) {
-    int v[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        float q = __fmul_rn(u[a], (float)(g.S[a] - 1));
-        v[a] = (int)floorf(__fadd_rn(q, 0.5f));
-        if (v[a] < 0 || v[a] >= g.S[a]) return false;
-    }
-    if (occ_bit(g, g.tp, v[0], v[1], v[2])) return true;
-    return g.use_tn && occ_bit(g, g.tn, v[0], v[1], v[2]);
-}
-
 __global__ void k_ray_init(const __grid_constant__ RenderGeo g, RayState* __restrict__ rs, int* __restrict__ alive,
                            int* __restrict__ n_alive, float4* __restrict__ rgba, int* __restrict__ counts) {
-    int pix = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pix >= g.W * g.H) return;
-    int i = pix % g.W, j = pix / g.W;
-    float sx = __fsub_rn(__fdiv_rn((float)(2 * i + 1), (float)g.W), 1.0f);
-    float sy = __fsub_rn(1.0f, __fdiv_rn((float)(2 * j + 1), (float)g.H));
-    float d[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) d[a] = __fadd_rn(__fadd_rn(g.fwd[a], __fmul_rn(sx, g.right[a])), __fmul_rn(sy, g.up[a]));
-    float ln = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(d[0], d[0]), __fmul_rn(d[1], d[1])), __fmul_rn(d[2], d[2])));
-#pragma unroll
-    for (int a = 0; a < 3; ++a) d[a] = __fdiv_rn(d[a], ln);
-    float tn = -INFINITY, tf = INFINITY;
-    bool hit = true;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (d[a] != 0.0f) {
-            float t0 = __fdiv_rn(__fsub_rn(-1.0f, g.eye[a]), d[a]);
-            float t1 = __fdiv_rn(__fsub_rn(1.0f, g.eye[a]), d[a]);
-            tn = fmaxf(tn, fminf(t0, t1));
-            tf = fminf(tf, fmaxf(t0, t1));
-        } else if (g.eye[a] < -1.0f || g.eye[a] > 1.0f) {
-            hit = false;
-        }
-    }
-    float tmin = fmaxf(tn, 0.0f), tmax = tf;
-    hit = hit && (tmin <= tmax);
-    RayState s;
-    s.d[0] = d[0]; s.d[1] = d[1]; s.d[2] = d[2];
-    s.tmin = tmin; s.tmax = tmax; s.k = 0; s.flags = hit ? 0 : 1;
-    s.C[0] = s.C[1] = s.C[2] = 0.0f; s.T = 1.0f; s.count = 0;
-    rs[pix] = s;
-    if (hit) {
-        alive[atomicAdd(n_alive, 1)] = pix;
-    } else {
-        rgba[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (counts) counts[pix] = 0;
-    }
+    const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix < g.W * g.H) ray_init_px(g, pix, rs, alive, n_alive, rgba, counts);
 }
 
-// Index of the last sample that surely still lies in the empty 8^3 brick holding voxel v, for a ray
-// whose sample k is in it.  The brick holds the samples whose nearest voxel is in [8b, 8b + 7] on each
-// axis, that is model coordinate q = u (S - 1) in [8b - 0.5, 8b + 7.5); the ray parameter where q
-// reaches that box's far faces, pulled in by 0.01 voxel (far more than the float32 rounding of q and of
-// this bound, about 1e-4 voxel), limits the samples that can be skipped.  Samples never evaluated there
-// are unoccupied, so the set of samples (and the image) is the same as stepping through them one by one.
-// Float32 throughout: the FP64 rate of this GPU is a small fraction of its FP32 rate.
-__device__ __forceinline__ int empty_brick_last_sample(const RenderGeo& g, const RayState& s, const int v[3], int k) {
-    float t_exit = 3.0e38f;
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-        const float d = s.d[ax];
-        if (d == 0.0f) continue;
-        const int b8 = (v[ax] >> 3) * 8;
-        const float qf = d > 0.0f ? (float)b8 + 7.49f : (float)b8 - 0.49f;  // the face the ray runs to
-        const float uf = qf / (float)(g.S[ax] - 1);
-        t_exit = fminf(t_exit, ((2.0f * uf - 1.0f) - g.eye[ax]) / d);  // u = (eye + t d + 1) / 2
-    }
-    const float kl = floorf((t_exit - s.tmin) / g.delta);
-    return kl > (float)k ? (int)fminf(kl, (float)(1 << 24)) : k;
-}
-
-// Marches each alive ray on until it has up to Ns occupied samples (or leaves the box); writes their
-// model coordinates to slots [a*Ns, a*Ns + cnt).  A sample in an 8^3 brick that is empty at both time
-// steps in use jumps the ray to the last sample inside that brick (empty-space skipping).
 __global__ void k_arm_generate(const __grid_constant__ RenderGeo g, RayState* __restrict__ rs,
                                const int* __restrict__ alive, int na, int ns, float4* __restrict__ coords,
                                int* __restrict__ cnt, unsigned long long* __restrict__ marched) {
-    int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= na) return;
-    int pix = alive[a];
-    RayState s = rs[pix];
-    int c = 0, k = s.k;
-    long long steps = 0;
-    while (c < ns) {
-        if (k >= (1 << 24)) { s.flags |= 1; break; }
-        float sk = __fadd_rn(s.tmin, __fmul_rn((float)k, g.delta));
-        if (!(sk <= s.tmax)) { s.flags |= 1; break; }
-        float u[3];
-#pragma unroll
-        for (int ax = 0; ax < 3; ++ax) u[ax] = __fmul_rn(__fadd_rn(__fadd_rn(g.eye[ax], __fmul_rn(sk, s.d[ax])), 1.0f), 0.5f);
-        ++steps;
-        int v[3];
-        bool inside = true;
-#pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-            v[ax] = (int)floorf(__fadd_rn(__fmul_rn(u[ax], (float)(g.S[ax] - 1)), 0.5f));
-            inside = inside && v[ax] >= 0 && v[ax] < g.S[ax];
-        }
-        if (!inside) { ++k; continue; }
-        const int64_t b = ((int64_t)(v[2] >> 3) * g.nby + (v[1] >> 3)) * g.nbx + (v[0] >> 3);
-        const bool any_p = g.occ_any[(int64_t)g.tp * g.nbrick + b] != 0;
-        const bool any_n = g.use_tn && g.occ_any[(int64_t)g.tn * g.nbrick + b] != 0;
-        if (!any_p && !any_n) {
-            k = empty_brick_last_sample(g, s, v, k) + 1;  // samples up to the returned one are empty
-            continue;
-        }
-        ++k;
-        if ((any_p && occ_bit(g, g.tp, v[0], v[1], v[2])) || (any_n && occ_bit(g, g.tn, v[0], v[1], v[2])))
-            coords[(int64_t)a * ns + c++] = make_float4(u[0], u[1], u[2], g.t_norm);
-    }
-    rs[pix].k = k;
-    rs[pix].flags = s.flags;
-    cnt[a] = c;
-    if (marched) atomicAdd(marched, (unsigned long long)steps);
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < na) arm_generate_ray(g, rs, alive[a], a, ns, coords, cnt, marched);
 }
 
-// Transfer function lookup (256 RGBA entries, linear interpolation) and front-to-back compositing;
-// rays that are done write their pixel, the others are appended to the next alive list.
 __global__ void k_arm_composite(const __grid_constant__ RenderGeo g, RayState* __restrict__ rs,
                                 const int* __restrict__ alive, int na, int ns, const int* __restrict__ cnt,
                                 const float* __restrict__ vals, const float4* __restrict__ tf,
                                 int* __restrict__ next, int* __restrict__ n_next, float4* __restrict__ rgba,
                                 int* __restrict__ counts, unsigned long long* __restrict__ used) {
-    int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= na) return;
-    int pix = alive[a];
-    RayState s = rs[pix];
-    int c = cnt[a];
-    bool opaque = false;
-    int u = 0;
-    for (int j = 0; j < c && !opaque; ++j) {
-        float v = vals[(int64_t)a * ns + j];
-        float x = fminf(fmaxf(v, 0.0f), 1.0f) * 255.0f;
-        int i0 = min((int)floorf(x), 254);
-        float f = x - (float)i0;
-        float4 p = __ldg(tf + i0), q = __ldg(tf + i0 + 1);
-        float r = p.x + f * (q.x - p.x), gg = p.y + f * (q.y - p.y), b = p.z + f * (q.z - p.z), al = p.w + f * (q.w - p.w);
-        float w = s.T * al;
-        s.C[0] += w * r; s.C[1] += w * gg; s.C[2] += w * b;
-        s.T *= (1.0f - al);
-        ++u;
-        if (1.0f - s.T > 0.99f) opaque = true;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < na) arm_composite_ray(g, rs, alive[a], a, ns, cnt, vals, tf, next, n_next, rgba, counts, used);
+}
+
+// The same round with its sizes read on the device, so that fhash_render issues rounds without waiting
+// for the alive count: N_a = *n_alive, N_s = max(min(N_r / N_a, pace), 1) (Algorithm 1); thread 0
+// publishes N_s and the round's sample count {0, N_a N_s} (the segment the persistent encode+MLP launch
+// reads), clears the next list's counter and counts the round.  A round issued after the last ray left
+// (N_a = 0) does nothing.
+__global__ void k_arm_generate_dev(const __grid_constant__ RenderGeo g, RayState* __restrict__ rs,
+                                   const int* __restrict__ alive, const int* __restrict__ n_alive, int max_pace,
+                                   int* __restrict__ ns_out, int64_t* __restrict__ seg, int* __restrict__ n_next,
+                                   int* __restrict__ rounds, float4* __restrict__ coords, int* __restrict__ cnt,
+                                   unsigned long long* __restrict__ acc) {
+    const int na = *n_alive;
+    const int64_t NR = (int64_t)g.W * g.H;
+    const int ns = (int)max((int64_t)1, min(na > 0 ? NR / na : (int64_t)1, (int64_t)max_pace));
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a == 0) {
+        *ns_out = ns;
+        seg[0] = 0;
+        seg[1] = (int64_t)na * ns;
+        *n_next = 0;
+        if (na > 0) {
+            *rounds += 1;
+            if (acc) acc[2] += (unsigned long long)na * ns;
+        }
     }
-    s.count += u;
-    if (used) atomicAdd(used, (unsigned long long)u);
-    if (opaque || (s.flags & 1)) {
-        rgba[pix] = make_float4(s.C[0], s.C[1], s.C[2], 1.0f - s.T);
-        if (counts) counts[pix] = s.count;
-        rs[pix].flags = s.flags | 2;
-    } else {
-        next[atomicAdd(n_next, 1)] = pix;
-    }
-    rs[pix].C[0] = s.C[0]; rs[pix].C[1] = s.C[1]; rs[pix].C[2] = s.C[2];
-    rs[pix].T = s.T;
-    rs[pix].count = s.count;
+    if (a < na) arm_generate_ray(g, rs, alive[a], a, ns, coords, cnt, acc);
+}
+
+__global__ void k_arm_composite_dev(const __grid_constant__ RenderGeo g, RayState* __restrict__ rs,
+                                    const int* __restrict__ alive, const int* __restrict__ n_alive,
+                                    const int* __restrict__ ns_in, const int* __restrict__ cnt,
+                                    const float* __restrict__ vals, const float4* __restrict__ tf,
+                                    int* __restrict__ next, int* __restrict__ n_next, float4* __restrict__ rgba,
+                                    int* __restrict__ counts, unsigned long long* __restrict__ used) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < *n_alive) arm_composite_ray(g, rs, alive[a], a, *ns_in, cnt, vals, tf, next, n_next, rgba, counts, used);
 }
 
 RenderGeo make_geo(const fhash_model* m, const fhash_camera* cam, float t_norm, int w, int h) {
@@ -339,40 +227,43 @@ fhash_status fhash_render(fhash_model* m, const fhash_camera* cam, float t_norm,
     int* cnt = (int*)(b + o_cnt);
     float4* co = (float4*)(b + o_co);
     float* val = (float*)(b + o_val);
-    int* ctr = (int*)(b + o_ctr);                                     // [0], [1]: alive counters
-    unsigned long long* acc = (unsigned long long*)(b + o_ctr + 16);  // marched, used
+    int* ctr = (int*)(b + o_ctr);  // [0], [1]: alive counters; [2]: the round's N_s; [3]: rounds with rays
+    int64_t* seg = (int64_t*)(b + o_ctr + 16);                         // the round's {offset, count}
+    unsigned long long* acc = (unsigned long long*)(b + o_ctr + 32);  // marched, used, evaluated
     FH_CUDA(cudaMemsetAsync(ctr, 0, 64, st));
-    k_ray_init<<<(unsigned)((NR + 255) / 256), 256, 0, st>>>(g, rs, al[0], ctr, (float4*)rgba, counts);
+    const unsigned gr = (unsigned)((NR + 127) / 128);
+    k_ray_init<<<gr, 128, 0, st>>>(g, rs, al[0], ctr, (float4*)rgba, counts);
     FH_CUDA(cudaGetLastError());
-    int na = 0;
-    FH_CUDA(cudaMemcpyAsync(&na, ctr, 4, cudaMemcpyDeviceToHost, st));
-    FH_CUDA(cudaStreamSynchronize(st));
-    int64_t rounds = 0, slots = 0;
-    int cur = 0;
-    while (na > 0) {
-        if (rounds > (1 << 24)) return set_error(FHASH_ETIMEOUT, "fhash_render: round limit exceeded");
-        int ns = (int)std::max<int64_t>(1, std::min<int64_t>(NR / na, max_pace));
-        k_arm_generate<<<(na + 127) / 128, 128, 0, st>>>(g, rs, al[cur], na, ns, co, cnt, stats ? acc : nullptr);
-        FH_CUDA(cudaGetLastError());
-        const int64_t nslots = (int64_t)na * ns;
-        FH_TRY(launch_forward(m, (const float*)co, nslots, val, st));
-        FH_CUDA(cudaMemsetAsync(ctr + 1 - cur, 0, 4, st));
-        k_arm_composite<<<(na + 127) / 128, 128, 0, st>>>(g, rs, al[cur], na, ns, cnt, val, (const float4*)tf,
-                                                          al[1 - cur], ctr + 1 - cur, (float4*)rgba, counts,
-                                                          stats ? acc + 1 : nullptr);
-        FH_CUDA(cudaGetLastError());
-        FH_CUDA(cudaMemcpyAsync(&na, ctr + 1 - cur, 4, cudaMemcpyDeviceToHost, st));
+    // Rounds are issued in batches of 1, 2, 4, ... 64 with no host wait inside a batch: every launch reads
+    // the alive count from device memory.  After a batch the host reads the count once; a round issued
+    // after the last ray has left does nothing.
+    int cur = 0, na = 1;
+    int64_t issued = 0;
+    for (int batch = 1; na > 0; batch = std::min(2 * batch, 64)) {
+        if (issued > (1 << 24)) return set_error(FHASH_ETIMEOUT, "fhash_render: round limit exceeded");
+        for (int r = 0; r < batch; ++r) {
+            k_arm_generate_dev<<<gr, 128, 0, st>>>(g, rs, al[cur], ctr + cur, max_pace, ctr + 2, seg, ctr + 1 - cur,
+                                                   ctr + 3, co, cnt, stats ? acc : nullptr);
+            FH_CUDA(cudaGetLastError());
+            FH_TRY(launch_forward_seg(m, (const float*)co, val, seg, NR, st));
+            k_arm_composite_dev<<<gr, 128, 0, st>>>(g, rs, al[cur], ctr + cur, ctr + 2, cnt, val, (const float4*)tf,
+                                                    al[1 - cur], ctr + 1 - cur, (float4*)rgba, counts,
+                                                    stats ? acc + 1 : nullptr);
+            FH_CUDA(cudaGetLastError());
+            cur = 1 - cur;
+        }
+        issued += batch;
+        FH_CUDA(cudaMemcpyAsync(&na, ctr + cur, 4, cudaMemcpyDeviceToHost, st));
         FH_CUDA(cudaStreamSynchronize(st));
-        cur = 1 - cur;
-        ++rounds;
-        slots += nslots;
     }
     if (stats) {
-        unsigned long long h2[2];
-        FH_CUDA(cudaMemcpyAsync(h2, acc, 16, cudaMemcpyDeviceToHost, st));
+        unsigned long long h2[3];
+        int hr[4];
+        FH_CUDA(cudaMemcpyAsync(h2, acc, 24, cudaMemcpyDeviceToHost, st));
+        FH_CUDA(cudaMemcpyAsync(hr, ctr, 16, cudaMemcpyDeviceToHost, st));
         FH_CUDA(cudaStreamSynchronize(st));
-        stats->rounds = rounds;
-        stats->samples_evaluated = slots;
+        stats->rounds = hr[3];
+        stats->samples_evaluated = (int64_t)h2[2];
         stats->samples_composited = (int64_t)h2[1];
         stats->steps_marched = (int64_t)h2[0];
     }

