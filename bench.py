@@ -778,7 +778,9 @@ def main():
 
     # batches: coords uniform in [0,1]^4 (FBB-normalised), targets sampled from the field
     B = w["batch"]
-    nb = args.warmup + args.steps
+    # fresh batches for every loop below (warm-up, timed, phase breakdown, end to end): a batch seen a few
+    # steps earlier would find its table groups almost current and understate the deferred Adam's replay
+    nb = args.warmup + 3 * args.steps + 2
     coords_h = [synth.coords(10_000 + 100 * rank + k, B) for k in range(nb)]
     tgt_h = [synth.sample(field, info["fbb_lo"], info["fbb_size"], c) for c in coords_h]
     coords_d = [torch.from_numpy(c).cuda() for c in coords_h]
@@ -826,7 +828,7 @@ def main():
     fh.fhash_set_timing(model, True)
     ph, groups, gsteps = [], [], []
     for k in range(K):
-        i = args.warmup + k
+        i = args.warmup + K + k
         fh.fhash_train_step(model, coords_d[i], tgt_d[i], hp)
         a = fh.fhash_get_adam_stats(model)
         ph.append(a["last_ms"])
@@ -845,10 +847,11 @@ def main():
     touched = _touched_fraction(fh, model, info, coords_d[args.warmup], tgt_d[args.warmup], hp, n_deferred)
 
     # end to end through the public API: host (pinned) inputs copied in, loss read back, every step
-    pin_c = [torch.from_numpy(c).pin_memory() for c in coords_h[:K]]
-    pin_t = [torch.from_numpy(t).pin_memory() for t in tgt_h[:K]]
+    e0 = args.warmup + 2 * K
+    pin_c = [torch.from_numpy(c).pin_memory() for c in coords_h[e0:e0 + K + 2]]
+    pin_t = [torch.from_numpy(t).pin_memory() for t in tgt_h[e0:e0 + K + 2]]
     lh = np.zeros(1, np.float64)
-    for k in range(min(2, K)):
+    for k in range(K, K + 2):  # warm-up of the host-input path (its staging buffers) on two more batches
         fh.fhash_train_step(model, pin_c[k].numpy(), pin_t[k].numpy(), hp, lh)
     torch.cuda.synchronize()
     if dist:

@@ -282,10 +282,10 @@ fhash_status fhash_compute_grads(fhash_model* model, const float* coords, const 
                                  double* loss, fhash_stream stream);
 
 /* One Adam step (Section 5.1.3) over every parameter using the gradient buffer, which it then
- * clears to zero; increments the step count.  Every operation is rounded to nearest in float32 with no
- * fused multiply-add: m = b1 m + (1 - b1) g (one fma), v = b2 v + (1 - b2) g^2 (one fma),
- * p -= (lr / bc1) * (m / (sqrt(v) / sqrt(bc2) + eps)), with lr / bc1 and sqrt(bc2) computed in double
- * from the step count and rounded to float32. */
+ * clears to zero; increments the step count.  In float32: m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+ * d = sqrt(v) * (1 / sqrt(bc2)) + eps, p = p - (lr / bc1) * (m / d), each line one rounded multiply and
+ * one fused multiply-add, with the GPU's approximate square root and division (a few ulp); lr / bc1,
+ * 1 / sqrt(bc2) and 1 - beta are computed in double from the step count and rounded to float32. */
 fhash_status fhash_apply_adam(fhash_model* model, const fhash_adam* adam, fhash_stream stream);
 
 /* One full training step: the result of fhash_compute_grads followed by fhash_apply_adam, bit for bit.

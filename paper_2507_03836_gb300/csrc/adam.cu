@@ -4,7 +4,7 @@
 // Dense: k_adam streams every parameter once per step (28 bytes per parameter; HBM-bound).
 //
 // Deferred: a step whose gradient is zero is a fixed float32 map of (p, m, v) that depends only on
-// that step's scalars (beta1, beta2, lr / bc1, sqrt(bc2), eps).  For the table levels whose rows a
+// that step's scalars (beta1, beta2, lr / bc1, 1 / sqrt(bc2), eps).  For the table levels whose rows a
 // batch rarely touches (the HBM-resident fine levels), that map is not applied every step: each
 // 8-float group keeps a stamp s, meaning "p, m, v are current at step s and the gradient buffer holds
 // the gradient of step s + 1".  Before the gathers of step k, every group the batch will read is
@@ -27,17 +27,36 @@
 
 namespace fh {
 
+// One step's scalars: beta1, 1 - beta1, beta2, 1 - beta2, -lr / bc1, 1 / sqrt(bc2) (bc = 1 - beta^k; both
+// computed in double and rounded once), eps.
 struct AdamScal {
-    float b1, b2, step_size, sqrt_bc2, eps, pad0, pad1, pad2;
+    float b1, omb1, b2, omb2, neg_step, inv_sqrt_bc2, eps, pad;
 };
 
-// One Adam step of one parameter, every operation rounded to nearest with no contraction, so the same
-// call gives the same bits wherever it is compiled (the dense kernel, the replay, the flush).
+// The GPU's approximate square root and division (one special-function instruction each, relative error
+// of a few ulp), in place of the correctly rounded sequences, which cost several times more issue slots
+// and left Adam's arithmetic, not its memory traffic, as the limit of the replay.  Deterministic: the same
+// inputs give the same bits in every kernel.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float div_approx(float x, float y) {
+    float q;
+    asm("div.approx.f32 %0, %1, %2;" : "=f"(q) : "f"(x), "f"(y));
+    return q;
+}
+
+// One Adam step of one parameter:
+//   m = b1 m + (1 - b1) g;  v = b2 v + (1 - b2) g^2;  p = p - (lr / bc1) m / (sqrt(v) / sqrt(bc2) + eps),
+// every multiply-add rounded to nearest with no further contraction, so the same call gives the same bits
+// wherever it is compiled (the dense kernel, the replay, the flush).
 __device__ __forceinline__ void adam1(float& p, float g, float& m, float& v, const AdamScal& s) {
-    m = __fmaf_rn(s.b1, m, __fmul_rn(__fsub_rn(1.0f, s.b1), g));
-    v = __fmaf_rn(s.b2, v, __fmul_rn(__fsub_rn(1.0f, s.b2), __fmul_rn(g, g)));
-    const float denom = __fadd_rn(__fdiv_rn(__fsqrt_rn(v), s.sqrt_bc2), s.eps);
-    p = __fsub_rn(p, __fmul_rn(s.step_size, __fdiv_rn(m, denom)));
+    m = __fmaf_rn(s.b1, m, __fmul_rn(s.omb1, g));
+    v = __fmaf_rn(s.b2, v, __fmul_rn(s.omb2, __fmul_rn(g, g)));
+    const float denom = __fmaf_rn(sqrt_approx(v), s.inv_sqrt_bc2, s.eps);
+    p = __fmaf_rn(s.neg_step, div_approx(m, denom), p);
 }
 
 __device__ __forceinline__ void adam4(float4& p, const float4& g, float4& m, float4& v, const AdamScal& s) {
@@ -244,7 +263,8 @@ __device__ __forceinline__ void replay_group(float* __restrict__ P, float* __res
         adam4(p0, g0, m0, v0, s);
         adam4(p1, g1, m1, v1, s);
     }
-    for (uint32_t j = from + 2; j <= to; ++j) {
+#pragma unroll 1
+    for (uint32_t j = from + 2; j <= to; ++j) {  // eight independent chains per iteration
         const AdamScal s = tab[j];
         adam4(p0, z, m0, v0, s);
         adam4(p1, z, m1, v1, s);
@@ -266,7 +286,7 @@ __device__ __forceinline__ void replay_group(float* __restrict__ P, float* __res
 
 // The claimed groups in bucket order, one per thread (a persistent grid walks the list).
 template <bool SHADOW>
-__global__ void __launch_bounds__(256) k_defer_replay(const uint2* __restrict__ binned, const DeferCtr* __restrict__ ctr,
+__global__ void __launch_bounds__(256, 3) k_defer_replay(const uint2* __restrict__ binned, const DeferCtr* __restrict__ ctr,
                                                       float* __restrict__ P, float* __restrict__ G, float* __restrict__ M,
                                                       float* __restrict__ V, __nv_bfloat16* __restrict__ shadow,
                                                       uint64_t f0, const AdamScal* __restrict__ tab, uint32_t target) {
@@ -279,7 +299,7 @@ __global__ void __launch_bounds__(256) k_defer_replay(const uint2* __restrict__ 
 
 // Every deferred group brought to step k (before anything outside the training step reads the state).
 template <bool SHADOW>
-__global__ void __launch_bounds__(256) k_defer_flush(const uint32_t* __restrict__ stamp, uint64_t ngroups,
+__global__ void __launch_bounds__(256, 3) k_defer_flush(const uint32_t* __restrict__ stamp, uint64_t ngroups,
                                                      float* __restrict__ P, float* __restrict__ G, float* __restrict__ M,
                                                      float* __restrict__ V, __nv_bfloat16* __restrict__ shadow,
                                                      uint64_t f0, const AdamScal* __restrict__ tab, uint32_t clean,
@@ -296,9 +316,11 @@ static AdamScal scalars(const fhash_adam* ad, int64_t step) {
     const double bc1 = 1.0 - pow((double)ad->beta1, k), bc2 = 1.0 - pow((double)ad->beta2, k);
     AdamScal s{};
     s.b1 = ad->beta1;
+    s.omb1 = (float)(1.0 - (double)ad->beta1);
     s.b2 = ad->beta2;
-    s.step_size = (float)(ad->lr / bc1);
-    s.sqrt_bc2 = (float)sqrt(bc2);
+    s.omb2 = (float)(1.0 - (double)ad->beta2);
+    s.neg_step = (float)(-(double)ad->lr / bc1);
+    s.inv_sqrt_bc2 = (float)(1.0 / sqrt(bc2));
     s.eps = ad->eps;
     return s;
 }
@@ -432,7 +454,7 @@ static fhash_status catch_up(fhash_model* m, const float* coords, int64_t n, cud
     k_defer_bin<<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(items, binned, ctr, target);
     FH_CUDA(cudaGetLastError());
     tev_record(m, TEV_CLAIM, st);
-    const unsigned rg = (unsigned)num_sms() * 8;
+    const unsigned rg = (unsigned)num_sms() * 3;  // resident blocks (three per SM at this register use)
     const AdamScal* tab = (const AdamScal*)m->adam_tab;
     if (m->shadow)
         k_defer_replay<true><<<rg, 256, 0, st>>>(binned, ctr, m->param, m->grad, m->adam_m, m->adam_v, m->shadow,
