@@ -841,11 +841,6 @@ def main():
     replay_groups, replay_steps = float(np.mean(groups)), float(np.mean(gsteps))
     n_deferred = int(adam_stats["deferred_params"])
 
-    # fraction of 4-parameter groups with a non-zero gradient after one step in the densely updated range
-    # (untimed): k_adam writes the cleared gradient back only there, so its algorithmic bytes are
-    # 28 B/param + 4 B x that fraction
-    touched = _touched_fraction(fh, model, info, coords_d[args.warmup], tgt_d[args.warmup], hp, n_deferred)
-
     # end to end through the public API: host (pinned) inputs copied in, loss read back, every step
     e0 = args.warmup + 2 * K
     pin_c = [torch.from_numpy(c).pin_memory() for c in coords_h[e0:e0 + K + 2]]
@@ -862,6 +857,12 @@ def main():
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(dist, time.perf_counter() - t1)
     fh.fhash_check(model)
+
+    # fraction of 4-parameter groups with a non-zero gradient after one step in the densely updated range
+    # (untimed, after every timed loop: reading the gradient brings every deferred group up to date, which
+    # would shorten the replays of the steps after it): k_adam writes the cleared gradient back only
+    # there, so its algorithmic bytes are 28 B/param + 4 B x that fraction
+    touched = _touched_fraction(fh, model, info, coords_d[args.warmup], tgt_d[args.warmup], hp, n_deferred)
 
     prec = None
     if not args.no_serve:

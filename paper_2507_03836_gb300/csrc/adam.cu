@@ -37,14 +37,16 @@ struct AdamScal {
 // of a few ulp), in place of the correctly rounded sequences, which cost several times more issue slots
 // and left Adam's arithmetic, not its memory traffic, as the limit of the replay.  Deterministic: the same
 // inputs give the same bits in every kernel.
+// Subnormal inputs are flushed to zero here: a subnormal v gives sqrt(v) below 1e-19, far under eps, and a
+// subnormal m an update below 1e-30 lr; either way the step is unchanged at float32 precision.
 __device__ __forceinline__ float sqrt_approx(float x) {
     float y;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 __device__ __forceinline__ float div_approx(float x, float y) {
     float q;
-    asm("div.approx.f32 %0, %1, %2;" : "=f"(q) : "f"(x), "f"(y));
+    asm("div.approx.ftz.f32 %0, %1, %2;" : "=f"(q) : "f"(x), "f"(y));
     return q;
 }
 
@@ -57,6 +59,23 @@ __device__ __forceinline__ void adam1(float& p, float g, float& m, float& v, con
     v = __fmaf_rn(s.b2, v, __fmul_rn(s.omb2, __fmul_rn(g, g)));
     const float denom = __fmaf_rn(sqrt_approx(v), s.inv_sqrt_bc2, s.eps);
     p = __fmaf_rn(s.neg_step, div_approx(m, denom), p);
+}
+
+// adam1 with g = +0, bit for bit: (1 - beta) is positive and finite, so (1 - beta) * (+0) and
+// (1 - beta) * (+0)^2 are +0 and the fused multiply-adds receive the same +0 addend.  Saves the two
+// multiplies by the zero gradient in the replay of steps without a gradient.
+__device__ __forceinline__ void adam1_zero(float& p, float& m, float& v, const AdamScal& s) {
+    m = __fmaf_rn(s.b1, m, 0.0f);
+    v = __fmaf_rn(s.b2, v, 0.0f);
+    const float denom = __fmaf_rn(sqrt_approx(v), s.inv_sqrt_bc2, s.eps);
+    p = __fmaf_rn(s.neg_step, div_approx(m, denom), p);
+}
+
+__device__ __forceinline__ void adam4_zero(float4& p, float4& m, float4& v, const AdamScal& s) {
+    adam1_zero(p.x, m.x, v.x, s);
+    adam1_zero(p.y, m.y, v.y, s);
+    adam1_zero(p.z, m.z, v.z, s);
+    adam1_zero(p.w, m.w, v.w, s);
 }
 
 __device__ __forceinline__ void adam4(float4& p, const float4& g, float4& m, float4& v, const AdamScal& s) {
@@ -266,8 +285,8 @@ __device__ __forceinline__ void replay_group(float* __restrict__ P, float* __res
 #pragma unroll 1
     for (uint32_t j = from + 2; j <= to; ++j) {  // eight independent chains per iteration
         const AdamScal s = tab[j];
-        adam4(p0, z, m0, v0, s);
-        adam4(p1, z, m1, v1, s);
+        adam4_zero(p0, m0, v0, s);
+        adam4_zero(p1, m1, v1, s);
     }
     P4[0] = p0; P4[1] = p1;
     M4[0] = m0; M4[1] = m1;
