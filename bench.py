@@ -791,7 +791,6 @@ def main():
 
     if args.adam_deferral >= 0:
         fh.fhash_set_adam_deferral(model, args.adam_deferral)
-
     # aging (untimed): steps on fresh batches, so that the deferred Adam state (how many steps each table
     # group is behind when a batch reads it) has the distribution of a long training run, not of a
     # fresh model (a fresh model's first steps replay almost nothing)

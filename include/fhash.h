@@ -192,9 +192,8 @@ fhash_status fhash_build(const fhash_build_desc* desc, fhash_stream stream, fhas
  *  - *n_levels and res[0 .. *n_levels - 1] = (Rx, Ry, Rz, Rt), coarse -> fine (res may hold
  *    FHASH_MAX_LEVELS rows);
  *  - *table_rows = sum of Rx*Ry*Rz*Rt and *n_params = table_rows * F + the MLP's weights and biases;
- *  - *state_bytes = 4 bytes per parameter (the parameter) plus one 128-byte record per 8 parameters
- *    (gradient, two Adam moments, the deferred-Adam stamp), plus 2 more per parameter for the bf16
- *    shadow of FHASH_BF16.
+ *  - *state_bytes = 16 bytes per parameter (parameter, gradient, two Adam moments), plus 2 more for
+ *    the bf16 shadow of FHASH_BF16.
  * Any output pointer may be NULL.  Errors (FHASH_EINVAL) as fhash_build reports them for the same
  * arguments: bad schedule, F, dtype, MLP shape, L*F above 64, or a level too large to index.
  */

@@ -85,32 +85,31 @@ __device__ __forceinline__ void adam4(float4& p, const float4& g, float4& m, flo
     adam1(p.w, g.w, m.w, v.w, s);
 }
 
-// Dense update of n parameters from a flat index that is a multiple of 8 (P and R point at its parameter
-// and its record): one thread per 4 parameters, plus one per leftover parameter.  Streams p and the
-// records once: 16 bytes read + 12 written per parameter (+2 for the bf16 shadow); the gradient is
-// cleared by writing zeros only where it is not zero already (a step's scatter touches few table rows,
-// and untouched sectors then cost no DRAM write).  With tab != nullptr the step's scalars are recorded at
+// Dense update of n parameters (one thread per float4, plus one per leftover parameter): streams p, g,
+// m, v once, 16 bytes read + 12 written per parameter (+2 for the bf16 shadow); the gradient is cleared
+// by writing zeros only where it is not zero already (a step's scatter touches few table rows, and
+// untouched sectors then cost no DRAM write).  With tab != nullptr the step's scalars are recorded at
 // tab[k] for later replays.
 template <bool SHADOW>
-__global__ void __launch_bounds__(256) k_adam(float* __restrict__ P, float* __restrict__ R, uint64_t n, const AdamScal s,
+__global__ void __launch_bounds__(256) k_adam(float* __restrict__ P, float* __restrict__ G, float* __restrict__ M,
+                                              float* __restrict__ V, uint64_t n, const AdamScal s,
                                               __nv_bfloat16* __restrict__ shadow, AdamScal* __restrict__ tab,
                                               int64_t k) {
     if (tab && blockIdx.x == 0 && threadIdx.x == 0) tab[k] = s;
     const uint64_t n4 = n / 4;
     const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (i < n4) {
-        float4* P4 = reinterpret_cast<float4*>(P) + i;
-        float* r = R + (i >> 1) * kRecWords + 4 * (i & 1);  // this thread's half of a record's fields
-        float4* M4 = reinterpret_cast<float4*>(r);
-        float4* V4 = reinterpret_cast<float4*>(r + 8);
-        float4* G4 = reinterpret_cast<float4*>(r + 16);
-        float4 p = __ldcs(P4), g = __ldcs(G4), m = __ldcs(M4), v = __ldcs(V4);
+        float4* P4 = reinterpret_cast<float4*>(P);
+        float4* G4 = reinterpret_cast<float4*>(G);
+        float4* M4 = reinterpret_cast<float4*>(M);
+        float4* V4 = reinterpret_cast<float4*>(V);
+        float4 p = __ldcs(P4 + i), g = __ldcs(G4 + i), m = __ldcs(M4 + i), v = __ldcs(V4 + i);
         const bool touched = (g.x != 0.0f) | (g.y != 0.0f) | (g.z != 0.0f) | (g.w != 0.0f);
         adam4(p, g, m, v, s);
-        __stcs(P4, p);
-        if (touched) __stcs(G4, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
-        __stcs(M4, m);
-        __stcs(V4, v);
+        __stcs(P4 + i, p);
+        if (touched) __stcs(G4 + i, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+        __stcs(M4 + i, m);
+        __stcs(V4 + i, v);
         if (SHADOW) {
             __nv_bfloat162* s2 = reinterpret_cast<__nv_bfloat162*>(shadow) + 2 * i;
             s2[0] = __floats2bfloat162_rn(p.x, p.y);
@@ -118,10 +117,10 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ P, float* __re
         }
     } else if (i - n4 < n - 4 * n4) {
         const uint64_t e = 4 * n4 + (i - n4);
-        float p = P[e], m = *rec_m(R, e), v = *rec_v(R, e);
-        adam1(p, *rec_g(R, e), m, v, s);
-        P[e] = p; *rec_m(R, e) = m; *rec_v(R, e) = v;
-        *rec_g(R, e) = 0.0f;
+        float p = P[e], m = M[e], v = V[e];
+        adam1(p, G[e], m, v, s);
+        P[e] = p; M[e] = m; V[e] = v;
+        G[e] = 0.0f;
         if (SHADOW) shadow[e] = __float2bfloat16_rn(p);
     }
 }
@@ -146,7 +145,7 @@ __device__ __forceinline__ uint32_t len_bucket(uint32_t len) {
 }
 
 struct DeferArgs {
-    float* rec;          // the model's state records (the stamp of group q is rec_stamp(rec, q))
+    uint32_t* stamp;     // per group of the deferred range
     uint64_t q0, q1;     // deferred groups [q0, q1) (group q = floats 8q .. 8q + 7 of the flat vector)
     uint32_t target;     // k - 1: the step every read group must reach
     uint32_t clean;      // every group is at least this current
@@ -187,7 +186,7 @@ __global__ void __launch_bounds__(256) k_defer_claim(const __grid_constant__ Lev
             const uint64_t g = (r * (uint64_t)F) >> 3;
             if (g == prev || g < d.q0 || g >= d.q1) continue;
             prev = g;
-            const uint32_t old = atomicMax(rec_stamp(d.rec, g), d.target);
+            const uint32_t old = atomicMax(d.stamp + (g - d.q0), d.target);
             if (old < d.target) {
                 const uint32_t from = max(old, d.clean);
                 if (from < d.target) {
@@ -264,29 +263,20 @@ __global__ void __launch_bounds__(256) k_defer_bin(const uint2* __restrict__ ite
     if (have) binned[off[b] + base[b] + r] = it;
 }
 
-// 16-byte load that does not allocate in L1: the groups are read once, and L1 is left to the per-step
-// scalar table that every replay iteration reads.
-__device__ __forceinline__ float4 ld_na(const float4* p) {
-    float4 v;
-    asm volatile("ld.global.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "l"(p));
-    return v;
-}
-
-// Replays steps from + 1 .. to of the group of parameters 8q .. 8q + 7: the first with the pending
-// gradient, the rest with a zero gradient; clears the gradient (where it is not zero already) and refreshes
-// the bf16 shadow.  One random 32-byte sector of parameters and one 128-byte record each way.
+// Replays steps from + 1 .. to of the 8-float group starting at float index f: the first with the
+// pending gradient, the rest with a zero gradient; clears the gradient (where it is not zero already)
+// and refreshes the bf16 shadow.
 template <bool SHADOW>
-__device__ __forceinline__ void replay_group(float* __restrict__ P, float* __restrict__ R,
-                                             __nv_bfloat16* __restrict__ shadow, uint64_t q, uint32_t from,
-                                             uint32_t to, const AdamScal* __restrict__ tab) {
-    float4* P4 = reinterpret_cast<float4*>(P + 8 * q);
-    float4* M4 = reinterpret_cast<float4*>(R + q * kRecWords);
-    float4* V4 = M4 + 2;
-    float4* G4 = M4 + 4;
-    float4 p0 = ld_na(P4), p1 = ld_na(P4 + 1), m0 = ld_na(M4), m1 = ld_na(M4 + 1), v0 = ld_na(V4), v1 = ld_na(V4 + 1);
-    const float4 g0 = ld_na(G4), g1 = ld_na(G4 + 1);
+__device__ __forceinline__ void replay_group(float* __restrict__ P, float* __restrict__ G, float* __restrict__ M,
+                                             float* __restrict__ V, __nv_bfloat16* __restrict__ shadow, uint64_t f,
+                                             uint32_t from, uint32_t to, const AdamScal* __restrict__ tab) {
+    float4* P4 = reinterpret_cast<float4*>(P + f);
+    float4* G4 = reinterpret_cast<float4*>(G + f);
+    float4* M4 = reinterpret_cast<float4*>(M + f);
+    float4* V4 = reinterpret_cast<float4*>(V + f);
+    float4 p0 = P4[0], p1 = P4[1], m0 = M4[0], m1 = M4[1], v0 = V4[0], v1 = V4[1];
+    const float4 g0 = G4[0], g1 = G4[1];
+    const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     {
         const AdamScal s = tab[from + 1];
         adam4(p0, g0, m0, v0, s);
@@ -301,12 +291,11 @@ __device__ __forceinline__ void replay_group(float* __restrict__ P, float* __res
     P4[0] = p0; P4[1] = p1;
     M4[0] = m0; M4[1] = m1;
     V4[0] = v0; V4[1] = v1;
-    const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     const bool touched = (g0.x != 0.0f) | (g0.y != 0.0f) | (g0.z != 0.0f) | (g0.w != 0.0f) | (g1.x != 0.0f) |
                          (g1.y != 0.0f) | (g1.z != 0.0f) | (g1.w != 0.0f);
     if (touched) { G4[0] = z; G4[1] = z; }
     if (SHADOW) {
-        __nv_bfloat162* s2 = reinterpret_cast<__nv_bfloat162*>(shadow + 8 * q);
+        __nv_bfloat162* s2 = reinterpret_cast<__nv_bfloat162*>(shadow + f);
         s2[0] = __floats2bfloat162_rn(p0.x, p0.y);
         s2[1] = __floats2bfloat162_rn(p0.z, p0.w);
         s2[2] = __floats2bfloat162_rn(p1.x, p1.y);
@@ -317,24 +306,26 @@ __device__ __forceinline__ void replay_group(float* __restrict__ P, float* __res
 // The claimed groups in bucket order, one per thread (a persistent grid walks the list).
 template <bool SHADOW>
 __global__ void __launch_bounds__(256, 3) k_defer_replay(const uint2* __restrict__ binned, const DeferCtr* __restrict__ ctr,
-                                                         float* __restrict__ P, float* __restrict__ R,
-                                                         __nv_bfloat16* __restrict__ shadow, uint64_t q0,
-                                                         const AdamScal* __restrict__ tab, uint32_t target) {
+                                                      float* __restrict__ P, float* __restrict__ G, float* __restrict__ M,
+                                                      float* __restrict__ V, __nv_bfloat16* __restrict__ shadow,
+                                                      uint64_t f0, const AdamScal* __restrict__ tab, uint32_t target) {
     const uint32_t n = ctr->count;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint2 it = binned[i];
-        replay_group<SHADOW>(P, R, shadow, q0 + it.x, it.y, target, tab);
+        replay_group<SHADOW>(P, G, M, V, shadow, f0 + 8ull * it.x, it.y, target, tab);
     }
 }
 
 // Every deferred group brought to step k (before anything outside the training step reads the state).
 template <bool SHADOW>
-__global__ void __launch_bounds__(256, 3) k_defer_flush(float* __restrict__ P, float* __restrict__ R,
-                                                        __nv_bfloat16* __restrict__ shadow, uint64_t q0, uint64_t q1,
-                                                        const AdamScal* __restrict__ tab, uint32_t clean, uint32_t k) {
-    for (uint64_t q = q0 + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < q1; q += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t from = max(*rec_stamp(R, q), clean);
-        if (from < k) replay_group<SHADOW>(P, R, shadow, q, from, k, tab);
+__global__ void __launch_bounds__(256, 3) k_defer_flush(const uint32_t* __restrict__ stamp, uint64_t ngroups,
+                                                     float* __restrict__ P, float* __restrict__ G, float* __restrict__ M,
+                                                     float* __restrict__ V, __nv_bfloat16* __restrict__ shadow,
+                                                     uint64_t f0, const AdamScal* __restrict__ tab, uint32_t clean,
+                                                     uint32_t k) {
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < ngroups; q += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t from = max(stamp[q], clean);
+        if (from < k) replay_group<SHADOW>(P, G, M, V, shadow, f0 + 8ull * q, from, k, tab);
     }
 }
 
@@ -366,11 +357,12 @@ static cudaError_t dense_range(fhash_model* m, uint64_t off, uint64_t n, const A
     // GB300 at this size (every thread issues its four 16-byte loads at once)
     const uint64_t n4 = n / 4, threads = n4 + (n - 4 * n4);
     const unsigned grid = (unsigned)std::max<uint64_t>(1, (threads + 255) / 256);
-    float* R = m->rec + (off / 8) * kRecWords;  // off is a multiple of 8
     if (m->shadow)
-        k_adam<true><<<grid, 256, 0, st>>>(m->param + off, R, n, s, m->shadow + off, tab, k);
+        k_adam<true><<<grid, 256, 0, st>>>(m->param + off, m->grad + off, m->adam_m + off, m->adam_v + off, n, s,
+                                           m->shadow + off, tab, k);
     else
-        k_adam<false><<<grid, 256, 0, st>>>(m->param + off, R, n, s, nullptr, tab, k);
+        k_adam<false><<<grid, 256, 0, st>>>(m->param + off, m->grad + off, m->adam_m + off, m->adam_v + off, n, s,
+                                            nullptr, tab, k);
     return cudaGetLastError();
 }
 
@@ -417,15 +409,15 @@ static fhash_status ensure_tab(fhash_model* m, int64_t k) {
 
 fhash_status settle_deferred(fhash_model* m, cudaStream_t st) {
     if (!m->dirty) return FHASH_OK;
-    const uint64_t q0 = m->planned_lo / 8, q1 = m->planned_hi / 8, ng = q1 - q0;
+    const uint64_t ng = (m->defer_hi - m->defer_lo) / 8;
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((ng + 255) / 256, (uint64_t)num_sms() * 64));
     const AdamScal* tab = (const AdamScal*)m->adam_tab;
     if (m->shadow)
-        k_defer_flush<true><<<grid, 256, 0, st>>>(m->param, m->rec, m->shadow, q0, q1, tab, (uint32_t)m->clean_step,
-                                                  (uint32_t)m->step);
+        k_defer_flush<true><<<grid, 256, 0, st>>>(m->stamp, ng, m->param, m->grad, m->adam_m, m->adam_v, m->shadow,
+                                                  m->defer_lo, tab, (uint32_t)m->clean_step, (uint32_t)m->step);
     else
-        k_defer_flush<false><<<grid, 256, 0, st>>>(m->param, m->rec, nullptr, q0, q1, tab, (uint32_t)m->clean_step,
-                                                   (uint32_t)m->step);
+        k_defer_flush<false><<<grid, 256, 0, st>>>(m->stamp, ng, m->param, m->grad, m->adam_m, m->adam_v, nullptr,
+                                                   m->defer_lo, tab, (uint32_t)m->clean_step, (uint32_t)m->step);
     FH_CUDA(cudaGetLastError());
     m->dirty = false;
     m->clean_step = m->step;
@@ -461,7 +453,7 @@ static fhash_status catch_up(fhash_model* m, const float* coords, int64_t n, cud
     uint2* binned = items + cap;
     FH_CUDA(cudaMemsetAsync(ctr, 0, sizeof(DeferCtr), st));
     DeferArgs d{};
-    d.rec = m->rec;
+    d.stamp = m->stamp;
     d.q0 = m->defer_lo / 8;
     d.q1 = m->defer_hi / 8;
     d.target = target;
@@ -484,9 +476,11 @@ static fhash_status catch_up(fhash_model* m, const float* coords, int64_t n, cud
     const unsigned rg = (unsigned)num_sms() * 3;  // resident blocks (three per SM at this register use)
     const AdamScal* tab = (const AdamScal*)m->adam_tab;
     if (m->shadow)
-        k_defer_replay<true><<<rg, 256, 0, st>>>(binned, ctr, m->param, m->rec, m->shadow, m->defer_lo / 8, tab, target);
+        k_defer_replay<true><<<rg, 256, 0, st>>>(binned, ctr, m->param, m->grad, m->adam_m, m->adam_v, m->shadow,
+                                                 m->defer_lo, tab, target);
     else
-        k_defer_replay<false><<<rg, 256, 0, st>>>(binned, ctr, m->param, m->rec, nullptr, m->defer_lo / 8, tab, target);
+        k_defer_replay<false><<<rg, 256, 0, st>>>(binned, ctr, m->param, m->grad, m->adam_m, m->adam_v, nullptr,
+                                                  m->defer_lo, tab, target);
     FH_CUDA(cudaGetLastError());
     m->last_ctr = ctr;
     return FHASH_OK;
@@ -509,12 +503,17 @@ fhash_status launch_train_step(fhash_model* m, const float* coords, const float*
         tev_record(m, TEV_ADAM, st);
         return FHASH_OK;
     }
-    if (m->defer_lo != m->planned_lo || m->defer_hi != m->planned_hi) {
-        // the deferred range changed since the last deferred step: start from a fully current state (the
-        // stamps in the records are then at most clean_step, which makes them current)
-        FH_TRY(settle_deferred(m, st));
-        m->planned_lo = m->defer_lo;
-        m->planned_hi = m->defer_hi;
+    if (!m->stamp || m->stamp_groups != (m->defer_hi - m->defer_lo) / 8) {
+        FH_TRY(settle_deferred(m, st));  // the deferred range changed: start from current state
+        if (m->stamp) {
+            cudaFree(m->stamp);
+            m->device_bytes -= m->stamp_groups * 4;
+            m->stamp = nullptr;
+        }
+        m->stamp_groups = (m->defer_hi - m->defer_lo) / 8;
+        FH_CUDA(cudaMalloc(&m->stamp, std::max<uint64_t>(4, m->stamp_groups * 4)));
+        m->device_bytes += m->stamp_groups * 4;
+        FH_CUDA(cudaMemsetAsync(m->stamp, 0, m->stamp_groups * 4, st));
     }
     FH_TRY(ensure_tab(m, m->step + 2));
     FH_TRY(catch_up(m, coords, n, st));

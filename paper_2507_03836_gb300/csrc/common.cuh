@@ -79,12 +79,11 @@ struct fhash_model {
     int64_t nt = 1;
     int64_t step = 0;
 
-    // state of the flat parameter vector [n_params] (table values then MLP): the parameters as one
-    // float32 array; gradient, both Adam moments and the deferred-Adam stamp in 128-byte records of 8
-    // parameters (fh::rec_m / rec_v / rec_g / rec_stamp), one cache line per group
+    // flat state vectors [n_params] float32 (table values then MLP)
     float* param = nullptr;
-    float* rec = nullptr;      // n_rec records of 32 words: m[8], v[8], g[8], stamp, 7 unused
-    uint64_t n_rec = 0;        // ceil(n_params / 8)
+    float* grad = nullptr;
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
     __nv_bfloat16* shadow = nullptr;  // bf16 copy of param (FHASH_BF16 only)
 
     // occupancy over the FBB: bricks of 8^3 voxels, 16 x u32 words each (Morton order inside)
@@ -106,13 +105,14 @@ struct fhash_model {
     int32_t forward_path = 0;  // FHASH_FORWARD_* (precision form only)
 
     // deferred Adam (csrc/adam.cu): levels from defer_level on (those with at least defer_min_rows
-    // rows) hold the 8-parameter groups [defer_lo/8, defer_hi/8), each with a stamp in its record: the
+    // rows) hold 8-float groups [defer_lo/8, defer_hi/8) of the flat vectors, each with a stamp: the
     // step its p, m, v are current at; every group is at least clean_step-current; dirty when some
     // group is behind `step`.
     uint64_t defer_min_rows = 1ull << 25;
     int32_t defer_level = -1;
     uint64_t defer_lo = 0, defer_hi = 0;
-    uint64_t planned_lo = 0, planned_hi = 0;  // the range the last deferred step used (what a flush covers)
+    uint32_t* stamp = nullptr;
+    uint64_t stamp_groups = 0;
     int64_t clean_step = 0;
     bool dirty = false;
     void* adam_tab = nullptr;  // per-step Adam scalars, indexed by step
@@ -143,17 +143,6 @@ __host__ __device__ __forceinline__ uint64_t sm_at(uint64_t seed, uint64_t i) { 
 enum { TEV_START = 0, TEV_CLAIM, TEV_REPLAY, TEV_ENCODE, TEV_MLP, TEV_SCATTER, TEV_DW, TEV_ADAM, TEV_N };
 inline void tev_record(fhash_model* m, int i, cudaStream_t st) {
     if (m->timing) cudaEventRecord(m->tev[i], st);
-}
-
-// State record of parameters 8q .. 8q + 7 at rec + 32q (words): m[8], v[8], g[8], stamp.  A run of
-// consecutive parameters inside one 8-aligned group is consecutive in each field (every row of F = 1, 2, 4
-// or 8 values, every 16-byte-aligned x-pair of F = 2 rows).
-constexpr int kRecWords = 32;
-__host__ __device__ __forceinline__ float* rec_m(float* rec, uint64_t i) { return rec + ((i >> 3) << 5) + (i & 7); }
-__host__ __device__ __forceinline__ float* rec_v(float* rec, uint64_t i) { return rec + ((i >> 3) << 5) + 8 + (i & 7); }
-__host__ __device__ __forceinline__ float* rec_g(float* rec, uint64_t i) { return rec + ((i >> 3) << 5) + 16 + (i & 7); }
-__host__ __device__ __forceinline__ uint32_t* rec_stamp(float* rec, uint64_t q) {
-    return reinterpret_cast<uint32_t*>(rec + (q << 5) + 24);
 }
 
 fhash_status grow(fhash_model* m, Scratch& s, size_t bytes);

@@ -111,19 +111,18 @@ __global__ void __launch_bounds__(128) k_dw_tc(const __grid_constant__ DwMaps M,
     if (warp == 0) tc::tmem_dealloc(tmem, 64);
 }
 
-// gradient of parameter i0 + e (the model's state records) += sum over chunks of partial[chunk][layer][e],
-// e < fo*fi.
+// grad[e] += sum over chunks of partial[chunk][layer][e], e < fo*fi.
 __global__ void k_dw_tc_reduce(const float* __restrict__ partial, int nchunk, int nlayers, int layer, int ne,
-                               float* __restrict__ rec, uint64_t i0) {
+                               float* __restrict__ grad) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ne) return;
     float s = 0.0f;
     for (int c = 0; c < nchunk; ++c) s += partial[((int64_t)c * nlayers + layer) * 4096 + e];
-    *rec_g(rec, i0 + e) += s;
+    grad[e] += s;
 }
 
 // Bias gradients, two deterministic stages: part[o][c] = sum of delta[o][s] over chunk c (64 chunks),
-// then the gradient of parameter i0 + o += sum over c.
+// then grad[o] += sum over c.
 constexpr int kRowChunks = 64;
 __global__ void k_rowsum_part(const float* __restrict__ d, int64_t n, float* __restrict__ part) {
     const int o = blockIdx.x, c = blockIdx.y;
@@ -139,12 +138,12 @@ __global__ void k_rowsum_part(const float* __restrict__ d, int64_t n, float* __r
     }
     if (threadIdx.x == 0) part[o * kRowChunks + c] = red[0];
 }
-__global__ void k_rowsum_final(const float* __restrict__ part, int fo, float* __restrict__ rec, uint64_t i0) {
+__global__ void k_rowsum_final(const float* __restrict__ part, int fo, float* __restrict__ grad) {
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= fo) return;
     float s = 0.0f;
     for (int c = 0; c < kRowChunks; ++c) s += part[o * kRowChunks + c];
-    *rec_g(rec, i0 + o) += s;
+    grad[o] += s;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -204,12 +203,12 @@ bool launch_dw_tc(fhash_model* m, const float* acts, const float* dl, int64_t n,
         k_dw_tc<<<dim3(nchunk, nl), 128, smem, st>>>(M, n, chunk, wpart, m->err_word);
         e = cudaGetLastError();
     }
+    float* gm = m->grad + m->n_table;
     for (int j = 0; j < nl && e == cudaSuccess; ++j) {
         const int fi = j == 0 ? sh.in : W, fo = j == sh.nh ? 1 : W;
-        k_dw_tc_reduce<<<(fo * fi + 255) / 256, 256, 0, st>>>(wpart, nchunk, nl, j, fo * fi, m->rec,
-                                                             m->n_table + sh.w_off[j]);
+        k_dw_tc_reduce<<<(fo * fi + 255) / 256, 256, 0, st>>>(wpart, nchunk, nl, j, fo * fi, gm + sh.w_off[j]);
         k_rowsum_part<<<dim3(fo, kRowChunks), 256, 0, st>>>(dl + (int64_t)j * W * n, n, rpart);
-        k_rowsum_final<<<1, 64, 0, st>>>(rpart, fo, m->rec, m->n_table + sh.b_off[j]);
+        k_rowsum_final<<<1, 64, 0, st>>>(rpart, fo, gm + sh.b_off[j]);
         e = cudaGetLastError();
     }
     *err = e;

@@ -69,14 +69,13 @@ __global__ void k_dw_partial(const float* __restrict__ a, const float* __restric
     }
 }
 
-// gradient of parameter i0 + e (the model's state records) += sum over chunks of partial[c][e] (fixed
-// order: deterministic).
-__global__ void k_dw_reduce(const float* __restrict__ partial, int nchunk, int ne, float* __restrict__ rec, uint64_t i0) {
+// grad[e] += sum over chunks of partial[c][e] (fixed order: deterministic).
+__global__ void k_dw_reduce(const float* __restrict__ partial, int nchunk, int ne, float* __restrict__ grad) {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ne) return;
     float s = 0.0f;
     for (int c = 0; c < nchunk; ++c) s += partial[(int64_t)c * ne + e];
-    *rec_g(rec, i0 + e) += s;
+    grad[e] += s;
 }
 
 // loss = (sum of per-block partial sums of squared residuals) / n, float64, fixed order.
@@ -100,7 +99,7 @@ static cudaError_t dispatch_fused(fhash_model* m, int which, FusedArgs& a) {
     a.lv = &m->lv;
     a.sh = &m->mlp;
     a.T = m->param;
-    a.G = m->rec;
+    a.G = m->grad;
     a.Pm = m->param + m->n_table;
     int64_t blocks = (a.n + TB - 1) / TB;
     a.grid = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)num_sms() * 16));

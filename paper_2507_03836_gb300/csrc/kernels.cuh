@@ -325,7 +325,7 @@ __device__ __forceinline__ void scatter_sample(const Levels& lv, float* __restri
             float w = corner_weight(k, c);
             const uint64_t r = corner_row<LAYOUT>(k, c);
             if (LAYOUT == 2 && r == kInactiveRow) continue;  // inactive corners take no gradient
-            float* dst = rec_g(G, r * F);  // G: the model's state records (gradient field)
+            float* dst = G + r * F;
             if constexpr (F == 2) {
                 red_add2(dst, w * g[0], w * g[1]);
             } else if constexpr (F == 4) {
@@ -381,7 +381,7 @@ struct FusedArgs {
     const Levels* lv;
     const MlpShape* sh;
     const float* T;
-    float* G;  // the model's state records (gradients through rec_g)
+    float* G;
     const float* Pm;
     const float* coords;
     const float* target;

@@ -407,10 +407,10 @@ static fhash_status make_schedule(const fhash_schedule& sc, const int64_t S[3], 
 static void destroy_model(fhash_model* m) {
     if (!m) return;
     cudaDeviceSynchronize();
-    void* ps[] = {m->param, m->rec, m->shadow, m->occ, m->occ_any, m->dir, m->err_word,
+    void* ps[] = {m->param, m->grad, m->adam_m, m->adam_v, m->shadow, m->occ, m->occ_any, m->dir, m->err_word,
                   m->s_coords.p, m->s_target.p, m->s_out.p, m->s_acts.p, m->s_gacts.p, m->s_partial.p,
                   m->s_loss.p, m->s_misc.p, m->s_render.p, m->s_enc.p, m->s_cs_ent.p, m->s_cs_val.p,
-                  m->adam_tab, m->s_defer.p};
+                  m->stamp, m->adam_tab, m->s_defer.p};
     for (void* p : ps)
         if (p) cudaFree(p);
     if (m->tev_init)
@@ -576,13 +576,16 @@ fhash_status fhash_build(const fhash_build_desc* d, fhash_stream stream, fhash_m
     sh.n_params = off;
     m->n_params = m->n_table + (uint64_t)off;
 
-    // ---- state: param, records of gradient, Adam m and v and the deferral stamp (+ bf16 shadow)
+    // ---- state: param, grad, Adam m and v (+ bf16 shadow)
     const size_t bytes = (size_t)m->n_params * 4;
-    m->n_rec = (m->n_params + 7) / 8;
     FH_TRY(dev_alloc(m, (void**)&m->param, bytes));
-    FH_TRY(dev_alloc(m, (void**)&m->rec, (size_t)m->n_rec * kRecWords * 4));
+    FH_TRY(dev_alloc(m, (void**)&m->grad, bytes));
+    FH_TRY(dev_alloc(m, (void**)&m->adam_m, bytes));
+    FH_TRY(dev_alloc(m, (void**)&m->adam_v, bytes));
     if (d->dtype == FHASH_BF16) FH_TRY(dev_alloc(m, (void**)&m->shadow, (size_t)m->n_params * 2));
-    FH_CUDA(cudaMemsetAsync(m->rec, 0, (size_t)m->n_rec * kRecWords * 4, st));
+    FH_CUDA(cudaMemsetAsync(m->grad, 0, bytes, st));
+    FH_CUDA(cudaMemsetAsync(m->adam_m, 0, bytes, st));
+    FH_CUDA(cudaMemsetAsync(m->adam_v, 0, bytes, st));
 
     // tables U(-r, r) from stream 200; MLP with nn.Linear bounds, streams 300+2k (W) / 301+2k (b)
     double r = d->init_range;
@@ -647,7 +650,7 @@ fhash_status fhash_plan(const fhash_schedule* sched, const int64_t fbb[3], int64
     if (n_levels) *n_levels = L;
     if (table_rows) *table_rows = rows;
     if (n_params) *n_params = np;
-    if (state_bytes) *state_bytes = np * 4 + (np + 7) / 8 * (kRecWords * 4) + (dtype == FHASH_BF16 ? np * 2 : 0);
+    if (state_bytes) *state_bytes = np * 16 + (dtype == FHASH_BF16 ? np * 2 : 0);
     return FHASH_OK;
 }
 
@@ -675,76 +678,35 @@ fhash_status fhash_get_info(const fhash_model* m, fhash_info* o) {
     return FHASH_OK;
 }
 
-// Word offset of a state field inside a record, or -1 for the flat parameter array (and -2: unknown).
-static int state_field(int which) {
+static float* state_ptr(fhash_model* m, int which) {
     switch (which) {
-        case FHASH_STATE_PARAM: return -1;
-        case FHASH_STATE_ADAM_M: return 0;
-        case FHASH_STATE_ADAM_V: return 8;
-        case FHASH_STATE_GRAD: return 16;
-        default: return -2;
+        case FHASH_STATE_PARAM: return m->param;
+        case FHASH_STATE_GRAD: return m->grad;
+        case FHASH_STATE_ADAM_M: return m->adam_m;
+        case FHASH_STATE_ADAM_V: return m->adam_v;
+        default: return nullptr;
     }
-}
-
-// Elements [off, off + n) of one record field to (to_buf) or from a flat buffer: a partial record at each
-// end as contiguous copies, the whole records between them as 2D copies of 32 bytes at a 128-byte pitch.
-static fhash_status copy_field(fhash_model* m, int field, uint64_t off, uint64_t n, float* buf, bool to_buf,
-                               cudaStream_t st) {
-    auto one = [&](uint64_t i, uint64_t cnt, float* b) -> cudaError_t {
-        float* r = m->rec + ((i >> 3) << 5) + field + (i & 7);
-        return to_buf ? cudaMemcpyAsync(b, r, cnt * 4, cudaMemcpyDefault, st)
-                      : cudaMemcpyAsync(r, b, cnt * 4, cudaMemcpyDefault, st);
-    };
-    uint64_t i = off, done = 0;
-    if (n && (i & 7)) {
-        const uint64_t cnt = std::min<uint64_t>(8 - (i & 7), n);
-        FH_CUDA(one(i, cnt, buf));
-        i += cnt;
-        done += cnt;
-    }
-    while (n - done >= 8) {
-        const uint64_t rows = std::min<uint64_t>((n - done) / 8, 1ull << 24);
-        float* r = m->rec + ((i >> 3) << 5) + field;
-        if (to_buf)
-            FH_CUDA(cudaMemcpy2DAsync(buf + done, 32, r, kRecWords * 4, 32, rows, cudaMemcpyDefault, st));
-        else
-            FH_CUDA(cudaMemcpy2DAsync(r, kRecWords * 4, buf + done, 32, 32, rows, cudaMemcpyDefault, st));
-        i += rows * 8;
-        done += rows * 8;
-    }
-    if (done < n) FH_CUDA(one(i, n - done, buf + done));
-    return FHASH_OK;
 }
 
 fhash_status fhash_read_state(fhash_model* m, int32_t which, uint64_t off, uint64_t n, float* buf, fhash_stream stream) {
     if (!m || (!buf && n)) return set_error(FHASH_EINVAL, "fhash_read_state: null argument");
-    const int field = state_field(which);
-    if (field < -1) return set_error(FHASH_EINVAL, "fhash_read_state: unknown state %d", which);
+    float* p = state_ptr(m, which);
+    if (!p) return set_error(FHASH_EINVAL, "fhash_read_state: unknown state %d", which);
     if (off > m->n_params || n > m->n_params - off) return set_error(FHASH_EINVAL, "fhash_read_state: range out of bounds");
-    cudaStream_t st = (cudaStream_t)stream;
-    FH_TRY(settle_deferred(m, st));
-    if (!n) return FHASH_OK;
-    if (field < 0) {
-        FH_CUDA(cudaMemcpyAsync(buf, m->param + off, n * 4, cudaMemcpyDefault, st));
-        return FHASH_OK;
-    }
-    return copy_field(m, field, off, n, buf, true, st);
+    FH_TRY(settle_deferred(m, (cudaStream_t)stream));
+    if (n) FH_CUDA(cudaMemcpyAsync(buf, p + off, n * 4, cudaMemcpyDefault, (cudaStream_t)stream));
+    return FHASH_OK;
 }
 
 fhash_status fhash_write_state(fhash_model* m, int32_t which, uint64_t off, uint64_t n, const float* buf, fhash_stream stream) {
     if (!m || (!buf && n)) return set_error(FHASH_EINVAL, "fhash_write_state: null argument");
-    const int field = state_field(which);
-    if (field < -1) return set_error(FHASH_EINVAL, "fhash_write_state: unknown state %d", which);
+    float* p = state_ptr(m, which);
+    if (!p) return set_error(FHASH_EINVAL, "fhash_write_state: unknown state %d", which);
     if (off > m->n_params || n > m->n_params - off) return set_error(FHASH_EINVAL, "fhash_write_state: range out of bounds");
-    cudaStream_t st = (cudaStream_t)stream;
-    FH_TRY(settle_deferred(m, st));
-    if (!n) return FHASH_OK;
-    if (field < 0) {
-        FH_CUDA(cudaMemcpyAsync(m->param + off, buf, n * 4, cudaMemcpyDefault, st));
-        FH_TRY(refresh_shadow(m, off, n, st));
-        return FHASH_OK;
-    }
-    return copy_field(m, field, off, n, const_cast<float*>(buf), false, st);
+    FH_TRY(settle_deferred(m, (cudaStream_t)stream));
+    if (n) FH_CUDA(cudaMemcpyAsync(p + off, buf, n * 4, cudaMemcpyDefault, (cudaStream_t)stream));
+    if (which == FHASH_STATE_PARAM) FH_TRY(refresh_shadow(m, off, n, (cudaStream_t)stream));
+    return FHASH_OK;
 }
 
 fhash_status fhash_get_params(fhash_model* m, float* tables, float* mlp, fhash_stream stream) {
@@ -877,7 +839,7 @@ fhash_status fhash_save(const fhash_model* mc, const char* path) {
     CkptHeader h;
     memset(&h, 0, sizeof h);
     memcpy(h.magic, kMagic, 8);
-    h.version = 4;  // 2: levels carry their row layout; 3: masked directories; 4: state records
+    h.version = 3;  // 2: levels carry their row layout; 3: masked directories
     h.header_bytes = sizeof h;
     h.desc = m->desc;
     h.desc.mask = nullptr;
@@ -894,9 +856,10 @@ fhash_status fhash_save(const fhash_model* mc, const char* path) {
     void* pin = nullptr;
     if (rc == FHASH_OK && cudaMallocHost(&pin, pin_bytes) != cudaSuccess) rc = set_error(FHASH_ENOMEM, "fhash_save: pinned buffer");
     const uint64_t nb = (uint64_t)(m->nbx * m->nby * m->nbz * m->nt);
-    void* arrays[] = {m->param, m->rec, m->occ, m->occ_any, m->dir};
-    const uint64_t sizes[] = {m->n_params * 4, m->n_rec * kRecWords * 4, nb * 64, nb, h.dir_words * sizeof(uint4)};
-    for (int i = 0; i < 5 && rc == FHASH_OK; ++i)
+    void* arrays[] = {m->param, m->grad, m->adam_m, m->adam_v, m->occ, m->occ_any, m->dir};
+    const uint64_t sizes[] = {m->n_params * 4, m->n_params * 4, m->n_params * 4, m->n_params * 4, nb * 64, nb,
+                              h.dir_words * sizeof(uint4)};
+    for (int i = 0; i < 7 && rc == FHASH_OK; ++i)
         if (sizes[i]) rc = stream_file(f, arrays[i], sizes[i], true, pin, pin_bytes);
     if (pin) cudaFreeHost(pin);
     if (fclose(f) != 0 && rc == FHASH_OK) rc = set_error(FHASH_EIO, "fhash_save: close failed");
@@ -910,7 +873,7 @@ fhash_status fhash_load(const char* path, fhash_stream stream, fhash_model** out
     FILE* f = fopen(path, "rb");
     if (!f) return set_error(FHASH_EIO, "fhash_load: cannot open %s", path);
     CkptHeader h;
-    if (fread(&h, sizeof h, 1, f) != 1 || memcmp(h.magic, kMagic, 8) != 0 || h.version != 4 ||
+    if (fread(&h, sizeof h, 1, f) != 1 || memcmp(h.magic, kMagic, 8) != 0 || h.version != 3 ||
         h.header_bytes != sizeof h || h.lv.L < 1 || h.lv.L > FHASH_MAX_LEVELS || h.n_params < h.n_table) {
         fclose(f);
         return set_error(FHASH_EIO, "fhash_load: %s is not an F-Hash checkpoint of this version", path);
@@ -932,9 +895,10 @@ fhash_status fhash_load(const char* path, fhash_stream stream, fhash_model** out
     const size_t bytes = (size_t)m->n_params * 4;
     FH_TRY(dev_alloc(m, (void**)&m->err_word, sizeof(int)));
     FH_CUDA(cudaMemset(m->err_word, 0, sizeof(int)));
-    m->n_rec = (m->n_params + 7) / 8;
     FH_TRY(dev_alloc(m, (void**)&m->param, bytes));
-    FH_TRY(dev_alloc(m, (void**)&m->rec, (size_t)m->n_rec * kRecWords * 4));
+    FH_TRY(dev_alloc(m, (void**)&m->grad, bytes));
+    FH_TRY(dev_alloc(m, (void**)&m->adam_m, bytes));
+    FH_TRY(dev_alloc(m, (void**)&m->adam_v, bytes));
     if (m->desc.dtype == FHASH_BF16) FH_TRY(dev_alloc(m, (void**)&m->shadow, (size_t)m->n_params * 2));
     FH_TRY(dev_alloc(m, (void**)&m->occ, (size_t)nb * 64));
     FH_TRY(dev_alloc(m, (void**)&m->occ_any, (size_t)nb));
@@ -946,10 +910,10 @@ fhash_status fhash_load(const char* path, fhash_stream stream, fhash_model** out
     const size_t pin_bytes = 64u << 20;
     void* pin = nullptr;
     if (cudaMallocHost(&pin, pin_bytes) != cudaSuccess) return set_error(FHASH_ENOMEM, "fhash_load: pinned buffer");
-    void* arrays[] = {m->param, m->rec, m->occ, m->occ_any, m->dir};
-    const uint64_t sizes[] = {bytes, m->n_rec * kRecWords * 4, nb * 64, nb, h.dir_words * sizeof(uint4)};
+    void* arrays[] = {m->param, m->grad, m->adam_m, m->adam_v, m->occ, m->occ_any, m->dir};
+    const uint64_t sizes[] = {bytes, bytes, bytes, bytes, nb * 64, nb, h.dir_words * sizeof(uint4)};
     fhash_status rc = FHASH_OK;
-    for (int i = 0; i < 5 && rc == FHASH_OK; ++i)
+    for (int i = 0; i < 7 && rc == FHASH_OK; ++i)
         if (sizes[i]) rc = stream_file(f, arrays[i], sizes[i], false, pin, pin_bytes);
     cudaFreeHost(pin);
     if (rc != FHASH_OK) return rc;

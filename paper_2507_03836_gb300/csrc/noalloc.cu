@@ -9,7 +9,7 @@ namespace fh {
 cudaError_t run_fused_any(int F, int which, const FusedArgs& a);
 __global__ void k_dw_partial(const float* __restrict__ a, const float* __restrict__ d, int fi, int fo, int64_t n,
                              int64_t chunk, float* __restrict__ partial);
-__global__ void k_dw_reduce(const float* __restrict__ partial, int nchunk, int ne, float* __restrict__ rec, uint64_t i0);
+__global__ void k_dw_reduce(const float* __restrict__ partial, int nchunk, int ne, float* __restrict__ grad);
 __global__ void k_loss(const double* __restrict__ partial, int nb, int64_t n, double* __restrict__ loss);
 
 // Held by every GPU that loads the library, until exit.  In host code this name is only a host-side
@@ -91,7 +91,7 @@ extern "C" fhash_status fhash_compute_grads_noalloc(fhash_model* m, const float*
     a.lv = &m->lv;
     a.sh = &m->mlp;
     a.T = m->param;
-    a.G = m->rec;
+    a.G = m->grad;
     a.Pm = m->param + m->n_table;
     a.coords = coords;
     a.target = target;
@@ -106,13 +106,14 @@ extern "C" fhash_status fhash_compute_grads_noalloc(fhash_model* m, const float*
     k_loss<<<1, 256, 0, st>>>(lpart, nb_loss, n, dev_loss ? loss : lossd);
     FH_CUDA(cudaGetLastError());
     FH_CUDA(run_fused_any(m->lv.F, 2, a));
+    float* gm = m->grad + m->n_table;
     for (int j = 0; j <= sh.nh; ++j) {
         int fi = j == 0 ? sh.in : W, fo = j == sh.nh ? 1 : W;
         const float* aj = (j == 0) ? acts : acts + (int64_t)(sh.in + (j - 1) * W) * n;
         const float* dj = dl + (int64_t)j * W * n;
         k_dw_partial<<<nchunk, 256, 0, st>>>(aj, dj, fi, fo, n, chunk, wpart);
         int ne = fo * fi + fo;
-        k_dw_reduce<<<(ne + 255) / 256, 256, 0, st>>>(wpart, nchunk, ne, m->rec, m->n_table + sh.w_off[j]);
+        k_dw_reduce<<<(ne + 255) / 256, 256, 0, st>>>(wpart, nchunk, ne, gm + sh.w_off[j]);
     }
     FH_CUDA(cudaGetLastError());
     if (loss && !dev_loss) {

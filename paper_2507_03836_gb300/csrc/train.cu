@@ -86,8 +86,9 @@ __global__ void __launch_bounds__(256) k_scatter_cols(const __grid_constant__ Le
             }
         }
         __syncthreads();
+        float* Gl = G + L.base * F;
         for (int64_t e = threadIdx.x; e < nrow * F; e += blockDim.x)
-            if (acc[e] != 0.0f) red_add(rec_g(G, L.base * F + e), acc[e]);
+            if (acc[e] != 0.0f) red_add(Gl + e, acc[e]);
     } else {
         const int64_t s = s0 + threadIdx.x;
         if (s >= s1) return;
@@ -110,10 +111,10 @@ __global__ void __launch_bounds__(256) k_scatter_cols(const __grid_constant__ Le
                 const float w0 = corner_weight(k, c), w1 = corner_weight(k, c + 1);
                 // (kInactiveRow is odd, so an inactive lower row never takes the paired form)
                 if (r1 == r + 1 && (r & 1u) == 0u) {
-                    red_add4(rec_g(G, r * 2), w0 * g[0], w0 * g[1], w1 * g[0], w1 * g[1]);
+                    red_add4(G + r * 2, w0 * g[0], w0 * g[1], w1 * g[0], w1 * g[1]);
                 } else {
-                    if (LAYOUT != 2 || r != kInactiveRow) red_add2(rec_g(G, r * 2), w0 * g[0], w0 * g[1]);
-                    if (LAYOUT != 2 || r1 != kInactiveRow) red_add2(rec_g(G, r1 * 2), w1 * g[0], w1 * g[1]);
+                    if (LAYOUT != 2 || r != kInactiveRow) red_add2(G + r * 2, w0 * g[0], w0 * g[1]);
+                    if (LAYOUT != 2 || r1 != kInactiveRow) red_add2(G + r1 * 2, w1 * g[0], w1 * g[1]);
                 }
             }
         } else {
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(256) k_scatter_cols(const __grid_constant__ Le
                 }
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
-                    if (LAYOUT != 2 || r[h] != kInactiveRow) red_row<F>(rec_g(G, r[h] * F), corner_weight(k, c + h), g);
+                    if (LAYOUT != 2 || r[h] != kInactiveRow) red_row<F>(G + r[h] * F, corner_weight(k, c + h), g);
             }
         }
     }
@@ -410,15 +411,14 @@ __global__ void __launch_bounds__(256) k_dw_tiles(const __grid_constant__ DwLaye
     }
 }
 
-// gradient of MLP parameter off[layer] + e (flat index m0 + that) += sum over chunks of the partials
-// (weights then biases, contiguous per layer).
+// grad[off[layer] + e] += sum over chunks of the partials (weights then biases, contiguous per layer).
 __global__ void k_dw_reduce2(const float* __restrict__ partial, int nchunk, const __grid_constant__ DwLayers Ls,
-                             const __grid_constant__ MlpShape sh, float* __restrict__ rec, uint64_t m0) {
+                             const __grid_constant__ MlpShape sh, float* __restrict__ gm) {
     const int layer = blockIdx.y, e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= Ls.fo[layer] * Ls.fi[layer] + Ls.fo[layer]) return;
     float s = 0.0f;
     for (int c = 0; c < nchunk; ++c) s += partial[((int64_t)c * gridDim.y + layer) * kDwStride + e];
-    *rec_g(rec, m0 + sh.w_off[layer] + e) += s;
+    gm[sh.w_off[layer] + e] += s;
 }
 
 __global__ void k_loss2(const double* __restrict__ partial, int nb, int64_t n, double* __restrict__ loss) {
@@ -447,10 +447,10 @@ static cudaError_t scatter_run(fhash_model* m, const ScatterPlan& Pp, const Scat
         cudaError_t e = cudaFuncSetAttribute((const void*)k_scatter_cols<F, LAYOUT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, std::max(smem, 1));
         if (e != cudaSuccess) return e;
-        k_scatter_cols<F, LAYOUT><<<bp, 256, smem, st>>>(m->lv, Pp, m->rec, coords, n, denc, dsf, dss);
+        k_scatter_cols<F, LAYOUT><<<bp, 256, smem, st>>>(m->lv, Pp, m->grad, coords, n, denc, dsf, dss);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if (bf > 0) k_scatter_cols<F, LAYOUT><<<bf, 256, 0, st>>>(m->lv, Pf, m->rec, coords, n, denc, dsf, dss);
+    if (bf > 0) k_scatter_cols<F, LAYOUT><<<bf, 256, 0, st>>>(m->lv, Pf, m->grad, coords, n, denc, dsf, dss);
     return cudaGetLastError();
 }
 
@@ -595,7 +595,7 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
     }
     k_dw_tiles<<<dim3(nchunk, nl), 256, 0, st>>>(Ls, n, chunk, wpart);
     FH_CUDA(cudaGetLastError());
-    k_dw_reduce2<<<dim3((kDwStride + 255) / 256, nl), 256, 0, st>>>(wpart, nchunk, Ls, sh, m->rec, m->n_table);
+    k_dw_reduce2<<<dim3((kDwStride + 255) / 256, nl), 256, 0, st>>>(wpart, nchunk, Ls, sh, m->grad + m->n_table);
     FH_CUDA(cudaGetLastError());
     tev_record(m, TEV_DW, st);
     return FHASH_OK;

@@ -48,7 +48,7 @@ def test_fold_plan_matches_oracle(row, rule):
     assert p["table_rows"] == schedule.bases(lv)[1]
     dims = [len(lv) * row["F"], 64, 64, 1]
     assert p["n_params"] == schedule.param_count(lv, row["F"], dims)
-    assert p["state_bytes"] == 4 * p["n_params"] + 128 * ((p["n_params"] + 7) // 8)
+    assert p["state_bytes"] == 16 * p["n_params"]
     if row["name"] == "combustion":
         assert p["table_rows"] * row["F"] == {"max": 25374176, "min": 25374080}[rule]
         assert round(p["table_rows"] * row["F"] / 2 ** 20, 2) == 24.20
@@ -65,7 +65,7 @@ def test_geometric_and_explicit_plans():
     assert p["table_rows"] * w["F"] == 3557118770
     dims = [len(lv) * w["F"]] + [w["width"]] * w["hidden"] + [1]
     assert p["n_params"] == schedule.param_count(lv, w["F"], dims)
-    assert p["state_bytes"] == 6 * p["n_params"] + 128 * ((p["n_params"] + 7) // 8)
+    assert p["state_bytes"] == 18 * p["n_params"]
     res = [[3, 5, 2, 1], [6, 9, 7, 2], [13, 10, 17, 3]]
     q = f.fhash_plan((30, 30, 30), 4, f.make_schedule(mode="explicit", res=res), F=4, mlp_hidden_layers=1,
                      mlp_width=16)
