@@ -36,6 +36,11 @@ ADAM_SMALL_CASE = {"workload": "advect-128^3x32", "bytes_per_param_measured": (4
 ADAM_SMALL_CASE["ratio"] = ADAM_SMALL_CASE["bytes_per_param_measured"] / ADAM_SMALL_CASE["bytes_per_param_algorithmic"]
 
 
+# DRAM traffic of k_defer_replay from one ncu capture (full set) of the kernel on advect-128^3x32 after 100
+# aging steps: 1.0437 GB read + 0.2952 GB written for 2,410,972 caught-up groups of 8 parameters.
+REPLAY_DRAM_BYTES_PER_GROUP = (1.043689e9 + 0.29517184e9) / 2410972
+
+
 def _layout(args):
     """Row layout of the tables: brick (4x4x4 bricks per time slice, a linearisation Section 3.2.3
     allows; the bench's default because it gathers faster) or linear (Eq. 9, the library's default)."""
@@ -720,6 +725,8 @@ def main():
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"],
                     help="training form: float32, or the bf16 precision form (tensor-core MLP)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving and precision legs")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="samples per step (0: the workload's batch; other values are for profiling cases only)")
     ap.add_argument("--age-steps", type=int, default=512,
                     help="untimed training steps on fresh batches before the warm-up (steady-state Adam deferral)")
     ap.add_argument("--adam-deferral", type=int, default=-1,
@@ -777,6 +784,8 @@ def main():
     setup_s = time.time() - t0
 
     # batches: coords uniform in [0,1]^4 (FBB-normalised), targets sampled from the field
+    if args.batch > 0:
+        w = dict(w, batch=args.batch)
     B = w["batch"]
     # fresh batches for every loop below (warm-up, timed, phase breakdown, end to end): a batch seen a few
     # steps earlier would find its table groups almost current and understate the deferred Adam's replay
@@ -909,6 +918,26 @@ def main():
         phases[name] = {"ms": ms, "bytes_per_launch": by, "achieved": ach, "frac": ach / hbm, "unit": "GB/s",
                         "bytes": note}
     top = max(phases, key=lambda k: phases[k]["ms"])
+    roofline = dict(kernel=top, bound="hbm", achieved=phases[top]["achieved"], peak=hbm, unit="GB/s",
+                    frac=phases[top]["frac"], traffic=None, peak_source=peak_kind,
+                    bytes_per_launch=phases[top]["bytes_per_launch"], bytes=phases[top]["bytes"], phases=phases)
+    if top == "k_defer_replay" and replay_ms > 0:
+        # The replay is bound by special-function arithmetic, not by streamed bytes: every parameter-step
+        # takes one approximate square root and one approximate division.  Peak: 16 special-function
+        # results per clock per SM (4 per sub-partition) x 152 SMs x the maximum SM clock, two per
+        # parameter-step.  traffic: DRAM bytes per caught-up group from one ncu capture of this kernel on
+        # advect-128^3x32 (a launch of the full workload exceeds the capture size rule; the replay's
+        # memory traffic grows with the groups it catches up, not with their replay lengths).
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak_steps = 152 * 16 * sm_mhz * 1e6 / 2 / 1e9
+        steps_s = replay_steps * 8 / (replay_ms / 1e3) / 1e9
+        roofline.update(bound="alu", unit="G parameter-steps/s", achieved=steps_s, peak=peak_steps,
+                        frac=steps_s / peak_steps, peak_source="derived: 152 SMs x 16 special-function results "
+                        "per clock x %.0f MHz / 2 per parameter-step" % sm_mhz,
+                        traffic=REPLAY_DRAM_BYTES_PER_GROUP * replay_groups,
+                        traffic_note="ncu dram__bytes_read.sum + dram__bytes_write.sum per caught-up group on "
+                                     "advect-128^3x32 (%.0f B), times the groups of this launch" % REPLAY_DRAM_BYTES_PER_GROUP,
+                        hbm_algorithmic_frac=phases[top]["frac"])
     value = job_rate(world, B * K, elapsed)
     nh = w["hidden"]
     deferred = adam_stats["first_deferred_level"] >= 0
@@ -938,10 +967,7 @@ def main():
         # gradients and 3 reductions per layer; then the deferred catch-up (claim, sort, replay) and Adam over
         # the dense ranges (2 launches), or one dense Adam launch
         "gpu_launches": K * per_step,
-        "roofline": dict(kernel=top, bound="hbm", achieved=phases[top]["achieved"], peak=hbm, unit="GB/s",
-                         frac=phases[top]["frac"], traffic=None, peak_source=peak_kind,
-                         bytes_per_launch=phases[top]["bytes_per_launch"], bytes=phases[top]["bytes"],
-                         phases=phases),
+        "roofline": roofline,
         "clocks": clk,
         "e2e": {"value": job_rate(world, B * K, e2e_s), "unit": "samples/s", "h2d_bytes_per_step": B * 20,
                 "d2h_bytes_per_step": 8},

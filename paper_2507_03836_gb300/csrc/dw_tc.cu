@@ -1,4 +1,5 @@
-// MLP weight gradients of the precision form on the tensor cores, fed by TMA.
+// MLP weight gradients on the tensor cores, fed by TMA: tf32 inputs for the precision form, the
+// error-compensated 3xTF32 split for the float32 form.
 //
 // dW_j[o][c] = sum over samples s of delta_j[o][s] * a_j[c][s].  The backward keeps deltas and
 // activations as float32 columns [feature][n], so both operands are already K-major with the samples
@@ -28,13 +29,28 @@ struct alignas(64) DwMaps {
     int32_t fi[FHASH_MAX_HIDDEN + 1], fo[FHASH_MAX_HIDDEN + 1];
 };
 
+// Round to the nearest tf32 value (10 explicit mantissa bits, ties to even), kept as float32.
+__device__ __forceinline__ float tf32_rn(float x) {
+    uint32_t u = __float_as_uint(x);
+    u += 0xFFFu + ((u >> 13) & 1u);
+    return __uint_as_float(u & 0xFFFFE000u);
+}
+
+// SPLIT3 (the float32 form): every staged value a is split in shared memory into hi = tf32(a) and
+// lo = a - hi (exact in float32), and each K step issues hi*hi + hi*lo + lo*hi (the lo*lo term is below
+// float32 rounding): the error-compensated "3xTF32" product of Ootomo and Yokota (2022), which keeps the
+// weight gradients at float32 accuracy on the tensor cores.  Without it (the precision form) the
+// tensor cores read the float32 inputs as tf32.
+template <bool SPLIT3>
 __global__ void __launch_bounds__(128) k_dw_tc(const __grid_constant__ DwMaps M, int64_t n, int64_t chunk,
                                                float* __restrict__ partial, int* __restrict__ err) {
     extern __shared__ uint8_t smraw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
     uint8_t* tileA = sm;
     uint8_t* tileB = sm + kDwStages * kDwTileA;
-    uint64_t* full = reinterpret_cast<uint64_t*>(tileB + kDwStages * kDwTileB);
+    uint8_t* loA = tileB + kDwStages * kDwTileB;             // SPLIT3 only
+    uint8_t* loB = loA + (SPLIT3 ? kDwStages * kDwTileA : 0);
+    uint64_t* full = reinterpret_cast<uint64_t*>(loB + (SPLIT3 ? kDwStages * kDwTileB : 0));
     uint64_t* empty = full + kDwStages;
     uint32_t* slot = reinterpret_cast<uint32_t*>(empty + kDwStages);
     const int t = threadIdx.x, warp = t >> 5, layer = blockIdx.y;
@@ -52,39 +68,97 @@ __global__ void __launch_bounds__(128) k_dw_tc(const __grid_constant__ DwMaps M,
     tc::fence_after_sync();
     const uint32_t tmem = *slot;
     bool bad = false;
-    if (t == 0 && nk > 0) {
-        const void* mapA = &M.a[layer];
-        const void* mapB = &M.b[layer];
-        auto load = [&](int kt) {
-            const int s = kt % kDwStages;
-            tc::mbar_expect_tx(&full[s], kDwTileA + kDwTileB);
-            const int x = (int)(s0 + 32 * (int64_t)kt);
-            tc::tma_load_2d(tileA + s * kDwTileA, mapA, x, 0, &full[s]);
-            tc::tma_load_2d(tileB + s * kDwTileB, mapB, x, 0, &full[s]);
-        };
-        for (int kt = 0; kt < nk && kt < kDwStages; ++kt) load(kt);
-        constexpr uint32_t idesc = tc::idesc_tf32(128, 64);
-        const uint32_t a0 = tc::smem_addr(tileA), b0 = tc::smem_addr(tileB);
-        for (int kt = 0; kt < nk && !bad; ++kt) {
+    const void* mapA = &M.a[layer];
+    const void* mapB = &M.b[layer];
+    auto load = [&](int kt) {
+        const int s = kt % kDwStages;
+        tc::mbar_expect_tx(&full[s], kDwTileA + kDwTileB);
+        const int x = (int)(s0 + 32 * (int64_t)kt);
+        tc::tma_load_2d(tileA + s * kDwTileA, mapA, x, 0, &full[s]);
+        tc::tma_load_2d(tileB + s * kDwTileB, mapB, x, 0, &full[s]);
+    };
+    constexpr uint32_t idesc = tc::idesc_tf32(128, 64);
+    const uint32_t a0 = tc::smem_addr(tileA), b0 = tc::smem_addr(tileB);
+    if (!SPLIT3) {
+        if (t == 0 && nk > 0) {
+            for (int kt = 0; kt < nk && kt < kDwStages; ++kt) load(kt);
+            for (int kt = 0; kt < nk && !bad; ++kt) {
+                const int s = kt % kDwStages;
+                const uint32_t ph = (uint32_t)(kt / kDwStages) & 1u;
+                if (!tc::mbar_wait(&full[s], ph)) { bad = true; break; }
+                tc::fence_after_sync();
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    tc::mma_tf32(tmem, tc::sdesc_sw128(a0 + s * kDwTileA + kk * 32), tc::sdesc_sw128(b0 + s * kDwTileB + kk * 32),
+                                 idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+                tc::mma_commit(&empty[s]);
+                if (kt + kDwStages < nk) {
+                    if (!tc::mbar_wait(&empty[s], ph)) { bad = true; break; }
+                    load(kt + kDwStages);
+                }
+            }
+            if (!bad) {  // every MMA has completed once the last commit has arrived
+                const int kl = nk - 1;
+                if (!tc::mbar_wait(&empty[kl % kDwStages], (uint32_t)(kl / kDwStages) & 1u)) bad = true;
+            }
+            if (bad) raise_error(err, 0x7C06);
+        }
+    } else if (nk > 0) {
+        const uint32_t la0 = tc::smem_addr(loA), lb0 = tc::smem_addr(loB);
+        int loaded = 0, consumed = 0, issued = 0;  // copies issued, copies waited for, MMA batches committed
+        if (t == 0)
+            for (; loaded < nk && loaded < kDwStages; ++loaded) load(loaded);
+        for (int kt = 0; kt < nk; ++kt) {
             const int s = kt % kDwStages;
             const uint32_t ph = (uint32_t)(kt / kDwStages) & 1u;
-            if (!tc::mbar_wait(&full[s], ph)) { bad = true; break; }
-            tc::fence_after_sync();
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-                tc::mma_tf32(tmem, tc::sdesc_sw128(a0 + s * kDwTileA + kk * 32), tc::sdesc_sw128(b0 + s * kDwTileB + kk * 32),
-                             idesc, (kt > 0 || kk > 0) ? 1u : 0u);
-            tc::mma_commit(&empty[s]);
-            if (kt + kDwStages < nk) {
-                if (!tc::mbar_wait(&empty[s], ph)) { bad = true; break; }
-                load(kt + kDwStages);
+            const bool ok = tc::mbar_wait(&full[s], ph);
+            if (__syncthreads_or(!ok)) { bad = true; break; }
+            consumed = kt + 1;
+            // split the stage in place: tile <- hi, lo buffer <- a - hi (same swizzled positions)
+            float4* ha = reinterpret_cast<float4*>(tileA + s * kDwTileA);
+            float4* hb = reinterpret_cast<float4*>(tileB + s * kDwTileB);
+            float4* la = reinterpret_cast<float4*>(loA + s * kDwTileA);
+            float4* lb = reinterpret_cast<float4*>(loB + s * kDwTileB);
+            for (int e = t; e < (kDwTileA + kDwTileB) / 16; e += blockDim.x) {
+                float4* h = e < kDwTileA / 16 ? ha + e : hb + (e - kDwTileA / 16);
+                float4* l = e < kDwTileA / 16 ? la + e : lb + (e - kDwTileA / 16);
+                const float4 v = *h;
+                const float4 hi = make_float4(tf32_rn(v.x), tf32_rn(v.y), tf32_rn(v.z), tf32_rn(v.w));
+                *h = hi;
+                *l = make_float4(v.x - hi.x, v.y - hi.y, v.z - hi.z, v.w - hi.w);
             }
+            tc::fence_async_smem();  // the generic-proxy stores become visible to the tensor cores
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+            if (t == 0) {
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint64_t ah = tc::sdesc_sw128(a0 + s * kDwTileA + kk * 32), bh = tc::sdesc_sw128(b0 + s * kDwTileB + kk * 32);
+                    const uint64_t al = tc::sdesc_sw128(la0 + s * kDwTileA + kk * 32), bl = tc::sdesc_sw128(lb0 + s * kDwTileB + kk * 32);
+                    tc::mma_tf32(tmem, ah, bh, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+                    tc::mma_tf32(tmem, ah, bl, idesc, 1u);
+                    tc::mma_tf32(tmem, al, bh, idesc, 1u);
+                }
+                tc::mma_commit(&empty[s]);
+                issued = kt + 1;
+                if (loaded < nk) {
+                    if (!tc::mbar_wait(&empty[s], ph)) bad = true;  // stage s free again: refill it
+                    else load(loaded++);
+                }
+            }
+            if (__syncthreads_or(bad)) { bad = true; break; }
         }
-        if (!bad) {  // every MMA has completed once the last commit has arrived
-            const int kl = nk - 1;
-            if (!tc::mbar_wait(&empty[kl % kDwStages], (uint32_t)(kl / kDwStages) & 1u)) bad = true;
+        if (t == 0) {
+            // wait (bounded) for the last committed batch, so that no MMA is in flight when TMEM is freed,
+            // and for every copy issued but not waited for, so that none lands after the CTA has left
+            if (issued > 0) {
+                const int kl = issued - 1;
+                if (!tc::mbar_wait(&empty[kl % kDwStages], (uint32_t)(kl / kDwStages) & 1u)) bad = true;
+            }
+            for (int k = consumed; k < loaded; ++k) tc::mbar_wait(&full[k % kDwStages], (uint32_t)(k / kDwStages) & 1u);
+            if (bad) raise_error(err, 0x7C06);
         }
-        if (bad) raise_error(err, 0x7C06);
     }
     tc::fence_before_sync();
     const int any_bad = __syncthreads_or(bad);
@@ -177,7 +251,7 @@ static bool make_map(CUtensorMap* m, const float* base, int64_t n, int rows, int
 // n samples).  Returns false (nothing launched) when the tensor-core path does not apply: n not a
 // multiple of 4 (row strides must be 16-byte multiples) or no tensor-map encoder.
 bool launch_dw_tc(fhash_model* m, const float* acts, const float* dl, int64_t n, float* wpart, size_t wpart_bytes,
-                  cudaStream_t st, cudaError_t* err) {
+                  cudaStream_t st, cudaError_t* err, bool split3) {
     *err = cudaSuccess;
     const MlpShape& sh = m->mlp;
     const int W = sh.width, nl = sh.nh + 1;
@@ -197,10 +271,14 @@ bool launch_dw_tc(fhash_model* m, const float* acts, const float* dl, int64_t n,
         M.fi[j] = fi;
         M.fo[j] = fo;
     }
-    const int smem = 1024 + kDwStages * (kDwTileA + kDwTileB) + 2 * kDwStages * 8 + 16;
-    cudaError_t e = cudaFuncSetAttribute((const void*)k_dw_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int smem = 1024 + (split3 ? 2 : 1) * kDwStages * (kDwTileA + kDwTileB) + 2 * kDwStages * 8 + 16;
+    const void* fn = split3 ? (const void*)k_dw_tc<true> : (const void*)k_dw_tc<false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) {
-        k_dw_tc<<<dim3(nchunk, nl), 128, smem, st>>>(M, n, chunk, wpart, m->err_word);
+        if (split3)
+            k_dw_tc<true><<<dim3(nchunk, nl), 128, smem, st>>>(M, n, chunk, wpart, m->err_word);
+        else
+            k_dw_tc<false><<<dim3(nchunk, nl), 128, smem, st>>>(M, n, chunk, wpart, m->err_word);
         e = cudaGetLastError();
     }
     float* gm = m->grad + m->n_table;

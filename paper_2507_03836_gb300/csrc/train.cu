@@ -436,7 +436,7 @@ __global__ void k_loss2(const double* __restrict__ partial, int nb, int64_t n, d
 
 cudaError_t run_tc_any(fhash_model* m, bool train, FusedArgs& a);
 bool launch_dw_tc(fhash_model* m, const float* acts, const float* dl, int64_t n, float* wpart, size_t wpart_bytes,
-                  cudaStream_t st, cudaError_t* err);
+                  cudaStream_t st, cudaError_t* err, bool split3);
 
 template <int F, int LAYOUT>
 static cudaError_t scatter_run(fhash_model* m, const ScatterPlan& Pp, const ScatterPlan& Pf, int bp, int bf,
@@ -523,7 +523,7 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
     // weight-gradient chunks: about 4 blocks per SM over all layers, at least 512 samples each
     const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>((n + 511) / 512, (int64_t)num_sms() * 4 / nl));
     const int64_t chunk = ((n + nchunk - 1) / nchunk + 31) / 32 * 32;
-    const size_t tc_part = m->shadow ? ((size_t)num_sms() * nl * 4096 + 64 * 64) * 4 : 0;
+    const size_t tc_part = ((size_t)num_sms() * nl * 4096 + 64 * 64) * 4;
     FH_TRY(grow(m, m->s_partial, std::max((size_t)nchunk * nl * kDwStride * 4, tc_part) + (size_t)nb * 8 + 64));
     float* acts = (float*)m->s_acts.p;
     float* gy = (float*)m->s_gacts.p;
@@ -576,11 +576,12 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
         case 8: FH_CUDA(scatter_launch<8>(m, coords, n, denc, n, 1, st)); break;
     }
     tev_record(m, TEV_SCATTER, st);
-    // weight gradients: tensor cores (TMA + tcgen05 kind::tf32) for the bf16 form, float32 SIMT tiles
-    // otherwise (the float32 form keeps full float32 products)
-    if (m->shadow) {
+    // weight gradients on the tensor cores (TMA + tcgen05 kind::tf32): tf32 inputs for the bf16 form, the
+    // 3xTF32 split (float32 accuracy) for the float32 form; float32 SIMT tiles when the batch does not
+    // suit the tensor maps (n not a multiple of 4, or below 32)
+    {
         cudaError_t e = cudaSuccess;
-        if (launch_dw_tc(m, acts, dl, n, wpart, m->s_partial.bytes - wpart_off, st, &e)) {
+        if (launch_dw_tc(m, acts, dl, n, wpart, m->s_partial.bytes - wpart_off, st, &e, m->shadow == nullptr)) {
             FH_CUDA(e);
             tev_record(m, TEV_DW, st);
             return FHASH_OK;

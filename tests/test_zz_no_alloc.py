@@ -3,9 +3,10 @@
 The no-allocation variant exists for callers that cannot call cudaMalloc (an application that has
 given all device memory to its own pool, or a loop that cannot take the implicit device
 synchronisation of cudaMalloc/cudaFree).  It must give the same loss and gradients as the regular
-entry point: checked here on two calls in a row (gradients accumulate), within the tolerance of the
-gradient parity test (1e-4 relative to the magnitude of the entries; the atomic scatter order differs
-between runs), for both rectangular row layouts, embedding sizes F = 1, 2, 4 and 8, and a model built
+entry point: checked here on two calls in a row (gradients accumulate), within the tolerances of the
+gradient parity tests (table gradients 1e-4 relative to the magnitude of the entries, the atomic
+scatter order differs between runs; MLP gradients, which the regular entry point forms on the tensor
+cores, within 2e-4 x the sum of the magnitudes of each entry's terms), for both rectangular row layouts, embedding sizes F = 1, 2, 4 and 8, and a model built
 in the bf16 precision form (whose float32 form this call evaluates: it is compared with a float32
 model holding the same parameters).  The call must also leave the device's free memory unchanged.
 This file is collected last so that a first-failure stop has run every other test.
@@ -15,6 +16,7 @@ import pytest
 
 import synth
 from synth import workloads
+from oracle import encode, mlp
 
 from _util import fh, read, set_params, to_dev, torch
 
@@ -52,7 +54,10 @@ def test_noalloc_matches_regular_entry_point(field_mask, layout, F, dtype):
     p = synth.init_mlp(8, info["mlp_dims"])
     set_params(ref, table, p)
     set_params(alt, table, p)
-    n_all = info["n_table_params"] + info["n_mlp_params"]
+    n_t, n_all = info["n_table_params"], info["n_table_params"] + info["n_mlp_params"]
+    T = table.reshape(-1, F).astype(np.float64)
+    pd = p.astype(np.float64)
+    abs_mlp = np.zeros(info["n_mlp_params"])
     for call, n in enumerate((fh().NOALLOC_MAX_SAMPLES, 777)):
         c = synth.coords(60 + call, n)
         tgt = synth.sample(f, info["fbb_lo"], info["fbb_size"], c)
@@ -66,7 +71,16 @@ def test_noalloc_matches_regular_entry_point(field_mask, layout, F, dtype):
         g_ref = read(ref, fh().STATE_GRAD, 0, n_all)
         g_alt = read(alt, fh().STATE_GRAD, 0, n_all)
         assert np.abs(g_ref).max() > 0
-        assert _close(g_alt, g_ref), call
+        # table gradients: the same float32 scatter arithmetic, element by element
+        assert _close(g_alt[:n_t], g_ref[:n_t]), call
+        # MLP gradients: the regular entry point forms them on the tensor cores (3xTF32 products), this
+        # one with float32 products on the CUDA cores; both within 1e-4 x the sum of the magnitudes of
+        # each entry's terms (the bound of the gradient parity tests), so within 2e-4 of each other
+        y, a, z = mlp.forward(pd, info["mlp_dims"], encode.encode(info["res"], info["base"], c, T, layout))
+        _, gy = mlp.mse(y, tgt)
+        abs_mlp += mlp.backward(np.abs(pd), info["mlp_dims"], [np.abs(x) for x in a],
+                                [np.where(x > 0, 1.0, -1.0) for x in z], np.abs(gy))[0]
+        assert (np.abs(g_alt[n_t:] - g_ref[n_t:]) <= 2e-4 * abs_mlp + 1e-12).all(), call
     fh().fhash_check(alt)
 
 
