@@ -326,7 +326,12 @@ typedef struct {
     float last_ms[7];                /* with timing on, the last training step's phases (ms): claim and
                                         sort of the catch-up, its replay, the gathers (bf16: the fused
                                         forward), MLP forward + loss + backward, table scatter, weight
-                                        gradients, dense Adam */
+                                        gradients, dense Adam (with deferred levels: only the recording
+                                        of the step's scalars; see last_side_ms) */
+    float last_side_ms;              /* with timing on and deferred levels: the dense update of the levels
+                                        below the deferred ones and the MLP, which a deferred step leaves to
+                                        the next step; that step runs it on a second stream beside its
+                                        replay and waits for it before its gathers.  0 otherwise */
 } fhash_adam_stats;
 
 /* Deferral state and the last training step's counters; synchronises with the last training step. */

@@ -282,11 +282,18 @@ __device__ __forceinline__ void replay_group(float* __restrict__ P, float* __res
         adam4(p0, g0, m0, v0, s);
         adam4(p1, g1, m1, v1, s);
     }
+    if (from + 2 <= to) {
+        // the next step's scalars are loaded while this step's eight independent chains run
+        AdamScal sn = tab[from + 2];
 #pragma unroll 1
-    for (uint32_t j = from + 2; j <= to; ++j) {  // eight independent chains per iteration
-        const AdamScal s = tab[j];
-        adam4_zero(p0, m0, v0, s);
-        adam4_zero(p1, m1, v1, s);
+        for (uint32_t j = from + 2; j < to; ++j) {
+            const AdamScal s = sn;
+            sn = tab[j + 1];
+            adam4_zero(p0, m0, v0, s);
+            adam4_zero(p1, m1, v1, s);
+        }
+        adam4_zero(p0, m0, v0, sn);
+        adam4_zero(p1, m1, v1, sn);
     }
     P4[0] = p0; P4[1] = p1;
     M4[0] = m0; M4[1] = m1;
@@ -407,17 +414,45 @@ static fhash_status ensure_tab(fhash_model* m, int64_t k) {
     return FHASH_OK;
 }
 
+// The pending dense-range update (levels below the deferred ones and the MLP) of step pend_k, on st.
+static fhash_status apply_pending_dense(fhash_model* m, cudaStream_t st) {
+    const AdamScal s = scalars(&m->pend_ad, m->pend_k);
+    FH_CUDA(dense_range(m, 0, m->planned_lo, s, nullptr, m->pend_k, st));
+    FH_CUDA(dense_range(m, m->planned_hi, m->n_params - m->planned_hi, s, nullptr, m->pend_k, st));
+    m->dense_pending = false;
+    return FHASH_OK;
+}
+
+// The pending dense-range update on the side stream, after everything issued on st so far; ev_join marks
+// its end.
+static fhash_status fork_pending_dense(fhash_model* m, cudaStream_t st) {
+    if (!m->side) {
+        FH_CUDA(cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking));
+        FH_CUDA(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
+        FH_CUDA(cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming));
+    }
+    FH_CUDA(cudaEventRecord(m->ev_fork, st));
+    FH_CUDA(cudaStreamWaitEvent(m->side, m->ev_fork, 0));
+    if (m->timing) FH_CUDA(cudaEventRecord(m->tev_side[0], m->side));
+    FH_TRY(apply_pending_dense(m, m->side));
+    if (m->timing) FH_CUDA(cudaEventRecord(m->tev_side[1], m->side));
+    m->side_timed = m->timing;
+    FH_CUDA(cudaEventRecord(m->ev_join, m->side));
+    return FHASH_OK;
+}
+
 fhash_status settle_deferred(fhash_model* m, cudaStream_t st) {
+    if (m->dense_pending) FH_TRY(apply_pending_dense(m, st));
     if (!m->dirty) return FHASH_OK;
-    const uint64_t ng = (m->defer_hi - m->defer_lo) / 8;
+    const uint64_t ng = (m->planned_hi - m->planned_lo) / 8;
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((ng + 255) / 256, (uint64_t)num_sms() * 64));
     const AdamScal* tab = (const AdamScal*)m->adam_tab;
     if (m->shadow)
         k_defer_flush<true><<<grid, 256, 0, st>>>(m->stamp, ng, m->param, m->grad, m->adam_m, m->adam_v, m->shadow,
-                                                  m->defer_lo, tab, (uint32_t)m->clean_step, (uint32_t)m->step);
+                                                  m->planned_lo, tab, (uint32_t)m->clean_step, (uint32_t)m->step);
     else
         k_defer_flush<false><<<grid, 256, 0, st>>>(m->stamp, ng, m->param, m->grad, m->adam_m, m->adam_v, nullptr,
-                                                   m->defer_lo, tab, (uint32_t)m->clean_step, (uint32_t)m->step);
+                                                   m->planned_lo, tab, (uint32_t)m->clean_step, (uint32_t)m->step);
     FH_CUDA(cudaGetLastError());
     m->dirty = false;
     m->clean_step = m->step;
@@ -439,8 +474,13 @@ static void claim_any(fhash_model* m, unsigned grid, const float* coords, int64_
     }
 }
 
-// Brings every group that a batch's gathers will read to step m->step (deferred step m->step + 1).
-static fhash_status catch_up(fhash_model* m, const float* coords, int64_t n, cudaStream_t st) {
+static fhash_status fork_pending_dense(fhash_model* m, cudaStream_t st);
+
+// Brings every group that a batch's gathers will read to step m->step (deferred step m->step + 1).  A
+// pending dense-range update is forked onto the side stream once the claim list is sorted, so that it
+// runs beside the replay (which is bound by its arithmetic) rather than beside the claim (whose random
+// stamp accesses compete with it for memory).
+static fhash_status catch_up(fhash_model* m, const float* coords, int64_t n, cudaStream_t st, bool* forked) {
     const uint32_t target = (uint32_t)m->step;
     if (target == (uint32_t)m->clean_step) return FHASH_OK;  // nothing is behind the previous step
     const int nd = m->lv.L - m->defer_level;
@@ -473,6 +513,10 @@ static fhash_status catch_up(fhash_model* m, const float* coords, int64_t n, cud
     k_defer_bin<<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(items, binned, ctr, target);
     FH_CUDA(cudaGetLastError());
     tev_record(m, TEV_CLAIM, st);
+    if (m->dense_pending) {
+        FH_TRY(fork_pending_dense(m, st));
+        *forked = true;
+    }
     const unsigned rg = (unsigned)num_sms() * 3;  // resident blocks (three per SM at this register use)
     const AdamScal* tab = (const AdamScal*)m->adam_tab;
     if (m->shadow)
@@ -494,6 +538,7 @@ fhash_status launch_train_step(fhash_model* m, const float* coords, const float*
     const bool defer = m->defer_level >= 0 && m->step + 1 < (int64_t)UINT32_MAX;
     tev_record(m, TEV_START, st);
     m->last_ctr = nullptr;
+    m->side_timed = false;
     if (!defer) {
         FH_TRY(settle_deferred(m, st));
         tev_record(m, TEV_CLAIM, st);
@@ -516,15 +561,26 @@ fhash_status launch_train_step(fhash_model* m, const float* coords, const float*
         FH_CUDA(cudaMemsetAsync(m->stamp, 0, m->stamp_groups * 4, st));
     }
     FH_TRY(ensure_tab(m, m->step + 2));
-    FH_TRY(catch_up(m, coords, n, st));
+    // The previous step's dense-range update runs on a second stream beside this step's catch-up (they
+    // touch disjoint parameters) and is joined before the gathers, which read those parameters.
+    bool forked = false;
+    FH_TRY(catch_up(m, coords, n, st, &forked));
     if (!m->last_ctr) tev_record(m, TEV_CLAIM, st);
+    if (m->dense_pending && !forked) {
+        FH_TRY(fork_pending_dense(m, st));
+        forked = true;
+    }
+    if (forked) FH_CUDA(cudaStreamWaitEvent(st, m->ev_join, 0));
+    m->planned_lo = m->defer_lo;  // the range this step defers (the pending update above used the last one)
+    m->planned_hi = m->defer_hi;
     tev_record(m, TEV_REPLAY, st);
     FH_TRY(launch_grads2(m, coords, target, n, loss_dev, st));
     const int64_t k = m->step + 1;
-    const AdamScal s = scalars(ad, k);
-    AdamScal* tab = (AdamScal*)m->adam_tab;
-    FH_CUDA(dense_range(m, 0, m->defer_lo, s, tab, k, st));
-    FH_CUDA(dense_range(m, m->defer_hi, m->n_params - m->defer_hi, s, nullptr, k, st));
+    k_set_tab<<<1, 1, 0, st>>>((AdamScal*)m->adam_tab, k, scalars(ad, k));  // for later replays
+    FH_CUDA(cudaGetLastError());
+    m->pend_ad = *ad;
+    m->pend_k = k;
+    m->dense_pending = true;
     m->step = k;
     m->dirty = true;
     tev_record(m, TEV_ADAM, st);
@@ -549,6 +605,7 @@ fhash_status fhash_set_timing(fhash_model* m, int32_t enable) {
     if (!m) return set_error(FHASH_EINVAL, "fhash_set_timing: null model");
     if (enable && !m->tev_init) {
         for (int i = 0; i < TEV_N; ++i) FH_CUDA(cudaEventCreate(&m->tev[i]));
+        for (int i = 0; i < 2; ++i) FH_CUDA(cudaEventCreate(&m->tev_side[i]));
         m->tev_init = true;
     }
     m->timing = enable != 0;
@@ -572,6 +629,7 @@ fhash_status fhash_get_adam_stats(fhash_model* m, fhash_adam_stats* out) {
     if (m->timing && m->tev_init) {
         FH_CUDA(cudaEventSynchronize(m->tev[TEV_ADAM]));
         for (int i = 0; i + 1 < TEV_N; ++i) FH_CUDA(cudaEventElapsedTime(&out->last_ms[i], m->tev[i], m->tev[i + 1]));
+        if (m->side_timed) FH_CUDA(cudaEventElapsedTime(&out->last_side_ms, m->tev_side[0], m->tev_side[1]));
     }
     return FHASH_OK;
 }

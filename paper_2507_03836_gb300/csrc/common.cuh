@@ -111,6 +111,7 @@ struct fhash_model {
     uint64_t defer_min_rows = 1ull << 25;
     int32_t defer_level = -1;
     uint64_t defer_lo = 0, defer_hi = 0;
+    uint64_t planned_lo = 0, planned_hi = 0;  // the range the last deferred step used (what a flush covers)
     uint32_t* stamp = nullptr;
     uint64_t stamp_groups = 0;
     int64_t clean_step = 0;
@@ -118,10 +119,19 @@ struct fhash_model {
     void* adam_tab = nullptr;  // per-step Adam scalars, indexed by step
     int64_t adam_tab_cap = 0;
     fh::Scratch s_defer;       // counters, claim list and its bucket-sorted copy
+    // the dense-range Adam update of step pend_k (hyper-parameters pend_ad) not run yet: the next
+    // training step runs it on `side` beside its catch-up; anything else runs it first
+    bool dense_pending = false;
+    fhash_adam pend_ad{};
+    int64_t pend_k = 0;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     void* last_ctr = nullptr;  // counters of the last step's catch-up (device), or null
     // phase timing of fhash_train_step (fhash_set_timing): events at the phase boundaries fh::TEV_*
     bool timing = false, tev_init = false;
     cudaEvent_t tev[8]{};
+    cudaEvent_t tev_side[2]{};  // around the dense-range update on `side`
+    bool side_timed = false;    // the last training step recorded them
 };
 
 namespace fh {

@@ -413,8 +413,13 @@ static void destroy_model(fhash_model* m) {
                   m->stamp, m->adam_tab, m->s_defer.p};
     for (void* p : ps)
         if (p) cudaFree(p);
-    if (m->tev_init)
+    if (m->tev_init) {
         for (cudaEvent_t e : m->tev) cudaEventDestroy(e);
+        for (cudaEvent_t e : m->tev_side) cudaEventDestroy(e);
+    }
+    if (m->ev_fork) cudaEventDestroy(m->ev_fork);
+    if (m->ev_join) cudaEventDestroy(m->ev_join);
+    if (m->side) cudaStreamDestroy(m->side);
     delete m;
 }
 
