@@ -1,14 +1,19 @@
-// MLP weight gradients on the tensor cores, fed by TMA: tf32 inputs for the precision form, the
-// error-compensated 3xTF32 split for the float32 form.
+// MLP weight and bias gradients on the tensor cores, fed by TMA: tf32 inputs for the precision form,
+// the error-compensated 3xTF32 split for the float32 form.
 //
-// dW_j[o][c] = sum over samples s of delta_j[o][s] * a_j[c][s].  The backward keeps deltas and
-// activations as float32 columns [feature][n], so both operands are already K-major with the samples
-// as K: TMA copies 32-sample boxes (128 bytes per feature row, 128-byte swizzle, zero fill past the
-// ends) straight into shared memory, and one thread issues tcgen05.mma kind::tf32 (M=128 with the
-// output rows zero-padded, N=64, K=8 per instruction) accumulating the CTA's whole chunk of samples in
-// 64 TMEM columns.  A 4-stage mbarrier pipeline keeps the copies ahead of the MMAs.  The four warps
-// then read the accumulator lanes back and write the CTA's partial dW; a reduction adds the partials
-// into the gradient.  Waits are bounded (2 s) and report through the model's error word.
+// dW_j[o][c] = sum over samples s of delta_j[o][s] * a_j[c][s] and db_j[o] = sum over s of delta_j[o][s].
+// The backward keeps deltas and activations as float32 columns [feature][n], so both operands are
+// already K-major with the samples as K: TMA copies 32-sample boxes (128 bytes per feature row, 128-byte
+// swizzle, zero fill past the ends) straight into shared memory, and one thread issues tcgen05.mma
+// kind::tf32 (M=128 with the output rows zero-padded, N = the inputs rounded up to 16, K=8 per
+// instruction) accumulating the CTA's whole chunk of samples in TMEM.  A 4-stage mbarrier ring keeps the
+// copies ahead; a stage is refilled one k-tile after its MMAs were issued, so the issuing thread never
+// waits on the MMAs it has just issued.  While a stage is resident every thread adds its share of the
+// delta rows into the bias sums, and in the float32 form splits its share of the rows for the 3xTF32
+// product.  A layer with a single output (the last) is a dot product per input: its CTAs accumulate it
+// on the CUDA cores in float32 and issue no MMA.  Each CTA writes its partial weight and bias gradients
+// (kDwStride layout); one reduction adds the partials into the gradient.  Waits are bounded (2 s) and
+// report through the model's error word.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -36,11 +41,29 @@ __device__ __forceinline__ float tf32_rn(float x) {
     return __uint_as_float(u & 0xFFFFE000u);
 }
 
+// hi = tf32(v) written back in place, lo = v - hi (exact in float32) to the lo buffer.
+__device__ __forceinline__ void split4(float4* h, float4* l, const float4 v) {
+    const float4 hi = make_float4(tf32_rn(v.x), tf32_rn(v.y), tf32_rn(v.z), tf32_rn(v.w));
+    *h = hi;
+    *l = make_float4(v.x - hi.x, v.y - hi.y, v.z - hi.z, v.w - hi.w);
+}
+
+// Sum over the 8 consecutive lanes that share a staged row (lanes differing in bits 0-2).
+__device__ __forceinline__ float sum8(float v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    return v;
+}
+
 // SPLIT3 (the float32 form): every staged value a is split in shared memory into hi = tf32(a) and
-// lo = a - hi (exact in float32), and each K step issues hi*hi + hi*lo + lo*hi (the lo*lo term is below
-// float32 rounding): the error-compensated "3xTF32" product of Ootomo and Yokota (2022), which keeps the
-// weight gradients at float32 accuracy on the tensor cores.  Without it (the precision form) the
-// tensor cores read the float32 inputs as tf32.
+// lo = a - hi, and each K step issues hi*hi + hi*lo + lo*hi (the lo*lo term is below float32 rounding):
+// the error-compensated "3xTF32" product of Ootomo and Yokota (2022), which keeps the weight gradients
+// at float32 accuracy on the tensor cores.  Without it (the precision form) the tensor cores read the
+// float32 inputs as tf32.
+//
+// Staged rows: a tile row is 128 bytes (8 float4 chunks, permuted within the row by the swizzle), so
+// float4 number e of a tile lies in row e / 8, and thread t visits rows t/8 + 16 i (i < 4) of each tile.
 template <bool SPLIT3>
 __global__ void __launch_bounds__(128) k_dw_tc(const __grid_constant__ DwMaps M, int64_t n, int64_t chunk,
                                                float* __restrict__ partial, int* __restrict__ err) {
@@ -55,19 +78,30 @@ __global__ void __launch_bounds__(128) k_dw_tc(const __grid_constant__ DwMaps M,
     uint32_t* slot = reinterpret_cast<uint32_t*>(empty + kDwStages);
     const int t = threadIdx.x, warp = t >> 5, layer = blockIdx.y;
     const int fi = M.fi[layer], fo = M.fo[layer];
+    const bool simt = fo == 1;         // a dot product per input on the CUDA cores, no MMA
+    const int nN = (fi + 15) / 16 * 16;  // MMA N
     const int64_t s0 = blockIdx.x * chunk, s1 = min(n, s0 + chunk);
     const int nk = s1 > s0 ? (int)((s1 - s0 + 31) / 32) : 0;
 
-    if (warp == 0) tc::tmem_alloc(slot, 64);
+    if (!simt && warp == 0) tc::tmem_alloc(slot, 64);
     if (t == 0) {
         for (int s = 0; s < kDwStages; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
         tc::fence_mbar_init();
     }
+    if (SPLIT3 && !simt) {
+        // the lo halves of the padding rows (A rows >= fo, B rows >= fi), which the split never writes
+        const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int s = 0; s < kDwStages; ++s) {
+            float4* la = reinterpret_cast<float4*>(loA + s * kDwTileA);
+            float4* lb = reinterpret_cast<float4*>(loB + s * kDwTileB);
+            for (int e = fo * 8 + t; e < kDwTileA / 16; e += 128) la[e] = z;
+            for (int e = fi * 8 + t; e < kDwTileB / 16; e += 128) lb[e] = z;
+        }
+    }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tmem = *slot;
-    bool bad = false;
+    const uint32_t tmem = simt ? 0u : *slot;
     const void* mapA = &M.a[layer];
     const void* mapB = &M.b[layer];
     auto load = [&](int kt) {
@@ -77,147 +111,126 @@ __global__ void __launch_bounds__(128) k_dw_tc(const __grid_constant__ DwMaps M,
         tc::tma_load_2d(tileA + s * kDwTileA, mapA, x, 0, &full[s]);
         tc::tma_load_2d(tileB + s * kDwTileB, mapB, x, 0, &full[s]);
     };
-    constexpr uint32_t idesc = tc::idesc_tf32(128, 64);
+    const uint32_t idesc = tc::idesc_tf32(128, nN);
     const uint32_t a0 = tc::smem_addr(tileA), b0 = tc::smem_addr(tileB);
-    if (!SPLIT3) {
-        if (t == 0 && nk > 0) {
-            for (int kt = 0; kt < nk && kt < kDwStages; ++kt) load(kt);
-            for (int kt = 0; kt < nk && !bad; ++kt) {
-                const int s = kt % kDwStages;
-                const uint32_t ph = (uint32_t)(kt / kDwStages) & 1u;
-                if (!tc::mbar_wait(&full[s], ph)) { bad = true; break; }
-                tc::fence_after_sync();
+    const uint32_t la0 = tc::smem_addr(loA), lb0 = tc::smem_addr(loB);
+    float bsum[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // bias sums of A rows t/8 + 16 i
+    float dot[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // simt: dW of B rows t/8 + 16 i
+    bool bad = false;
+    int loaded = 0, consumed = 0, issued = 0;  // thread 0: copies issued, waited for; MMA batches committed
+    if (t == 0)
+        for (; loaded < nk && loaded < kDwStages; ++loaded) load(loaded);
+    for (int kt = 0; kt < nk; ++kt) {
+        const int s = kt % kDwStages;
+        const uint32_t ph = (uint32_t)(kt / kDwStages) & 1u;
+        const bool ok = tc::mbar_wait(&full[s], ph);
+        if (__syncthreads_or(!ok || bad)) { bad = true; break; }
+        consumed = kt + 1;
+        float4* ha = reinterpret_cast<float4*>(tileA + s * kDwTileA);
+        float4* hb = reinterpret_cast<float4*>(tileB + s * kDwTileB);
+        float4* la = reinterpret_cast<float4*>(loA + s * kDwTileA);
+        float4* lb = reinterpret_cast<float4*>(loB + s * kDwTileB);
+        // delta rows (< fo): bias sums, and the split
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk)
-                    tc::mma_tf32(tmem, tc::sdesc_sw128(a0 + s * kDwTileA + kk * 32), tc::sdesc_sw128(b0 + s * kDwTileB + kk * 32),
-                                 idesc, (kt > 0 || kk > 0) ? 1u : 0u);
-                tc::mma_commit(&empty[s]);
-                if (kt + kDwStages < nk) {
-                    if (!tc::mbar_wait(&empty[s], ph)) { bad = true; break; }
-                    load(kt + kDwStages);
+        for (int i = 0; i < 4; ++i) {
+            const int e = t + 128 * i;
+            if (e < fo * 8) {
+                const float4 v = ha[e];
+                bsum[i] += (v.x + v.y) + (v.z + v.w);
+                if (SPLIT3 && !simt) split4(ha + e, la + e, v);
+            }
+        }
+        // activation rows (< fi): the split, or the single output's dot products
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int e = t + 128 * i;
+            if (e < fi * 8) {
+                const float4 v = hb[e];
+                if (simt) {
+                    // stored chunk e & 7 of row r holds samples 4j .. 4j+3, j = (e & 7) ^ (r & 7); the delta
+                    // row is row 0 of A, whose chunks are not permuted
+                    const float4 d = ha[(e & 7) ^ ((e >> 3) & 7)];
+                    dot[i] = fmaf(v.x, d.x, fmaf(v.y, d.y, fmaf(v.z, d.z, fmaf(v.w, d.w, dot[i]))));
+                } else if (SPLIT3) {
+                    split4(hb + e, lb + e, v);
                 }
             }
-            if (!bad) {  // every MMA has completed once the last commit has arrived
-                const int kl = nk - 1;
-                if (!tc::mbar_wait(&empty[kl % kDwStages], (uint32_t)(kl / kDwStages) & 1u)) bad = true;
-            }
-            if (bad) raise_error(err, 0x7C06);
         }
-    } else if (nk > 0) {
-        const uint32_t la0 = tc::smem_addr(loA), lb0 = tc::smem_addr(loB);
-        int loaded = 0, consumed = 0, issued = 0;  // copies issued, copies waited for, MMA batches committed
-        if (t == 0)
-            for (; loaded < nk && loaded < kDwStages; ++loaded) load(loaded);
-        for (int kt = 0; kt < nk; ++kt) {
-            const int s = kt % kDwStages;
-            const uint32_t ph = (uint32_t)(kt / kDwStages) & 1u;
-            const bool ok = tc::mbar_wait(&full[s], ph);
-            if (__syncthreads_or(!ok)) { bad = true; break; }
-            consumed = kt + 1;
-            // split the stage in place: tile <- hi, lo buffer <- a - hi (same swizzled positions)
-            float4* ha = reinterpret_cast<float4*>(tileA + s * kDwTileA);
-            float4* hb = reinterpret_cast<float4*>(tileB + s * kDwTileB);
-            float4* la = reinterpret_cast<float4*>(loA + s * kDwTileA);
-            float4* lb = reinterpret_cast<float4*>(loB + s * kDwTileB);
-            for (int e = t; e < (kDwTileA + kDwTileB) / 16; e += blockDim.x) {
-                float4* h = e < kDwTileA / 16 ? ha + e : hb + (e - kDwTileA / 16);
-                float4* l = e < kDwTileA / 16 ? la + e : lb + (e - kDwTileA / 16);
-                const float4 v = *h;
-                const float4 hi = make_float4(tf32_rn(v.x), tf32_rn(v.y), tf32_rn(v.z), tf32_rn(v.w));
-                *h = hi;
-                *l = make_float4(v.x - hi.x, v.y - hi.y, v.z - hi.z, v.w - hi.w);
-            }
-            tc::fence_async_smem();  // the generic-proxy stores become visible to the tensor cores
-            tc::fence_before_sync();
-            __syncthreads();
-            tc::fence_after_sync();
-            if (t == 0) {
+        if (SPLIT3 && !simt) tc::fence_async_smem();  // the generic-proxy stores become visible to the MMAs
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (t == 0) {
+            if (!simt) {
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
                     const uint64_t ah = tc::sdesc_sw128(a0 + s * kDwTileA + kk * 32), bh = tc::sdesc_sw128(b0 + s * kDwTileB + kk * 32);
-                    const uint64_t al = tc::sdesc_sw128(la0 + s * kDwTileA + kk * 32), bl = tc::sdesc_sw128(lb0 + s * kDwTileB + kk * 32);
                     tc::mma_tf32(tmem, ah, bh, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
-                    tc::mma_tf32(tmem, ah, bl, idesc, 1u);
-                    tc::mma_tf32(tmem, al, bh, idesc, 1u);
+                    if (SPLIT3) {
+                        const uint64_t al = tc::sdesc_sw128(la0 + s * kDwTileA + kk * 32), bl = tc::sdesc_sw128(lb0 + s * kDwTileB + kk * 32);
+                        tc::mma_tf32(tmem, ah, bl, idesc, 1u);
+                        tc::mma_tf32(tmem, al, bh, idesc, 1u);
+                    }
                 }
                 tc::mma_commit(&empty[s]);
                 issued = kt + 1;
-                if (loaded < nk) {
-                    if (!tc::mbar_wait(&empty[s], ph)) bad = true;  // stage s free again: refill it
+                // refill the stage of the previous k-tile, whose MMAs were issued a whole stage ago
+                if (kt > 0 && loaded < nk) {
+                    const int kp = kt - 1;
+                    if (!tc::mbar_wait(&empty[kp % kDwStages], (uint32_t)(kp / kDwStages) & 1u)) bad = true;
                     else load(loaded++);
                 }
+            } else if (loaded < nk) {
+                load(loaded++);  // every thread has read stage s
             }
-            if (__syncthreads_or(bad)) { bad = true; break; }
         }
-        if (t == 0) {
-            // wait (bounded) for the last committed batch, so that no MMA is in flight when TMEM is freed,
-            // and for every copy issued but not waited for, so that none lands after the CTA has left
-            if (issued > 0) {
-                const int kl = issued - 1;
-                if (!tc::mbar_wait(&empty[kl % kDwStages], (uint32_t)(kl / kDwStages) & 1u)) bad = true;
-            }
-            for (int k = consumed; k < loaded; ++k) tc::mbar_wait(&full[k % kDwStages], (uint32_t)(k / kDwStages) & 1u);
-            if (bad) raise_error(err, 0x7C06);
+    }
+    if (t == 0) {
+        // wait (bounded) for the last committed batch, so that no MMA is in flight when TMEM is freed, and
+        // for every copy issued but not waited for, so that none lands after the CTA has left
+        if (issued > 0) {
+            const int kl = issued - 1;
+            if (!tc::mbar_wait(&empty[kl % kDwStages], (uint32_t)(kl / kDwStages) & 1u)) bad = true;
         }
+        for (int k = consumed; k < loaded; ++k) tc::mbar_wait(&full[k % kDwStages], (uint32_t)(k / kDwStages) & 1u);
+        if (bad) raise_error(err, 0x7C06);
     }
     tc::fence_before_sync();
     const int any_bad = __syncthreads_or(bad);
     tc::fence_after_sync();
-    float* out = partial + ((int64_t)blockIdx.x * gridDim.y + layer) * 4096;
+    float* out = partial + ((int64_t)blockIdx.x * gridDim.y + layer) * kDwStride;
     if (!any_bad) {
-        const int o = warp * 32 + (t & 31);  // TMEM lane = output row
-        float v[32];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 32 * h, v);
-            tc::tmem_ld_wait();
-            if (o < fo) {
+        for (int i = 0; i < 4; ++i) {
+            const int r = (t >> 3) + 16 * i;
+            const float b = sum8(bsum[i]);
+            if ((t & 7) == 0 && r < fo) out[fo * fi + r] = b;
+            if (simt) {
+                const float d = sum8(dot[i]);
+                if ((t & 7) == 0 && r < fi) out[r] = d;
+            }
+        }
+        if (!simt) {
+            const int o = warp * 32 + (t & 31);  // TMEM lane = output row
+            float v[32];
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const int c = 32 * h + q;
-                    if (c < fi) out[o * fi + c] = nk > 0 ? v[q] : 0.0f;
+            for (int h = 0; h < 2; ++h) {
+                if (32 * h >= nN) break;
+                tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 32 * h, v);
+                tc::tmem_ld_wait();
+                if (o < fo) {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        const int c = 32 * h + q;
+                        if (c < fi) out[o * fi + c] = nk > 0 ? v[q] : 0.0f;
+                    }
                 }
             }
         }
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, 64);
-}
-
-// grad[e] += sum over chunks of partial[chunk][layer][e], e < fo*fi.
-__global__ void k_dw_tc_reduce(const float* __restrict__ partial, int nchunk, int nlayers, int layer, int ne,
-                               float* __restrict__ grad) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= ne) return;
-    float s = 0.0f;
-    for (int c = 0; c < nchunk; ++c) s += partial[((int64_t)c * nlayers + layer) * 4096 + e];
-    grad[e] += s;
-}
-
-// Bias gradients, two deterministic stages: part[o][c] = sum of delta[o][s] over chunk c (64 chunks),
-// then grad[o] += sum over c.
-constexpr int kRowChunks = 64;
-__global__ void k_rowsum_part(const float* __restrict__ d, int64_t n, float* __restrict__ part) {
-    const int o = blockIdx.x, c = blockIdx.y;
-    const int64_t per = (n + kRowChunks - 1) / kRowChunks, s0 = c * per, s1 = min(n, s0 + per);
-    float acc = 0.0f;
-    for (int64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) acc += d[(int64_t)o * n + s];
-    __shared__ float red[256];
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w; w >>= 1) {
-        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) part[o * kRowChunks + c] = red[0];
-}
-__global__ void k_rowsum_final(const float* __restrict__ part, int fo, float* __restrict__ grad) {
-    const int o = blockIdx.x * blockDim.x + threadIdx.x;
-    if (o >= fo) return;
-    float s = 0.0f;
-    for (int c = 0; c < kRowChunks; ++c) s += part[o * kRowChunks + c];
-    grad[o] += s;
+    if (!simt && warp == 0) tc::tmem_dealloc(tmem, 64);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -247,20 +260,19 @@ static bool make_map(CUtensorMap* m, const float* base, int64_t n, int rows, int
     return r == CUDA_SUCCESS;
 }
 
-// Weight and bias gradients of every layer from activations `acts` and deltas `dl` (column-major,
-// n samples).  Returns false (nothing launched) when the tensor-core path does not apply: n not a
-// multiple of 4 (row strides must be 16-byte multiples) or no tensor-map encoder.
+// Partial weight and bias gradients of every layer (kDwStride layout, *nchunk_out chunks) from
+// activations `acts` and deltas `dl` (column-major, n samples).  Returns false (nothing launched) when
+// the tensor-core path does not apply: n not a multiple of 4 (row strides must be 16-byte multiples),
+// fewer than 32 samples, a layer wider than 64 or no tensor-map encoder.
 bool launch_dw_tc(fhash_model* m, const float* acts, const float* dl, int64_t n, float* wpart, size_t wpart_bytes,
-                  cudaStream_t st, cudaError_t* err, bool split3) {
+                  int* nchunk_out, cudaStream_t st, cudaError_t* err, bool split3) {
     *err = cudaSuccess;
     const MlpShape& sh = m->mlp;
     const int W = sh.width, nl = sh.nh + 1;
-    if (n % 4 != 0 || n < 32 || !tensor_map_encoder()) return false;
+    if (n % 4 != 0 || n < 32 || W > 64 || sh.in > 64 || !tensor_map_encoder()) return false;
     const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>((n + 2047) / 2048, (int64_t)num_sms()));
     const int64_t chunk = ((n + nchunk - 1) / nchunk + 31) / 32 * 32;
-    const size_t dw_floats = (size_t)nchunk * nl * 4096;
-    if ((dw_floats + (size_t)64 * kRowChunks) * 4 > wpart_bytes) return false;
-    float* rpart = wpart + dw_floats;
+    if ((size_t)nchunk * nl * kDwStride * 4 > wpart_bytes) return false;
     DwMaps M;
     memset(&M, 0, sizeof M);
     for (int j = 0; j < nl; ++j) {
@@ -281,14 +293,7 @@ bool launch_dw_tc(fhash_model* m, const float* acts, const float* dl, int64_t n,
             k_dw_tc<false><<<dim3(nchunk, nl), 128, smem, st>>>(M, n, chunk, wpart, m->err_word);
         e = cudaGetLastError();
     }
-    float* gm = m->grad + m->n_table;
-    for (int j = 0; j < nl && e == cudaSuccess; ++j) {
-        const int fi = j == 0 ? sh.in : W, fo = j == sh.nh ? 1 : W;
-        k_dw_tc_reduce<<<(fo * fi + 255) / 256, 256, 0, st>>>(wpart, nchunk, nl, j, fo * fi, gm + sh.w_off[j]);
-        k_rowsum_part<<<dim3(fo, kRowChunks), 256, 0, st>>>(dl + (int64_t)j * W * n, n, rpart);
-        k_rowsum_final<<<1, 64, 0, st>>>(rpart, fo, gm + sh.b_off[j]);
-        e = cudaGetLastError();
-    }
+    *nchunk_out = nchunk;
     *err = e;
     return true;
 }

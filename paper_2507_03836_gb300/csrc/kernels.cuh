@@ -113,6 +113,10 @@ __global__ void k_encode(const __grid_constant__ Levels lv, const float* __restr
 // are runtime values and no thread reads another thread's column (no barriers between layers).
 // Weights are staged once per block, transposed (Wt[in][out]) for the forward pass and row-major
 // (W[out][in]) for the backward pass, so both inner loops read float4 broadcasts.
+// Weight-gradient partials: partial[(chunk * layers + layer) * kDwStride + e], e < fo*fi the weights
+// (row-major [fo][fi]), fo*fi + o the biases.
+constexpr int kDwStride = 64 * 64 + 64;
+
 constexpr int TB = 128;  // threads (= samples) per block
 
 struct MlpSmemLayout {

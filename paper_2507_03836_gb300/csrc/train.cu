@@ -337,8 +337,7 @@ __global__ void __launch_bounds__(256) k_mlp_bwd_t(const __grid_constant__ MlpSh
 // owns dW[4ob..4ob+3][4ib..4ib+3] and, when ib == 0, db of its rows.  Slabs of 32 samples are staged in
 // shared memory sample-major (sd[c][o], sa[c][i]), double-buffered through registers, so each thread
 // reads one float4 of deltas and one float4 of activations per sample: 16 FMAs per 2 shared loads.
-// partial[(chunk * layers + layer) * kDwStride + e]: e < fo*fi the weights, fo*fi + o the biases.
-constexpr int kDwStride = 64 * 64 + 64;
+// Partials in the kDwStride layout.
 struct DwLayers {
     const float* a[FHASH_MAX_HIDDEN + 1];
     const float* d[FHASH_MAX_HIDDEN + 1];
@@ -436,7 +435,7 @@ __global__ void k_loss2(const double* __restrict__ partial, int nb, int64_t n, d
 
 cudaError_t run_tc_any(fhash_model* m, bool train, FusedArgs& a);
 bool launch_dw_tc(fhash_model* m, const float* acts, const float* dl, int64_t n, float* wpart, size_t wpart_bytes,
-                  cudaStream_t st, cudaError_t* err, bool split3);
+                  int* nchunk_out, cudaStream_t st, cudaError_t* err, bool split3);
 
 template <int F, int LAYOUT>
 static cudaError_t scatter_run(fhash_model* m, const ScatterPlan& Pp, const ScatterPlan& Pf, int bp, int bf,
@@ -523,7 +522,7 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
     // weight-gradient chunks: about 4 blocks per SM over all layers, at least 512 samples each
     const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>((n + 511) / 512, (int64_t)num_sms() * 4 / nl));
     const int64_t chunk = ((n + nchunk - 1) / nchunk + 31) / 32 * 32;
-    const size_t tc_part = ((size_t)num_sms() * nl * 4096 + 64 * 64) * 4;
+    const size_t tc_part = (size_t)num_sms() * nl * kDwStride * 4;
     FH_TRY(grow(m, m->s_partial, std::max((size_t)nchunk * nl * kDwStride * 4, tc_part) + (size_t)nb * 8 + 64));
     float* acts = (float*)m->s_acts.p;
     float* gy = (float*)m->s_gacts.p;
@@ -576,17 +575,9 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
         case 8: FH_CUDA(scatter_launch<8>(m, coords, n, denc, n, 1, st)); break;
     }
     tev_record(m, TEV_SCATTER, st);
-    // weight gradients on the tensor cores (TMA + tcgen05 kind::tf32): tf32 inputs for the bf16 form, the
-    // 3xTF32 split (float32 accuracy) for the float32 form; float32 SIMT tiles when the batch does not
-    // suit the tensor maps (n not a multiple of 4, or below 32)
-    {
-        cudaError_t e = cudaSuccess;
-        if (launch_dw_tc(m, acts, dl, n, wpart, m->s_partial.bytes - wpart_off, st, &e, m->shadow == nullptr)) {
-            FH_CUDA(e);
-            tev_record(m, TEV_DW, st);
-            return FHASH_OK;
-        }
-    }
+    // weight and bias gradients on the tensor cores (TMA + tcgen05 kind::tf32): tf32 inputs for the bf16
+    // form, the 3xTF32 split (float32 accuracy) for the float32 form; float32 SIMT tiles when the batch
+    // does not suit the tensor maps (n not a multiple of 4, or below 32); then one reduction of the partials
     DwLayers Ls{};
     for (int j = 0; j < nl; ++j) {
         Ls.fi[j] = j == 0 ? sh.in : W;
@@ -594,9 +585,16 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
         Ls.a[j] = (j == 0) ? acts : acts + (int64_t)(sh.in + (j - 1) * W) * n;
         Ls.d[j] = dl + (int64_t)j * W * n;
     }
-    k_dw_tiles<<<dim3(nchunk, nl), 256, 0, st>>>(Ls, n, chunk, wpart);
-    FH_CUDA(cudaGetLastError());
-    k_dw_reduce2<<<dim3((kDwStride + 255) / 256, nl), 256, 0, st>>>(wpart, nchunk, Ls, sh, m->grad + m->n_table);
+    int nparts = nchunk;
+    cudaError_t e = cudaSuccess;
+    if (launch_dw_tc(m, acts, dl, n, wpart, m->s_partial.bytes - wpart_off, &nparts, st, &e, m->shadow == nullptr)) {
+        FH_CUDA(e);
+    } else {
+        nparts = nchunk;
+        k_dw_tiles<<<dim3(nchunk, nl), 256, 0, st>>>(Ls, n, chunk, wpart);
+        FH_CUDA(cudaGetLastError());
+    }
+    k_dw_reduce2<<<dim3((kDwStride + 255) / 256, nl), 256, 0, st>>>(wpart, nparts, Ls, sh, m->grad + m->n_table);
     FH_CUDA(cudaGetLastError());
     tev_record(m, TEV_DW, st);
     return FHASH_OK;
