@@ -945,9 +945,8 @@ def main():
                                      "advect-128^3x32 (%.0f B), times the groups of this launch" % REPLAY_DRAM_BYTES_PER_GROUP,
                         hbm_algorithmic_frac=phases[top]["frac"])
     value = job_rate(world, B * K, elapsed)
-    nh = w["hidden"]
     deferred = adam_stats["first_deferred_level"] >= 0
-    per_step = (7 if not bf16 else 6) + 3 * (nh + 1) + (3 + 3 if deferred else 1)
+    per_step = (8 if not bf16 else 7) + (3 + 3 if deferred else 1)
 
     out = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -971,8 +970,8 @@ def main():
                           "first_deferred_level": adam_stats["first_deferred_level"],
                           "deferred_params": n_deferred},
         # per step, float32: encode, MLP forward, loss, MLP backward, 2 scatters; precision form: fused
-        # forward, loss, MLP backward, 2 scatters; both: the tensor-core weight gradients and 3 reductions
-        # per layer; then the deferred catch-up (claim, sort, replay), the previous step's Adam over the
+        # forward, loss, MLP backward, 2 scatters; both: the tensor-core weight gradients and their
+        # reduction; then the deferred catch-up (claim, sort, replay), the previous step's Adam over the
         # dense ranges (2 launches) and the step's scalar record, or one dense Adam launch
         "gpu_launches": K * per_step,
         "roofline": roofline,
