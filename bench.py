@@ -36,9 +36,10 @@ ADAM_SMALL_CASE = {"workload": "advect-128^3x32", "bytes_per_param_measured": (4
 ADAM_SMALL_CASE["ratio"] = ADAM_SMALL_CASE["bytes_per_param_measured"] / ADAM_SMALL_CASE["bytes_per_param_algorithmic"]
 
 
-# DRAM traffic of k_defer_replay from one ncu capture (full set) of the kernel on advect-128^3x32 after 100
-# aging steps: 1.0437 GB read + 0.2952 GB written for 2,410,972 caught-up groups of 8 parameters.
-REPLAY_DRAM_BYTES_PER_GROUP = (1.043689e9 + 0.29517184e9) / 2410972
+# DRAM traffic of k_defer_replay per caught-up group of 32 floats, from one ncu capture of the kernel on
+# advect-128^3x32 after 100 aging steps: 0.7668 GB read + 0.5926 GB written, over the 1,473,749 groups per
+# step that the same command's live phase loop reported (algorithmic: 896 B per group).
+REPLAY_DRAM_BYTES_PER_GROUP = (0.766776832e9 + 0.59256832e9) / 1473749
 
 
 def _layout(args):
@@ -854,6 +855,7 @@ def main():
         tab_ms, dense_ms = dense_ms, side_ms
     replay_groups, replay_steps = float(np.mean(groups)), float(np.mean(gsteps))
     n_deferred = int(adam_stats["deferred_params"])
+    gsize = int(adam_stats["group_params"])
 
     # end to end through the public API: host (pinned) inputs copied in, loss read back, every step
     e0 = args.warmup + 2 * K
@@ -893,7 +895,7 @@ def main():
     # weight-gradient phases):
     #  k_adam (dense range): read p, g, m, v; write p, m, v, and the cleared g where it was not zero
     #    (+ the bf16 shadow of p in the precision form);
-    #  k_defer_replay: per caught-up 8-float group, one 32-byte sector each of p, g, m, v read and of p,
+    #  k_defer_replay: per caught-up group of G floats, G x 4 bytes each of p, g, m, v read and of p,
     #    m, v written (+16 bytes of bf16 shadow);
     #  k_encode_cols: per sample 16 corner rows of F float32 per level, the 16-byte coordinates and the
     #    L*F encoding values written;
@@ -904,9 +906,9 @@ def main():
         "k_adam": (adam_bpp * n_dense, dense_ms, "dense Adam over %d parameters (levels below the deferred ones "
                                                  "and the MLP), %.2f B/param%s" % (n_dense, adam_bpp,
                                                  "; runs beside the replay, sharing the GPU" if overlapped else "")),
-        "k_defer_replay": (replay_groups * (7 * 32 + (16 if bf16 else 0)), replay_ms,
-                           "%.0f caught-up 8-float groups per step, %.1f replayed steps each on average"
-                           % (replay_groups, replay_steps / max(replay_groups, 1))),
+        "k_defer_replay": (replay_groups * gsize * (7 * 4 + (2 if bf16 else 0)), replay_ms,
+                           "%.0f caught-up groups of %d floats per step, %.1f replayed steps each on average"
+                           % (replay_groups, gsize, replay_steps / max(replay_groups, 1))),
         "k_encode_cols": (B * (16 * L * F * 4 + 16 + L * F * 4), encode_ms,
                           "%d samples x (16 x %d levels x %d floats gathered + 16 B coordinates + %d floats written)"
                           % (B, L, F, L * F)),
@@ -936,11 +938,11 @@ def main():
         # memory traffic grows with the groups it catches up, not with their replay lengths).
         sm_mhz = peaks.get("sm_max_mhz", 2070.0)
         peak_steps = 152 * 16 * sm_mhz * 1e6 / 2 / 1e9
-        steps_s = replay_steps * 8 / (replay_ms / 1e3) / 1e9
+        steps_s = replay_steps * gsize / (replay_ms / 1e3) / 1e9
         roofline.update(bound="alu", unit="G parameter-steps/s", achieved=steps_s, peak=peak_steps,
                         frac=steps_s / peak_steps, peak_source="derived: 152 SMs x 16 special-function results "
                         "per clock x %.0f MHz / 2 per parameter-step" % sm_mhz,
-                        traffic=REPLAY_DRAM_BYTES_PER_GROUP * replay_groups,
+                        traffic=REPLAY_DRAM_BYTES_PER_GROUP * replay_groups if REPLAY_DRAM_BYTES_PER_GROUP else None,
                         traffic_note="ncu dram__bytes_read.sum + dram__bytes_write.sum per caught-up group on "
                                      "advect-128^3x32 (%.0f B), times the groups of this launch" % REPLAY_DRAM_BYTES_PER_GROUP,
                         hbm_algorithmic_frac=phases[top]["frac"])

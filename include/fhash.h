@@ -300,14 +300,14 @@ fhash_status fhash_train_step(fhash_model* model, const float* coords, const flo
  * whose gradient is zero moves every parameter by a fixed float32 map of (parameter, first moment,
  * second moment) that depends only on that step's scalars.  In fhash_train_step the table levels with
  * at least min_level_rows rows (and every finer level) do not take that map every step: each group of
- * 8 consecutive parameters remembers the last step applied to it, and when a batch is about to read
+ * 32 consecutive parameters remembers the last step applied to it, and when a batch is about to read
  * it (or any other call touches the state) it replays the missed steps, the first with its pending
  * gradient and the others with a zero gradient, with the same float32 operations in the same order as
  * the dense update.  Parameters, gradients and moments are therefore bit-identical to dense Adam at
  * every point a caller can observe, while a step streams only the groups its batch touches instead of
  * every parameter.  Coarser levels and the MLP take the dense update every step.
  *  min_level_rows: 0 turns deferral off; the default is 2^25 (33,554,432 rows).  Changing it first
- *  brings every group to the current step (a kernel on `stream`).  The state costs 4 bytes per 8
+ *  brings every group to the current step (a kernel on `stream`).  The state costs 4 bytes per 32
  *  deferred parameters (allocated at the first deferred step) and 32 bytes per step taken.
  */
 #define FHASH_ADAM_DEFER_DEFAULT_ROWS (1ull << 25)
@@ -328,6 +328,7 @@ typedef struct {
                                         forward), MLP forward + loss + backward, table scatter, weight
                                         gradients, dense Adam (with deferred levels: only the recording
                                         of the step's scalars; see last_side_ms) */
+    uint32_t group_params;           /* parameters per deferral group (one stamp, caught up together) */
     float last_side_ms;              /* with timing on and deferred levels: the dense update of the levels
                                         below the deferred ones and the MLP, which a deferred step leaves to
                                         the next step; that step runs it on a second stream beside its

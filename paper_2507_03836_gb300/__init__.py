@@ -85,7 +85,7 @@ class fhash_adam_stats(ctypes.Structure):
     _fields_ = [("first_deferred_level", ctypes.c_int32), ("deferred_params", ctypes.c_uint64),
                 ("step", ctypes.c_int64), ("clean_step", ctypes.c_int64), ("last_replayed_groups", ctypes.c_uint64),
                 ("last_replayed_steps", ctypes.c_uint64), ("last_ms", ctypes.c_float * 7),
-                ("last_side_ms", ctypes.c_float)]
+                ("group_params", ctypes.c_uint32), ("last_side_ms", ctypes.c_float)]
 
 
 ADAM_DEFER_DEFAULT_ROWS = 1 << 25
@@ -335,7 +335,7 @@ def fhash_get_adam_stats(model):
     return {"first_deferred_level": st.first_deferred_level, "deferred_params": st.deferred_params,
             "step": st.step, "clean_step": st.clean_step, "last_replayed_groups": st.last_replayed_groups,
             "last_replayed_steps": st.last_replayed_steps, "last_ms": list(st.last_ms),
-            "last_side_ms": st.last_side_ms}
+            "group_params": st.group_params, "last_side_ms": st.last_side_ms}
 
 
 def fhash_coreset_build(model, volume, key_frames, stream=None):

@@ -5,8 +5,8 @@
 //
 // Deferred: a step whose gradient is zero is a fixed float32 map of (p, m, v) that depends only on
 // that step's scalars (beta1, beta2, lr / bc1, 1 / sqrt(bc2), eps).  For the table levels whose rows a
-// batch rarely touches (the HBM-resident fine levels), that map is not applied every step: each
-// 8-float group keeps a stamp s, meaning "p, m, v are current at step s and the gradient buffer holds
+// batch rarely touches (the HBM-resident fine levels), that map is not applied every step: each group
+// of kGroup consecutive floats keeps a stamp s, meaning "p, m, v are current at step s and the gradient buffer holds
 // the gradient of step s + 1".  Before the gathers of step k, every group the batch will read is
 // brought to step k - 1 by replaying, with the same float32 operations in the same order, step s + 1
 // with its pending gradient and steps s + 2 .. k - 1 with a zero gradient (the scalars of every step
@@ -126,6 +126,13 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ P, float* __re
 }
 
 // ------------------------------------------------------------------ deferred form
+// Floats per deferral group (one stamp each; a claim catches up the whole group).  32 floats = one
+// 128-byte line of each state vector: a batch's corners then fall into about half as many groups as
+// with 8-float groups, and the replay's random accesses (p, g, m, v read, p, m, v, g written) move whole
+// lines, which a random access costs nearly the same as one sector.  kLanes lanes replay a group, 8
+// floats each.
+constexpr uint32_t kGroup = 32;
+constexpr uint32_t kLanes = kGroup / 8;
 constexpr int kBuckets = 64;
 
 // Counters of one deferred step (device memory, cleared before the claim).
@@ -146,7 +153,7 @@ __device__ __forceinline__ uint32_t len_bucket(uint32_t len) {
 
 struct DeferArgs {
     uint32_t* stamp;     // per group of the deferred range
-    uint64_t q0, q1;     // deferred groups [q0, q1) (group q = floats 8q .. 8q + 7 of the flat vector)
+    uint64_t q0, q1;     // deferred groups [q0, q1) (group q = floats kGroup q .. kGroup q + kGroup - 1)
     uint32_t target;     // k - 1: the step every read group must reach
     uint32_t clean;      // every group is at least this current
     int32_t l0;          // first deferred level
@@ -183,7 +190,7 @@ __global__ void __launch_bounds__(256) k_defer_claim(const __grid_constant__ Lev
         for (int c = 0; c < 16; ++c) {
             const uint64_t r = corner_row<LAYOUT>(k, c);
             if (LAYOUT == 2 && r == kInactiveRow) continue;
-            const uint64_t g = (r * (uint64_t)F) >> 3;
+            const uint64_t g = (r * (uint64_t)F) / kGroup;
             if (g == prev || g < d.q0 || g >= d.q1) continue;
             prev = g;
             const uint32_t old = atomicMax(d.stamp + (g - d.q0), d.target);
@@ -263,7 +270,7 @@ __global__ void __launch_bounds__(256) k_defer_bin(const uint2* __restrict__ ite
     if (have) binned[off[b] + base[b] + r] = it;
 }
 
-// Replays steps from + 1 .. to of the 8-float group starting at float index f: the first with the
+// Replays steps from + 1 .. to of the 8 floats starting at float index f: the first with the
 // pending gradient, the rest with a zero gradient; clears the gradient (where it is not zero already)
 // and refreshes the bf16 shadow.
 template <bool SHADOW>
@@ -310,16 +317,17 @@ __device__ __forceinline__ void replay_group(float* __restrict__ P, float* __res
     }
 }
 
-// The claimed groups in bucket order, one per thread (a persistent grid walks the list).
+// The claimed groups in bucket order, kLanes consecutive threads per group, 8 floats each (a persistent
+// grid walks the list).
 template <bool SHADOW>
 __global__ void __launch_bounds__(256, 3) k_defer_replay(const uint2* __restrict__ binned, const DeferCtr* __restrict__ ctr,
                                                       float* __restrict__ P, float* __restrict__ G, float* __restrict__ M,
                                                       float* __restrict__ V, __nv_bfloat16* __restrict__ shadow,
                                                       uint64_t f0, const AdamScal* __restrict__ tab, uint32_t target) {
-    const uint32_t n = ctr->count;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint2 it = binned[i];
-        replay_group<SHADOW>(P, G, M, V, shadow, f0 + 8ull * it.x, it.y, target, tab);
+    const uint64_t n = (uint64_t)ctr->count * kLanes;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint2 it = binned[i / kLanes];
+        replay_group<SHADOW>(P, G, M, V, shadow, f0 + (uint64_t)kGroup * it.x + 8 * (i % kLanes), it.y, target, tab);
     }
 }
 
@@ -330,9 +338,11 @@ __global__ void __launch_bounds__(256, 3) k_defer_flush(const uint32_t* __restri
                                                      float* __restrict__ V, __nv_bfloat16* __restrict__ shadow,
                                                      uint64_t f0, const AdamScal* __restrict__ tab, uint32_t clean,
                                                      uint32_t k) {
-    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < ngroups; q += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t n = ngroups * kLanes;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t q = i / kLanes;
         const uint32_t from = max(stamp[q], clean);
-        if (from < k) replay_group<SHADOW>(P, G, M, V, shadow, f0 + 8ull * q, from, k, tab);
+        if (from < k) replay_group<SHADOW>(P, G, M, V, shadow, f0 + (uint64_t)kGroup * q + 8 * (i % kLanes), from, k, tab);
     }
 }
 
@@ -382,7 +392,7 @@ fhash_status launch_adam(fhash_model* m, const fhash_adam* ad, cudaStream_t st) 
 }
 
 // Levels from the first one whose rows (and every finer level's) reach min_rows; the deferred range is
-// the 8-float groups wholly inside those levels' tables.
+// the kGroup-float groups wholly inside those levels' tables.
 static void plan_deferral(fhash_model* m) {
     m->defer_level = -1;
     m->defer_lo = m->defer_hi = 0;
@@ -391,7 +401,7 @@ static void plan_deferral(fhash_model* m) {
     while (l0 > 0 && m->lv.lv[l0 - 1].nrows >= m->defer_min_rows) --l0;
     if (l0 >= m->lv.L) return;
     const uint64_t F = (uint64_t)m->lv.F;
-    const uint64_t lo = (m->lv.lv[l0].base * F + 7) / 8 * 8, hi = m->n_table / 8 * 8;
+    const uint64_t lo = (m->lv.lv[l0].base * F + kGroup - 1) / kGroup * kGroup, hi = m->n_table / kGroup * kGroup;
     if (lo >= hi) return;
     m->defer_level = l0;
     m->defer_lo = lo;
@@ -444,8 +454,8 @@ static fhash_status fork_pending_dense(fhash_model* m, cudaStream_t st) {
 fhash_status settle_deferred(fhash_model* m, cudaStream_t st) {
     if (m->dense_pending) FH_TRY(apply_pending_dense(m, st));
     if (!m->dirty) return FHASH_OK;
-    const uint64_t ng = (m->planned_hi - m->planned_lo) / 8;
-    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((ng + 255) / 256, (uint64_t)num_sms() * 64));
+    const uint64_t ng = (m->planned_hi - m->planned_lo) / kGroup;
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((ng * kLanes + 255) / 256, (uint64_t)num_sms() * 64));
     const AdamScal* tab = (const AdamScal*)m->adam_tab;
     if (m->shadow)
         k_defer_flush<true><<<grid, 256, 0, st>>>(m->stamp, ng, m->param, m->grad, m->adam_m, m->adam_v, m->shadow,
@@ -484,7 +494,7 @@ static fhash_status catch_up(fhash_model* m, const float* coords, int64_t n, cud
     const uint32_t target = (uint32_t)m->step;
     if (target == (uint32_t)m->clean_step) return FHASH_OK;  // nothing is behind the previous step
     const int nd = m->lv.L - m->defer_level;
-    const uint64_t ng = (m->defer_hi - m->defer_lo) / 8;
+    const uint64_t ng = (m->defer_hi - m->defer_lo) / kGroup;
     const uint64_t cap = std::min<uint64_t>((uint64_t)n * nd * 16, ng);
     const size_t ctr_bytes = (sizeof(DeferCtr) + 255) / 256 * 256;
     FH_TRY(grow(m, m->s_defer, ctr_bytes + 2 * cap * sizeof(uint2)));
@@ -494,8 +504,8 @@ static fhash_status catch_up(fhash_model* m, const float* coords, int64_t n, cud
     FH_CUDA(cudaMemsetAsync(ctr, 0, sizeof(DeferCtr), st));
     DeferArgs d{};
     d.stamp = m->stamp;
-    d.q0 = m->defer_lo / 8;
-    d.q1 = m->defer_hi / 8;
+    d.q0 = m->defer_lo / kGroup;
+    d.q1 = m->defer_hi / kGroup;
     d.target = target;
     d.clean = (uint32_t)m->clean_step;
     d.l0 = m->defer_level;
@@ -548,14 +558,14 @@ fhash_status launch_train_step(fhash_model* m, const float* coords, const float*
         tev_record(m, TEV_ADAM, st);
         return FHASH_OK;
     }
-    if (!m->stamp || m->stamp_groups != (m->defer_hi - m->defer_lo) / 8) {
+    if (!m->stamp || m->stamp_groups != (m->defer_hi - m->defer_lo) / kGroup) {
         FH_TRY(settle_deferred(m, st));  // the deferred range changed: start from current state
         if (m->stamp) {
             cudaFree(m->stamp);
             m->device_bytes -= m->stamp_groups * 4;
             m->stamp = nullptr;
         }
-        m->stamp_groups = (m->defer_hi - m->defer_lo) / 8;
+        m->stamp_groups = (m->defer_hi - m->defer_lo) / kGroup;
         FH_CUDA(cudaMalloc(&m->stamp, std::max<uint64_t>(4, m->stamp_groups * 4)));
         m->device_bytes += m->stamp_groups * 4;
         FH_CUDA(cudaMemsetAsync(m->stamp, 0, m->stamp_groups * 4, st));
@@ -620,6 +630,7 @@ fhash_status fhash_get_adam_stats(fhash_model* m, fhash_adam_stats* out) {
     out->deferred_params = m->defer_hi - m->defer_lo;
     out->clean_step = m->clean_step;
     out->step = m->step;
+    out->group_params = kGroup;
     if (m->last_ctr) {
         DeferCtr c;
         FH_CUDA(cudaMemcpy(&c, m->last_ctr, sizeof c, cudaMemcpyDeviceToHost));

@@ -105,7 +105,7 @@ struct fhash_model {
     int32_t forward_path = 0;  // FHASH_FORWARD_* (precision form only)
 
     // deferred Adam (csrc/adam.cu): levels from defer_level on (those with at least defer_min_rows
-    // rows) hold 8-float groups [defer_lo/8, defer_hi/8) of the flat vectors, each with a stamp: the
+    // rows) hold groups of 32 floats [defer_lo/32, defer_hi/32) of the flat vectors, each with a stamp: the
     // step its p, m, v are current at; every group is at least clean_step-current; dirty when some
     // group is behind `step`.
     uint64_t defer_min_rows = 1ull << 25;

@@ -5,10 +5,11 @@
 // The backward keeps deltas and activations as float32 columns [feature][n], so both operands are
 // already K-major with the samples as K: TMA copies 32-sample boxes (128 bytes per feature row, 128-byte
 // swizzle, zero fill past the ends) straight into shared memory, and one thread issues tcgen05.mma
-// kind::tf32 (M=128 with the output rows zero-padded, N = the inputs rounded up to 16, K=8 per
-// instruction) accumulating the CTA's whole chunk of samples in TMEM.  A 4-stage mbarrier ring keeps the
-// copies ahead; a stage is refilled one k-tile after its MMAs were issued, so the issuing thread never
-// waits on the MMAs it has just issued.  While a stage is resident every thread adds its share of the
+// kind::tf32 (M=64: the outputs, zero-padded to 64 by the box; N = the inputs rounded up to 16; K=8 per
+// instruction) accumulating the CTA's whole chunk of samples in TMEM.  A deep mbarrier ring (10 stages
+// of 16 KB in the float32 form, 6 in the precision form) keeps enough copies in flight for HBM; a stage
+// is refilled one k-tile after its MMAs were issued, so the issuing thread never waits on the MMAs it
+// has just issued.  While a stage is resident every thread adds its share of the
 // delta rows into the bias sums, and in the float32 form splits its share of the rows for the 3xTF32
 // product.  A layer with a single output (the last) is a dot product per input: its CTAs accumulate it
 // on the CUDA cores in float32 and issue no MMA.  Each CTA writes its partial weight and bias gradients
@@ -24,9 +25,18 @@
 
 namespace fh {
 
-constexpr int kDwStages = 4;
-constexpr int kDwTileA = 128 * 128;  // bytes: 128 rows (padded outputs) x 32 float32
-constexpr int kDwTileB = 64 * 128;   // bytes: 64 rows (inputs) x 32 float32
+constexpr int kDwTileA = 64 * 128;  // bytes: 64 rows (outputs, zero-padded) x 32 float32
+constexpr int kDwTileB = 64 * 128;  // bytes: 64 rows (inputs, zero-padded) x 32 float32
+constexpr int kDwLo = 2;            // lo tiles of the float32 form: k-tile kt uses lo buffer kt % 2
+constexpr int kDwThreads = 512;     // 16 warps: the per-stage split and sums are latency-bound per warp
+constexpr int kDwPer = kDwTileA / 16 / kDwThreads;  // float4 chunks of each tile per thread
+template <bool SPLIT3>
+__host__ __device__ constexpr int dw_stages() { return SPLIT3 ? 10 : 6; }
+template <bool SPLIT3>
+constexpr int dw_smem() {
+    return 1024 + dw_stages<SPLIT3>() * (kDwTileA + kDwTileB) + (SPLIT3 ? kDwLo * (kDwTileA + kDwTileB) : 0) +
+           2 * dw_stages<SPLIT3>() * 8 + 16;
+}
 
 struct alignas(64) DwMaps {
     CUtensorMap a[FHASH_MAX_HIDDEN + 1];
@@ -56,24 +66,27 @@ __device__ __forceinline__ float sum8(float v) {
     return v;
 }
 
-// SPLIT3 (the float32 form): every staged value a is split in shared memory into hi = tf32(a) and
-// lo = a - hi, and each K step issues hi*hi + hi*lo + lo*hi (the lo*lo term is below float32 rounding):
+// SPLIT3 (the float32 form): every staged value a is split in shared memory into hi = tf32(a) (in place)
+// and lo = a - hi (into the k-tile's lo buffer), and each K step issues hi*hi + hi*lo + lo*hi (the lo*lo term is below float32 rounding):
 // the error-compensated "3xTF32" product of Ootomo and Yokota (2022), which keeps the weight gradients
 // at float32 accuracy on the tensor cores.  Without it (the precision form) the tensor cores read the
 // float32 inputs as tf32.
 //
 // Staged rows: a tile row is 128 bytes (8 float4 chunks, permuted within the row by the swizzle), so
-// float4 number e of a tile lies in row e / 8, and thread t visits rows t/8 + 16 i (i < 4) of each tile.
+// float4 number e of a tile lies in row e / 8, and thread t visits float4s t + kDwThreads i (i < kDwPer),
+// rows t/8 + (kDwThreads/8) i, of each tile; the 8 lanes sharing a row are consecutive.
+// TMEM: with M = 64, row r of the accumulator is lane 32 (r / 16) + r % 16.
 template <bool SPLIT3>
-__global__ void __launch_bounds__(128) k_dw_tc(const __grid_constant__ DwMaps M, int64_t n, int64_t chunk,
+__global__ void __launch_bounds__(kDwThreads) k_dw_tc(const __grid_constant__ DwMaps M, int64_t n, int64_t chunk,
                                                float* __restrict__ partial, int* __restrict__ err) {
+    constexpr int kDwStages = dw_stages<SPLIT3>();
     extern __shared__ uint8_t smraw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
     uint8_t* tileA = sm;
     uint8_t* tileB = sm + kDwStages * kDwTileA;
-    uint8_t* loA = tileB + kDwStages * kDwTileB;             // SPLIT3 only
-    uint8_t* loB = loA + (SPLIT3 ? kDwStages * kDwTileA : 0);
-    uint64_t* full = reinterpret_cast<uint64_t*>(loB + (SPLIT3 ? kDwStages * kDwTileB : 0));
+    uint8_t* loA = tileB + kDwStages * kDwTileB;  // SPLIT3 only: kDwLo tiles each
+    uint8_t* loB = loA + (SPLIT3 ? kDwLo * kDwTileA : 0);
+    uint64_t* full = reinterpret_cast<uint64_t*>(loB + (SPLIT3 ? kDwLo * kDwTileB : 0));
     uint64_t* empty = full + kDwStages;
     uint32_t* slot = reinterpret_cast<uint32_t*>(empty + kDwStages);
     const int t = threadIdx.x, warp = t >> 5, layer = blockIdx.y;
@@ -91,11 +104,11 @@ __global__ void __launch_bounds__(128) k_dw_tc(const __grid_constant__ DwMaps M,
     if (SPLIT3 && !simt) {
         // the lo halves of the padding rows (A rows >= fo, B rows >= fi), which the split never writes
         const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        for (int s = 0; s < kDwStages; ++s) {
+        for (int s = 0; s < kDwLo; ++s) {
             float4* la = reinterpret_cast<float4*>(loA + s * kDwTileA);
             float4* lb = reinterpret_cast<float4*>(loB + s * kDwTileB);
-            for (int e = fo * 8 + t; e < kDwTileA / 16; e += 128) la[e] = z;
-            for (int e = fi * 8 + t; e < kDwTileB / 16; e += 128) lb[e] = z;
+            for (int e = fo * 8 + t; e < kDwTileA / 16; e += kDwThreads) la[e] = z;
+            for (int e = fi * 8 + t; e < kDwTileB / 16; e += kDwThreads) lb[e] = z;
         }
     }
     tc::fence_before_sync();
@@ -111,11 +124,11 @@ __global__ void __launch_bounds__(128) k_dw_tc(const __grid_constant__ DwMaps M,
         tc::tma_load_2d(tileA + s * kDwTileA, mapA, x, 0, &full[s]);
         tc::tma_load_2d(tileB + s * kDwTileB, mapB, x, 0, &full[s]);
     };
-    const uint32_t idesc = tc::idesc_tf32(128, nN);
+    const uint32_t idesc = tc::idesc_tf32(64, nN);
     const uint32_t a0 = tc::smem_addr(tileA), b0 = tc::smem_addr(tileB);
     const uint32_t la0 = tc::smem_addr(loA), lb0 = tc::smem_addr(loB);
-    float bsum[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // bias sums of A rows t/8 + 16 i
-    float dot[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // simt: dW of B rows t/8 + 16 i
+    float bsum[kDwPer] = {};  // bias sums of the thread's A rows
+    float dot[kDwPer] = {};   // simt: dW of the thread's B rows
     bool bad = false;
     int loaded = 0, consumed = 0, issued = 0;  // thread 0: copies issued, waited for; MMA batches committed
     if (t == 0)
@@ -128,12 +141,13 @@ __global__ void __launch_bounds__(128) k_dw_tc(const __grid_constant__ DwMaps M,
         consumed = kt + 1;
         float4* ha = reinterpret_cast<float4*>(tileA + s * kDwTileA);
         float4* hb = reinterpret_cast<float4*>(tileB + s * kDwTileB);
-        float4* la = reinterpret_cast<float4*>(loA + s * kDwTileA);
-        float4* lb = reinterpret_cast<float4*>(loB + s * kDwTileB);
+        const int lo = kt % kDwLo;
+        float4* la = reinterpret_cast<float4*>(loA + lo * kDwTileA);
+        float4* lb = reinterpret_cast<float4*>(loB + lo * kDwTileB);
         // delta rows (< fo): bias sums, and the split
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int e = t + 128 * i;
+        for (int i = 0; i < kDwPer; ++i) {
+            const int e = t + kDwThreads * i;
             if (e < fo * 8) {
                 const float4 v = ha[e];
                 bsum[i] += (v.x + v.y) + (v.z + v.w);
@@ -142,8 +156,8 @@ __global__ void __launch_bounds__(128) k_dw_tc(const __grid_constant__ DwMaps M,
         }
         // activation rows (< fi): the split, or the single output's dot products
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int e = t + 128 * i;
+        for (int i = 0; i < kDwPer; ++i) {
+            const int e = t + kDwThreads * i;
             if (e < fi * 8) {
                 const float4 v = hb[e];
                 if (simt) {
@@ -167,18 +181,19 @@ __global__ void __launch_bounds__(128) k_dw_tc(const __grid_constant__ DwMaps M,
                     const uint64_t ah = tc::sdesc_sw128(a0 + s * kDwTileA + kk * 32), bh = tc::sdesc_sw128(b0 + s * kDwTileB + kk * 32);
                     tc::mma_tf32(tmem, ah, bh, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
                     if (SPLIT3) {
-                        const uint64_t al = tc::sdesc_sw128(la0 + s * kDwTileA + kk * 32), bl = tc::sdesc_sw128(lb0 + s * kDwTileB + kk * 32);
+                        const uint64_t al = tc::sdesc_sw128(la0 + lo * kDwTileA + kk * 32), bl = tc::sdesc_sw128(lb0 + lo * kDwTileB + kk * 32);
                         tc::mma_tf32(tmem, ah, bl, idesc, 1u);
                         tc::mma_tf32(tmem, al, bh, idesc, 1u);
                     }
                 }
                 tc::mma_commit(&empty[s]);
                 issued = kt + 1;
-                // refill the stage of the previous k-tile, whose MMAs were issued a whole stage ago
-                if (kt > 0 && loaded < nk) {
+                // the previous k-tile's MMAs (issued a whole stage ago) have completed before its stage is
+                // refilled and before the next k-tile's split overwrites its lo buffer
+                if (kt > 0) {
                     const int kp = kt - 1;
                     if (!tc::mbar_wait(&empty[kp % kDwStages], (uint32_t)(kp / kDwStages) & 1u)) bad = true;
-                    else load(loaded++);
+                    else if (loaded < nk) load(loaded++);
                 }
             } else if (loaded < nk) {
                 load(loaded++);  // every thread has read stage s
@@ -201,8 +216,8 @@ __global__ void __launch_bounds__(128) k_dw_tc(const __grid_constant__ DwMaps M,
     float* out = partial + ((int64_t)blockIdx.x * gridDim.y + layer) * kDwStride;
     if (!any_bad) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int r = (t >> 3) + 16 * i;
+        for (int i = 0; i < kDwPer; ++i) {
+            const int r = (t >> 3) + (kDwThreads / 8) * i;
             const float b = sum8(bsum[i]);
             if ((t & 7) == 0 && r < fo) out[fo * fi + r] = b;
             if (simt) {
@@ -210,15 +225,15 @@ __global__ void __launch_bounds__(128) k_dw_tc(const __grid_constant__ DwMaps M,
                 if ((t & 7) == 0 && r < fi) out[r] = d;
             }
         }
-        if (!simt) {
-            const int o = warp * 32 + (t & 31);  // TMEM lane = output row
+        if (!simt && warp < 4) {  // warp w reads TMEM lane quarter w
+            const int o = warp * 16 + (t & 31);  // lanes 0-15 of the warp's quarter hold rows 16 warp + 0..15
             float v[32];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 if (32 * h >= nN) break;
                 tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 32 * h, v);
                 tc::tmem_ld_wait();
-                if (o < fo) {
+                if ((t & 31) < 16 && o < fo) {
 #pragma unroll
                     for (int q = 0; q < 32; ++q) {
                         const int c = 32 * h + q;
@@ -279,18 +294,18 @@ bool launch_dw_tc(fhash_model* m, const float* acts, const float* dl, int64_t n,
         const int fi = j == 0 ? sh.in : W, fo = j == sh.nh ? 1 : W;
         const float* aj = (j == 0) ? acts : acts + (int64_t)(sh.in + (j - 1) * W) * n;
         const float* dj = dl + (int64_t)j * W * n;
-        if (!make_map(&M.a[j], dj, n, fo, 128) || !make_map(&M.b[j], aj, n, fi, 64)) return false;
+        if (!make_map(&M.a[j], dj, n, fo, 64) || !make_map(&M.b[j], aj, n, fi, 64)) return false;
         M.fi[j] = fi;
         M.fo[j] = fo;
     }
-    const int smem = 1024 + (split3 ? 2 : 1) * kDwStages * (kDwTileA + kDwTileB) + 2 * kDwStages * 8 + 16;
+    const int smem = split3 ? dw_smem<true>() : dw_smem<false>();
     const void* fn = split3 ? (const void*)k_dw_tc<true> : (const void*)k_dw_tc<false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) {
         if (split3)
-            k_dw_tc<true><<<dim3(nchunk, nl), 128, smem, st>>>(M, n, chunk, wpart, m->err_word);
+            k_dw_tc<true><<<dim3(nchunk, nl), kDwThreads, smem, st>>>(M, n, chunk, wpart, m->err_word);
         else
-            k_dw_tc<false><<<dim3(nchunk, nl), 128, smem, st>>>(M, n, chunk, wpart, m->err_word);
+            k_dw_tc<false><<<dim3(nchunk, nl), kDwThreads, smem, st>>>(M, n, chunk, wpart, m->err_word);
         e = cudaGetLastError();
     }
     *nchunk_out = nchunk;
