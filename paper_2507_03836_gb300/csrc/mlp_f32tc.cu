@@ -1,0 +1,314 @@
+// Float32 MLP of a training step on the tensor cores: forward, MSE loss and the backward data path of
+// one 128-sample tile in one CTA, every layer a tcgen05.mma kind::tf32 GEMM with the error-compensated
+// 3xTF32 split (hi*hi + hi*lo + lo*hi, Ootomo and Yokota 2022), so the results keep float32 accuracy.
+//
+// A tile's samples are the TMEM lanes and the CTA's 128 threads (thread t = sample t = lane t), so a
+// layer's accumulator row is one thread's registers after tcgen05.ld.  Every GEMM has the samples as
+// M = 128 and K-major operands in the 128-byte swizzle layout:
+//   forward layer j:   z[s][o] = sum_c a[s][c] W_j[o][c]     A = activations, B = W_j as stored;
+//   backward layer j:  p[s][c] = sum_o d[s][o] W_j[o][c]     A = deltas,      B = W_j transposed.
+// The weights of every hidden layer, both ways and split into hi and lo, are staged once per CTA; the
+// A operand of each GEMM is written by its producing epilogue (each thread its own row: the encoding
+// read from its feature-major columns, the activations, the deltas), split into hi and lo.  The ReLU
+// masks stay in registers (one bit per unit), so the backward needs no activation reloads.  Global
+// outputs are the ones the split kernels write, feature-major [row][n] and coalesced across the
+// threads: the hidden activations (for the weight gradients), the deltas of every layer and
+// d(loss)/d(encoding) (for the table scatter), plus one loss partial per CTA.
+//
+// Shapes: encoding width IN in {16, 32, 64}, hidden width 64, up to kTcMaxHidden hidden layers (the
+// weights of both directions must fit in shared memory); others take the float32 SIMT kernels.
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "kernels.cuh"
+#include "tc.cuh"
+
+namespace fh {
+
+constexpr int kMt = 128;         // samples per tile = TMEM lanes = threads
+constexpr int kMw = 64;          // hidden width handled here
+constexpr int kTcMaxHidden = 2;  // hidden layers whose weights (both directions, hi and lo) fit
+
+// Shared-memory layout (bytes from the 1024-aligned base).  A K-major operand of R rows and K floats is
+// ceil(K / 32) blocks of R x 128 bytes (8-row swizzle atoms of 1024 bytes); hi and lo copies are
+// separate regions of the same shape.
+struct TcMlpLayout {
+    int a_hi, a_lo;                                   // A: 128 rows x 64 floats (two blocks)
+    int wf_hi[kTcMaxHidden], wf_lo[kTcMaxHidden];     // forward B of layer j: 64 rows x fi_j floats
+    int wb_hi[kTcMaxHidden], wb_lo[kTcMaxHidden];     // backward B of layer j: fi_j rows x 64 floats
+    int bias, wout, bar, slot, total;
+};
+
+__host__ __device__ inline int tc_blocks(int k) { return (k + 31) / 32; }
+
+__host__ __device__ inline TcMlpLayout tc_mlp_layout(int in, int nh) {
+    TcMlpLayout L{};
+    int o = 0;
+    L.a_hi = o; o += 2 * kMt * 128;
+    L.a_lo = o; o += 2 * kMt * 128;
+    for (int j = 0; j < nh; ++j) {
+        const int fi = j == 0 ? in : kMw;
+        const int wf = tc_blocks(fi) * kMw * 128, wb = tc_blocks(kMw) * fi * 128;
+        L.wf_hi[j] = o; o += wf;
+        L.wf_lo[j] = o; o += wf;
+        L.wb_hi[j] = o; o += wb;
+        L.wb_lo[j] = o; o += wb;
+    }
+    L.bias = o; o += kTcMaxHidden * kMw * 4;
+    L.wout = o; o += kMw * 4 + 16;
+    L.bar = o; o += 16;
+    L.slot = o; o += 16;
+    L.total = o + 1024;  // alignment slack of the dynamic shared-memory base
+    return L;
+}
+
+// Byte offset of element (row r, k) in a K-major 128-byte-swizzled operand of R rows.
+__device__ __forceinline__ int sw128_off(int R, int r, int k) {
+    return (k >> 5) * R * 128 + r * 128 + ((((k & 31) >> 2) ^ (r & 7)) << 4) + ((k & 3) << 2);
+}
+
+// Round to the nearest tf32 value (10 explicit mantissa bits, ties to even), kept as float32.
+__device__ __forceinline__ float tf32_hi(float x) {
+    uint32_t u = __float_as_uint(x);
+    u += 0xFFFu + ((u >> 13) & 1u);
+    return __uint_as_float(u & 0xFFFFE000u);
+}
+
+// Writes this thread's row (row t) of an A operand: K values, hi and lo, 16 bytes at a time.
+template <int K>
+__device__ __forceinline__ void put_row(uint8_t* hi, uint8_t* lo, int t, const float (&v)[K]) {
+#pragma unroll
+    for (int c = 0; c < K / 4; ++c) {
+        const int off = (c >> 3) * kMt * 128 + t * 128 + (((c & 7) ^ (t & 7)) << 4);
+        float4 h, l;
+        h.x = tf32_hi(v[4 * c + 0]); l.x = v[4 * c + 0] - h.x;
+        h.y = tf32_hi(v[4 * c + 1]); l.y = v[4 * c + 1] - h.y;
+        h.z = tf32_hi(v[4 * c + 2]); l.z = v[4 * c + 2] - h.z;
+        h.w = tf32_hi(v[4 * c + 3]); l.w = v[4 * c + 3] - h.w;
+        *reinterpret_cast<float4*>(hi + off) = h;
+        *reinterpret_cast<float4*>(lo + off) = l;
+    }
+}
+
+// Every hidden layer's weights, split into hi and lo, in both operand forms; biases and output weights.
+__device__ __forceinline__ void stage_tc_weights(uint8_t* sm, const TcMlpLayout& L, const MlpShape& sh,
+                                                 const float* __restrict__ Pm, int in) {
+    for (int j = 0; j < sh.nh; ++j) {
+        const int fi = j == 0 ? in : kMw;
+        const float* W = Pm + sh.w_off[j];  // [64][fi]
+        for (int e = threadIdx.x; e < kMw * fi; e += blockDim.x) {
+            const int o = e / fi, c = e % fi;
+            const float w = W[e], h = tf32_hi(w), l = w - h;
+            const int f = sw128_off(kMw, o, c), b = sw128_off(fi, c, o);
+            *reinterpret_cast<float*>(sm + L.wf_hi[j] + f) = h;
+            *reinterpret_cast<float*>(sm + L.wf_lo[j] + f) = l;
+            *reinterpret_cast<float*>(sm + L.wb_hi[j] + b) = h;
+            *reinterpret_cast<float*>(sm + L.wb_lo[j] + b) = l;
+        }
+        for (int o = threadIdx.x; o < kMw; o += blockDim.x)
+            reinterpret_cast<float*>(sm + L.bias)[j * kMw + o] = Pm[sh.b_off[j] + o];
+    }
+    float* wout = reinterpret_cast<float*>(sm + L.wout);
+    for (int o = threadIdx.x; o < kMw; o += blockDim.x) wout[o] = Pm[sh.w_off[sh.nh] + o];
+    if (threadIdx.x == 0) wout[kMw] = Pm[sh.b_off[sh.nh]];
+}
+
+// Columns [0, N) of this thread's accumulator row into v (N = 16, 32 or 64).
+template <int N>
+__device__ __forceinline__ void read_acc(uint32_t taddr, float (&v)[kMw]) {
+    float part[32];
+#pragma unroll
+    for (int h = 0; h < (N + 31) / 32; ++h) {
+        tc::tmem_ld32(taddr + 32 * h, part);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+            if (32 * h + q < N) v[32 * h + q] = part[q];
+    }
+}
+
+// acts rows [0, IN) hold the encoding; the kernel writes rows IN + j*64 + o (hidden activations), dl
+// (deltas: row j*64 + o of hidden layer j, row nh*64 the output's dL/dy) and denc (IN rows), all
+// feature-major with row stride n, and one loss partial (sum of squared errors) per CTA.
+template <int IN>
+__global__ void __launch_bounds__(kMt, 1) k_mlp_f32tc(const __grid_constant__ MlpShape sh, const float* __restrict__ Pm,
+                                                   const float* __restrict__ target, int64_t n, float two_over_n,
+                                                   float* __restrict__ acts, float* __restrict__ dl,
+                                                   float* __restrict__ denc, double* __restrict__ partial,
+                                                   int* __restrict__ err) {
+    extern __shared__ uint8_t smraw[];
+    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+    const int nh = sh.nh, t = threadIdx.x, warp = t >> 5;
+    const TcMlpLayout L = tc_mlp_layout(IN, nh);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.bar);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(sm + L.slot);
+    const float* bias = reinterpret_cast<const float*>(sm + L.bias);
+    const float* wout = reinterpret_cast<const float*>(sm + L.wout);
+    uint8_t* a_hi = sm + L.a_hi;
+    uint8_t* a_lo = sm + L.a_lo;
+    if (warp == 0) tc::tmem_alloc(slot, 64);
+    if (t == 0) {
+        tc::mbar_init(bar, 1);
+        tc::fence_mbar_init();
+    }
+    stage_tc_weights(sm, L, sh, Pm, IN);
+    tc::fence_async_smem();  // the staged weights become visible to the tensor cores
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *slot;
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);  // this thread's lane
+    const uint32_t ah0 = tc::smem_addr(a_hi), al0 = tc::smem_addr(a_lo);
+    const float bo = wout[kMw];
+    uint32_t phase = 0;
+    bool bad = false;
+    double lsum = 0.0;
+
+    // D = A * B^T over K (3xTF32), B of N rows at (b_hi, b_lo); every thread has written its A row.
+    auto gemm = [&](int off_hi, int off_lo, int N, int K) -> bool {
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (t == 0) {
+            const uint32_t idesc = tc::idesc_tf32(kMt, N);
+            const uint32_t bh0 = tc::smem_addr(sm + off_hi), bl0 = tc::smem_addr(sm + off_lo);
+            for (int kk = 0; kk < K / 8; ++kk) {
+                const uint32_t ka = (kk >> 2) * kMt * 128 + (kk & 3) * 32, kb = (kk >> 2) * N * 128 + (kk & 3) * 32;
+                const uint64_t ah = tc::sdesc_sw128(ah0 + ka), al = tc::sdesc_sw128(al0 + ka);
+                const uint64_t bh = tc::sdesc_sw128(bh0 + kb), bl = tc::sdesc_sw128(bl0 + kb);
+                tc::mma_tf32(tmem, ah, bh, idesc, kk > 0 ? 1u : 0u);
+                tc::mma_tf32(tmem, ah, bl, idesc, 1u);
+                tc::mma_tf32(tmem, al, bh, idesc, 1u);
+            }
+            tc::mma_commit(bar);
+        }
+        const bool ok = tc::mbar_wait(bar, phase);
+        phase ^= 1u;
+        tc::fence_after_sync();
+        return !__syncthreads_or(!ok);
+    };
+
+    const int64_t ntiles = (n + kMt - 1) / kMt;
+    float x[IN];
+    auto load_x = [&](int64_t tl) {
+        const int64_t i = tl * kMt + t;
+        const bool in_range = tl < ntiles && i < n;
+#pragma unroll
+        for (int k = 0; k < IN; ++k) x[k] = in_range ? acts[(int64_t)k * n + i] : 0.0f;
+    };
+    load_x(blockIdx.x);
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t i = tile * kMt + t;
+        const bool valid = i < n;
+        put_row<IN>(a_hi, a_lo, t, x);
+        load_x(tile + gridDim.x);  // the next tile's encoding stays in flight during this one
+        float v[kMw];
+        uint32_t mk[kTcMaxHidden][2] = {};
+        // forward: z = W a + b, a = ReLU(z) (mask bit: z > 0)
+#pragma unroll
+        for (int j = 0; j < kTcMaxHidden; ++j) {
+            if (j >= nh) break;
+            const bool ok = j == 0 ? gemm(L.wf_hi[0], L.wf_lo[0], kMw, IN) : gemm(L.wf_hi[j], L.wf_lo[j], kMw, kMw);
+            if (!ok) { bad = true; break; }
+            read_acc<kMw>(taddr, v);
+#pragma unroll
+            for (int o = 0; o < kMw; ++o) {
+                const float z = v[o] + bias[j * kMw + o];
+                if (z > 0.0f) mk[j][o >> 5] |= 1u << (o & 31);
+                v[o] = fmaxf(z, 0.0f);
+                if (valid) acts[(int64_t)(IN + j * kMw + o) * n + i] = v[o];
+            }
+            if (j + 1 < nh) put_row<kMw>(a_hi, a_lo, t, v);
+        }
+        if (bad) break;
+        // output unit, squared error, dL/dy = 2 (y - target) / N
+        float y = bo;
+#pragma unroll
+        for (int o = 0; o < kMw; ++o) y = fmaf(wout[o], v[o], y);
+        float gy = 0.0f;
+        if (valid) {
+            const float d = y - target[i];
+            gy = two_over_n * d;
+            lsum += (double)d * (double)d;
+            dl[(int64_t)(nh * kMw) * n + i] = gy;
+        }
+        // delta of the last hidden layer: wout * dL/dy where its unit was active
+        uint32_t m0 = 0u, m1 = 0u;
+#pragma unroll
+        for (int j = 0; j < kTcMaxHidden; ++j)
+            if (j == nh - 1) { m0 = mk[j][0]; m1 = mk[j][1]; }
+#pragma unroll
+        for (int o = 0; o < kMw; ++o) {
+            const bool on = (((o < 32) ? m0 : m1) >> (o & 31)) & 1u;
+            v[o] = on ? wout[o] * gy : 0.0f;
+            if (valid) dl[(int64_t)((nh - 1) * kMw + o) * n + i] = v[o];
+        }
+        // backward: p = W^T delta; below a hidden layer, delta = p where that layer was active
+#pragma unroll
+        for (int j = kTcMaxHidden - 1; j >= 0; --j) {
+            if (j >= nh) continue;
+            put_row<kMw>(a_hi, a_lo, t, v);
+            if (j > 0) {
+                if (!gemm(L.wb_hi[j], L.wb_lo[j], kMw, kMw)) { bad = true; break; }
+                read_acc<kMw>(taddr, v);
+#pragma unroll
+                for (int c = 0; c < kMw; ++c) {
+                    const bool on = (mk[j - 1][c >> 5] >> (c & 31)) & 1u;
+                    v[c] = on ? v[c] : 0.0f;
+                    if (valid) dl[(int64_t)((j - 1) * kMw + c) * n + i] = v[c];
+                }
+            } else {
+                if (!gemm(L.wb_hi[0], L.wb_lo[0], IN, kMw)) { bad = true; break; }
+                read_acc<IN>(taddr, v);
+                if (valid) {
+#pragma unroll
+                    for (int c = 0; c < IN; ++c) denc[(int64_t)c * n + i] = v[c];
+                }
+            }
+        }
+        if (bad) break;
+    }
+    tc::fence_before_sync();
+    const double tot = block_sum(lsum);  // synchronises the CTA
+    if (t == 0) {
+        partial[blockIdx.x] = tot;
+        if (bad) raise_error(err, 0x7C0A);
+    }
+    if (warp == 0) tc::tmem_dealloc(tmem, 64);
+}
+
+// The fused float32 MLP pass over n samples (one CTA per SM, persistent over 128-sample tiles).  Returns
+// false, launching nothing, when the model's shape is not handled here; otherwise *grid receives the
+// number of loss partials written (at most max_partials).
+bool launch_mlp_f32tc(fhash_model* m, const float* target, int64_t n, float* acts, float* dl, float* denc,
+                      double* partial, int max_partials, int* grid, cudaStream_t st, cudaError_t* err) {
+    *err = cudaSuccess;
+    const MlpShape& sh = m->mlp;
+    if (sh.width != kMw || sh.nh < 1 || sh.nh > kTcMaxHidden || (sh.in != 16 && sh.in != 32 && sh.in != 64) ||
+        n < 1 || max_partials < 1)
+        return false;
+    const TcMlpLayout L = tc_mlp_layout(sh.in, sh.nh);
+    if (L.total > 227 * 1024) return false;
+    const int64_t ntiles = (n + kMt - 1) / kMt;
+    const int g = (int)std::min<int64_t>(std::min<int64_t>(ntiles, num_sms()), max_partials);
+    const float* Pm = m->param + m->n_table;
+    const float two_over_n = 2.0f / (float)n;
+    const void* fn = sh.in == 16 ? (const void*)k_mlp_f32tc<16> : sh.in == 32 ? (const void*)k_mlp_f32tc<32>
+                                                                             : (const void*)k_mlp_f32tc<64>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+    if (e == cudaSuccess) {
+        switch (sh.in) {
+            case 16: k_mlp_f32tc<16><<<g, kMt, L.total, st>>>(sh, Pm, target, n, two_over_n, acts, dl, denc, partial, m->err_word); break;
+            case 32: k_mlp_f32tc<32><<<g, kMt, L.total, st>>>(sh, Pm, target, n, two_over_n, acts, dl, denc, partial, m->err_word); break;
+            default: k_mlp_f32tc<64><<<g, kMt, L.total, st>>>(sh, Pm, target, n, two_over_n, acts, dl, denc, partial, m->err_word); break;
+        }
+        e = cudaGetLastError();
+    }
+    *grid = g;
+    *err = e;
+    return true;
+}
+
+}  // namespace fh

@@ -434,6 +434,8 @@ __global__ void k_loss2(const double* __restrict__ partial, int nb, int64_t n, d
 }
 
 cudaError_t run_tc_any(fhash_model* m, bool train, FusedArgs& a);
+bool launch_mlp_f32tc(fhash_model* m, const float* target, int64_t n, float* acts, float* dl, float* denc,
+                      double* partial, int max_partials, int* grid, cudaStream_t st, cudaError_t* err);
 bool launch_dw_tc(fhash_model* m, const float* acts, const float* dl, int64_t n, float* wpart, size_t wpart_bytes,
                   int* nchunk_out, cudaStream_t st, cudaError_t* err, bool split3);
 
@@ -538,6 +540,7 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
                                                                        (int64_t)num_sms() * std::max(1, (227 * 1024) / tsmem)));
 
     // forward: encoding + MLP (bf16 form: one tensor-core kernel writes the same activations)
+    bool fused_mlp = false;
     if (m->shadow) {
         FusedArgs a{};
         a.coords = coords; a.target = target; a.n = n; a.acts = acts; a.gy = gy; a.partial = lpart; a.st = st;
@@ -555,18 +558,30 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
         }
         FH_CUDA(cudaGetLastError());
         tev_record(m, TEV_ENCODE, st);
-        FH_CUDA(cudaFuncSetAttribute((const void*)k_mlp_fwd_t, cudaFuncAttributeMaxDynamicSharedMemorySize, tsmem));
-        nb = std::min(nb, tile_grid);  // one loss partial per block
-        k_mlp_fwd_t<<<nb, 256, tsmem, st>>>(sh, Pm, target, n, 2.0f / (float)n, acts, gy, lpart);
-        FH_CUDA(cudaGetLastError());
+        // the MLP's forward, loss and backward data path fused on the tensor cores (3xTF32), where the
+        // shape allows; otherwise the float32 SIMT tile kernels
+        int g = 0;
+        cudaError_t e = cudaSuccess;
+        if (launch_mlp_f32tc(m, target, n, acts, dl, denc, lpart, nb, &g, st, &e)) {
+            FH_CUDA(e);
+            nb = g;
+            fused_mlp = true;
+        } else {
+            FH_CUDA(cudaFuncSetAttribute((const void*)k_mlp_fwd_t, cudaFuncAttributeMaxDynamicSharedMemorySize, tsmem));
+            nb = std::min(nb, tile_grid);  // one loss partial per block
+            k_mlp_fwd_t<<<nb, 256, tsmem, st>>>(sh, Pm, target, n, 2.0f / (float)n, acts, gy, lpart);
+            FH_CUDA(cudaGetLastError());
+        }
     }
     k_loss2<<<1, 256, 0, st>>>(lpart, nb, n, loss_dev);
     FH_CUDA(cudaGetLastError());
     // backward: MLP data path, table scatter, weight gradients
-    const int bb = tile_grid;
-    FH_CUDA(cudaFuncSetAttribute((const void*)k_mlp_bwd_t, cudaFuncAttributeMaxDynamicSharedMemorySize, tsmem));
-    k_mlp_bwd_t<<<bb, 256, tsmem, st>>>(sh, Pm, n, acts, gy, dl, denc);
-    FH_CUDA(cudaGetLastError());
+    if (!fused_mlp) {
+        const int bb = tile_grid;
+        FH_CUDA(cudaFuncSetAttribute((const void*)k_mlp_bwd_t, cudaFuncAttributeMaxDynamicSharedMemorySize, tsmem));
+        k_mlp_bwd_t<<<bb, 256, tsmem, st>>>(sh, Pm, n, acts, gy, dl, denc);
+        FH_CUDA(cudaGetLastError());
+    }
     tev_record(m, TEV_MLP, st);
     switch (F) {
         case 1: FH_CUDA(scatter_launch<1>(m, coords, n, denc, n, 1, st)); break;
