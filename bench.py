@@ -916,6 +916,14 @@ def main():
                            "%d samples x (16 x %d levels x %d floats reduced + 16 B coordinates + %d floats read)"
                            % (B, L, F, L * F)),
     }
+    dims = info["mlp_dims"]
+    nh_m, in_m = len(dims) - 2, dims[0]
+    if not bf16 and in_m in (16, 32, 64) and 1 <= nh_m <= 2 and all(d == 64 for d in dims[1:-1]):
+        # the float32 MLP fused on the tensor cores (its phase also holds the one-block loss reduction):
+        # per sample the encoding and target read; hidden activations, every delta and d(encoding) written
+        mlp_b = 4 * (in_m + 1) + 4 * (nh_m * 64 + nh_m * 64 + 1 + in_m)
+        kern["k_mlp_f32tc"] = (B * mlp_b, mlp_ms, "%d samples x %d B (encoding and target read; activations, "
+                                                  "deltas and d(encoding) written)" % (B, mlp_b))
     if bf16:  # the fused tensor-core forward replaces k_encode_cols in the precision form
         kern["k_forward_tc"] = (B * (16 * L * F * elem + 16), encode_ms, "%d samples x (16 x %d levels x %d bf16 "
                                 "gathered + 16 B coordinates)" % (B, L, F))

@@ -2,8 +2,9 @@
 // one 128-sample tile in one CTA, every layer a tcgen05.mma kind::tf32 GEMM with the error-compensated
 // 3xTF32 split (hi*hi + hi*lo + lo*hi, Ootomo and Yokota 2022), so the results keep float32 accuracy.
 //
-// A tile's samples are the TMEM lanes and the CTA's 128 threads (thread t = sample t = lane t), so a
-// layer's accumulator row is one thread's registers after tcgen05.ld.  Every GEMM has the samples as
+// A tile's samples are the TMEM lanes.  Two threads share a sample: warps 0-3 take columns 0-31 of
+// its rows and warps 4-7 columns 32-63 (warp w reads TMEM lane quarter w % 4), so an accumulator row is
+// two threads' registers after tcgen05.ld, and 8 warps per SM hide the epilogues' latency.  Every GEMM has the samples as
 // M = 128 and K-major operands in the 128-byte swizzle layout:
 //   forward layer j:   z[s][o] = sum_c a[s][c] W_j[o][c]     A = activations, B = W_j as stored;
 //   backward layer j:  p[s][c] = sum_o d[s][o] W_j[o][c]     A = deltas,      B = W_j transposed.
@@ -26,7 +27,8 @@
 
 namespace fh {
 
-constexpr int kMt = 128;         // samples per tile = TMEM lanes = threads
+constexpr int kMt = 128;         // samples per tile = TMEM lanes
+constexpr int kMthreads = 256;   // two threads per sample, 32 columns each
 constexpr int kMw = 64;          // hidden width handled here
 constexpr int kTcMaxHidden = 2;  // hidden layers whose weights (both directions, hi and lo) fit
 
@@ -37,7 +39,7 @@ struct TcMlpLayout {
     int a_hi, a_lo;                                   // A: 128 rows x 64 floats (two blocks)
     int wf_hi[kTcMaxHidden], wf_lo[kTcMaxHidden];     // forward B of layer j: 64 rows x fi_j floats
     int wb_hi[kTcMaxHidden], wb_lo[kTcMaxHidden];     // backward B of layer j: fi_j rows x 64 floats
-    int bias, wout, bar, slot, total;
+    int bias, wout, ypart, bar, slot, total;
 };
 
 __host__ __device__ inline int tc_blocks(int k) { return (k + 31) / 32; }
@@ -57,6 +59,7 @@ __host__ __device__ inline TcMlpLayout tc_mlp_layout(int in, int nh) {
     }
     L.bias = o; o += kTcMaxHidden * kMw * 4;
     L.wout = o; o += kMw * 4 + 16;
+    L.ypart = o; o += 2 * kMt * 4;  // the two column halves' partial output sums
     L.bar = o; o += 16;
     L.slot = o; o += 16;
     L.total = o + 1024;  // alignment slack of the dynamic shared-memory base
@@ -68,6 +71,7 @@ __device__ __forceinline__ int sw128_off(int R, int r, int k) {
     return (k >> 5) * R * 128 + r * 128 + ((((k & 31) >> 2) ^ (r & 7)) << 4) + ((k & 3) << 2);
 }
 
+
 // Round to the nearest tf32 value (10 explicit mantissa bits, ties to even), kept as float32.
 __device__ __forceinline__ float tf32_hi(float x) {
     uint32_t u = __float_as_uint(x);
@@ -75,20 +79,31 @@ __device__ __forceinline__ float tf32_hi(float x) {
     return __uint_as_float(u & 0xFFFFE000u);
 }
 
-// Writes this thread's row (row t) of an A operand: K values, hi and lo, 16 bytes at a time.
+// Writes values [h K/2, (h + 1) K/2) of row r of an A operand of K floats (hi and lo), 16 bytes at a time.
 template <int K>
-__device__ __forceinline__ void put_row(uint8_t* hi, uint8_t* lo, int t, const float (&v)[K]) {
+__device__ __forceinline__ void put_half(uint8_t* hi, uint8_t* lo, int r, int h, const float (&v)[K / 2]) {
 #pragma unroll
-    for (int c = 0; c < K / 4; ++c) {
-        const int off = (c >> 3) * kMt * 128 + t * 128 + (((c & 7) ^ (t & 7)) << 4);
-        float4 h, l;
-        h.x = tf32_hi(v[4 * c + 0]); l.x = v[4 * c + 0] - h.x;
-        h.y = tf32_hi(v[4 * c + 1]); l.y = v[4 * c + 1] - h.y;
-        h.z = tf32_hi(v[4 * c + 2]); l.z = v[4 * c + 2] - h.z;
-        h.w = tf32_hi(v[4 * c + 3]); l.w = v[4 * c + 3] - h.w;
-        *reinterpret_cast<float4*>(hi + off) = h;
-        *reinterpret_cast<float4*>(lo + off) = l;
+    for (int q = 0; q < K / 8; ++q) {
+        const int c = h * (K / 8) + q;  // 16-byte chunk along K
+        const int off = (c >> 3) * kMt * 128 + r * 128 + (((c & 7) ^ (r & 7)) << 4);
+        float4 a, b;
+        a.x = tf32_hi(v[4 * q + 0]); b.x = v[4 * q + 0] - a.x;
+        a.y = tf32_hi(v[4 * q + 1]); b.y = v[4 * q + 1] - a.y;
+        a.z = tf32_hi(v[4 * q + 2]); b.z = v[4 * q + 2] - a.z;
+        a.w = tf32_hi(v[4 * q + 3]); b.w = v[4 * q + 3] - a.w;
+        *reinterpret_cast<float4*>(hi + off) = a;
+        *reinterpret_cast<float4*>(lo + off) = b;
     }
+}
+
+// Columns [h N/2, (h + 1) N/2) of this thread's accumulator lane (N = 16, 32 or 64; 64 are allocated).
+template <int N>
+__device__ __forceinline__ void read_half(uint32_t taddr, int h, float (&v)[N / 2]) {
+    float part[32];
+    tc::tmem_ld32(taddr + h * (N / 2), part);
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int q = 0; q < N / 2; ++q) v[q] = part[q];
 }
 
 // Every hidden layer's weights, split into hi and lo, in both operand forms; biases and output weights.
@@ -99,12 +114,12 @@ __device__ __forceinline__ void stage_tc_weights(uint8_t* sm, const TcMlpLayout&
         const float* W = Pm + sh.w_off[j];  // [64][fi]
         for (int e = threadIdx.x; e < kMw * fi; e += blockDim.x) {
             const int o = e / fi, c = e % fi;
-            const float w = W[e], h = tf32_hi(w), l = w - h;
+            const float w = W[e], hw = tf32_hi(w), lw = w - hw;
             const int f = sw128_off(kMw, o, c), b = sw128_off(fi, c, o);
-            *reinterpret_cast<float*>(sm + L.wf_hi[j] + f) = h;
-            *reinterpret_cast<float*>(sm + L.wf_lo[j] + f) = l;
-            *reinterpret_cast<float*>(sm + L.wb_hi[j] + b) = h;
-            *reinterpret_cast<float*>(sm + L.wb_lo[j] + b) = l;
+            *reinterpret_cast<float*>(sm + L.wf_hi[j] + f) = hw;
+            *reinterpret_cast<float*>(sm + L.wf_lo[j] + f) = lw;
+            *reinterpret_cast<float*>(sm + L.wb_hi[j] + b) = hw;
+            *reinterpret_cast<float*>(sm + L.wb_lo[j] + b) = lw;
         }
         for (int o = threadIdx.x; o < kMw; o += blockDim.x)
             reinterpret_cast<float*>(sm + L.bias)[j * kMw + o] = Pm[sh.b_off[j] + o];
@@ -114,37 +129,27 @@ __device__ __forceinline__ void stage_tc_weights(uint8_t* sm, const TcMlpLayout&
     if (threadIdx.x == 0) wout[kMw] = Pm[sh.b_off[sh.nh]];
 }
 
-// Columns [0, N) of this thread's accumulator row into v (N = 16, 32 or 64).
-template <int N>
-__device__ __forceinline__ void read_acc(uint32_t taddr, float (&v)[kMw]) {
-    float part[32];
-#pragma unroll
-    for (int h = 0; h < (N + 31) / 32; ++h) {
-        tc::tmem_ld32(taddr + 32 * h, part);
-        tc::tmem_ld_wait();
-#pragma unroll
-        for (int q = 0; q < 32; ++q)
-            if (32 * h + q < N) v[32 * h + q] = part[q];
-    }
-}
-
 // acts rows [0, IN) hold the encoding; the kernel writes rows IN + j*64 + o (hidden activations), dl
 // (deltas: row j*64 + o of hidden layer j, row nh*64 the output's dL/dy) and denc (IN rows), all
 // feature-major with row stride n, and one loss partial (sum of squared errors) per CTA.
 template <int IN>
-__global__ void __launch_bounds__(kMt, 1) k_mlp_f32tc(const __grid_constant__ MlpShape sh, const float* __restrict__ Pm,
-                                                   const float* __restrict__ target, int64_t n, float two_over_n,
-                                                   float* __restrict__ acts, float* __restrict__ dl,
-                                                   float* __restrict__ denc, double* __restrict__ partial,
-                                                   int* __restrict__ err) {
+__global__ void __launch_bounds__(kMthreads, 1) k_mlp_f32tc(const __grid_constant__ MlpShape sh, const float* __restrict__ Pm,
+                                                         const float* __restrict__ target, int64_t n, float two_over_n,
+                                                         float* __restrict__ acts, float* __restrict__ dl,
+                                                         float* __restrict__ denc, double* __restrict__ partial,
+                                                         int* __restrict__ err) {
+    constexpr int HI = IN / 2;  // encoding values per thread
     extern __shared__ uint8_t smraw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
     const int nh = sh.nh, t = threadIdx.x, warp = t >> 5;
+    const int h = warp >> 2;                      // column half: 0 -> columns 0-31, 1 -> 32-63
+    const int r = (warp & 3) * 32 + (t & 31);     // sample of the tile = TMEM lane
     const TcMlpLayout L = tc_mlp_layout(IN, nh);
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.bar);
     uint32_t* slot = reinterpret_cast<uint32_t*>(sm + L.slot);
     const float* bias = reinterpret_cast<const float*>(sm + L.bias);
     const float* wout = reinterpret_cast<const float*>(sm + L.wout);
+    float* ypart = reinterpret_cast<float*>(sm + L.ypart);
     uint8_t* a_hi = sm + L.a_hi;
     uint8_t* a_lo = sm + L.a_lo;
     if (warp == 0) tc::tmem_alloc(slot, 64);
@@ -158,14 +163,14 @@ __global__ void __launch_bounds__(kMt, 1) k_mlp_f32tc(const __grid_constant__ Ml
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *slot;
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);  // this thread's lane
+    const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16);  // this thread's lane quarter
     const uint32_t ah0 = tc::smem_addr(a_hi), al0 = tc::smem_addr(a_lo);
     const float bo = wout[kMw];
     uint32_t phase = 0;
     bool bad = false;
     double lsum = 0.0;
 
-    // D = A * B^T over K (3xTF32), B of N rows at (b_hi, b_lo); every thread has written its A row.
+    // D = A * B^T over K (3xTF32), B of N rows at (off_hi, off_lo); every thread has written its A half-row.
     auto gemm = [&](int off_hi, int off_lo, int N, int K) -> bool {
         tc::fence_async_smem();
         tc::fence_before_sync();
@@ -191,80 +196,86 @@ __global__ void __launch_bounds__(kMt, 1) k_mlp_f32tc(const __grid_constant__ Ml
     };
 
     const int64_t ntiles = (n + kMt - 1) / kMt;
-    float x[IN];
+    float x[HI];
     auto load_x = [&](int64_t tl) {
-        const int64_t i = tl * kMt + t;
+        const int64_t i = tl * kMt + r;
         const bool in_range = tl < ntiles && i < n;
 #pragma unroll
-        for (int k = 0; k < IN; ++k) x[k] = in_range ? acts[(int64_t)k * n + i] : 0.0f;
+        for (int k = 0; k < HI; ++k) x[k] = in_range ? acts[(int64_t)(h * HI + k) * n + i] : 0.0f;
     };
     load_x(blockIdx.x);
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t i = tile * kMt + t;
+        const int64_t i = tile * kMt + r;
         const bool valid = i < n;
-        put_row<IN>(a_hi, a_lo, t, x);
+        put_half<IN>(a_hi, a_lo, r, h, x);
         load_x(tile + gridDim.x);  // the next tile's encoding stays in flight during this one
-        float v[kMw];
-        uint32_t mk[kTcMaxHidden][2] = {};
-        // forward: z = W a + b, a = ReLU(z) (mask bit: z > 0)
+        float v[32];
+        uint32_t mk[kTcMaxHidden] = {};  // ReLU masks of this thread's 32 units per hidden layer
+        // forward: z = W a + b, a = ReLU(z)
 #pragma unroll
         for (int j = 0; j < kTcMaxHidden; ++j) {
             if (j >= nh) break;
             const bool ok = j == 0 ? gemm(L.wf_hi[0], L.wf_lo[0], kMw, IN) : gemm(L.wf_hi[j], L.wf_lo[j], kMw, kMw);
             if (!ok) { bad = true; break; }
-            read_acc<kMw>(taddr, v);
+            read_half<kMw>(taddr, h, v);
 #pragma unroll
-            for (int o = 0; o < kMw; ++o) {
-                const float z = v[o] + bias[j * kMw + o];
-                if (z > 0.0f) mk[j][o >> 5] |= 1u << (o & 31);
-                v[o] = fmaxf(z, 0.0f);
-                if (valid) acts[(int64_t)(IN + j * kMw + o) * n + i] = v[o];
+            for (int q = 0; q < 32; ++q) {
+                const int o = 32 * h + q;
+                const float z = v[q] + bias[j * kMw + o];
+                if (z > 0.0f) mk[j] |= 1u << q;
+                v[q] = fmaxf(z, 0.0f);
+                if (valid) acts[(int64_t)(IN + j * kMw + o) * n + i] = v[q];
             }
-            if (j + 1 < nh) put_row<kMw>(a_hi, a_lo, t, v);
+            if (j + 1 < nh) put_half<kMw>(a_hi, a_lo, r, h, v);
         }
         if (bad) break;
-        // output unit, squared error, dL/dy = 2 (y - target) / N
-        float y = bo;
+        // output unit: the two halves' partial sums, added in a fixed order; dL/dy = 2 (y - target) / N
+        float part = h == 0 ? bo : 0.0f;
 #pragma unroll
-        for (int o = 0; o < kMw; ++o) y = fmaf(wout[o], v[o], y);
+        for (int q = 0; q < 32; ++q) part = fmaf(wout[32 * h + q], v[q], part);
+        ypart[h * kMt + r] = part;
+        __syncthreads();
+        const float y = ypart[r] + ypart[kMt + r];
         float gy = 0.0f;
         if (valid) {
             const float d = y - target[i];
             gy = two_over_n * d;
-            lsum += (double)d * (double)d;
-            dl[(int64_t)(nh * kMw) * n + i] = gy;
+            if (h == 0) {
+                lsum += (double)d * (double)d;
+                dl[(int64_t)(nh * kMw) * n + i] = gy;
+            }
         }
         // delta of the last hidden layer: wout * dL/dy where its unit was active
-        uint32_t m0 = 0u, m1 = 0u;
+        uint32_t ml = 0u;
 #pragma unroll
         for (int j = 0; j < kTcMaxHidden; ++j)
-            if (j == nh - 1) { m0 = mk[j][0]; m1 = mk[j][1]; }
+            if (j == nh - 1) ml = mk[j];
 #pragma unroll
-        for (int o = 0; o < kMw; ++o) {
-            const bool on = (((o < 32) ? m0 : m1) >> (o & 31)) & 1u;
-            v[o] = on ? wout[o] * gy : 0.0f;
-            if (valid) dl[(int64_t)((nh - 1) * kMw + o) * n + i] = v[o];
+        for (int q = 0; q < 32; ++q) {
+            const int o = 32 * h + q;
+            v[q] = ((ml >> q) & 1u) ? wout[o] * gy : 0.0f;
+            if (valid) dl[(int64_t)((nh - 1) * kMw + o) * n + i] = v[q];
         }
         // backward: p = W^T delta; below a hidden layer, delta = p where that layer was active
 #pragma unroll
         for (int j = kTcMaxHidden - 1; j >= 0; --j) {
             if (j >= nh) continue;
-            put_row<kMw>(a_hi, a_lo, t, v);
+            put_half<kMw>(a_hi, a_lo, r, h, v);
             if (j > 0) {
                 if (!gemm(L.wb_hi[j], L.wb_lo[j], kMw, kMw)) { bad = true; break; }
-                read_acc<kMw>(taddr, v);
+                read_half<kMw>(taddr, h, v);
 #pragma unroll
-                for (int c = 0; c < kMw; ++c) {
-                    const bool on = (mk[j - 1][c >> 5] >> (c & 31)) & 1u;
-                    v[c] = on ? v[c] : 0.0f;
-                    if (valid) dl[(int64_t)((j - 1) * kMw + c) * n + i] = v[c];
+                for (int q = 0; q < 32; ++q) {
+                    v[q] = ((mk[j - 1] >> q) & 1u) ? v[q] : 0.0f;
+                    if (valid) dl[(int64_t)((j - 1) * kMw + 32 * h + q) * n + i] = v[q];
                 }
             } else {
                 if (!gemm(L.wb_hi[0], L.wb_lo[0], IN, kMw)) { bad = true; break; }
-                read_acc<IN>(taddr, v);
+                float p[HI];
+                read_half<IN>(taddr, h, p);
                 if (valid) {
 #pragma unroll
-                    for (int c = 0; c < IN; ++c) denc[(int64_t)c * n + i] = v[c];
+                    for (int q = 0; q < HI; ++q) denc[(int64_t)(h * HI + q) * n + i] = p[q];
                 }
             }
         }
@@ -278,7 +289,6 @@ __global__ void __launch_bounds__(kMt, 1) k_mlp_f32tc(const __grid_constant__ Ml
     }
     if (warp == 0) tc::tmem_dealloc(tmem, 64);
 }
-
 // The fused float32 MLP pass over n samples (one CTA per SM, persistent over 128-sample tiles).  Returns
 // false, launching nothing, when the model's shape is not handled here; otherwise *grid receives the
 // number of loss partials written (at most max_partials).
@@ -300,9 +310,9 @@ bool launch_mlp_f32tc(fhash_model* m, const float* target, int64_t n, float* act
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
     if (e == cudaSuccess) {
         switch (sh.in) {
-            case 16: k_mlp_f32tc<16><<<g, kMt, L.total, st>>>(sh, Pm, target, n, two_over_n, acts, dl, denc, partial, m->err_word); break;
-            case 32: k_mlp_f32tc<32><<<g, kMt, L.total, st>>>(sh, Pm, target, n, two_over_n, acts, dl, denc, partial, m->err_word); break;
-            default: k_mlp_f32tc<64><<<g, kMt, L.total, st>>>(sh, Pm, target, n, two_over_n, acts, dl, denc, partial, m->err_word); break;
+            case 16: k_mlp_f32tc<16><<<g, kMthreads, L.total, st>>>(sh, Pm, target, n, two_over_n, acts, dl, denc, partial, m->err_word); break;
+            case 32: k_mlp_f32tc<32><<<g, kMthreads, L.total, st>>>(sh, Pm, target, n, two_over_n, acts, dl, denc, partial, m->err_word); break;
+            default: k_mlp_f32tc<64><<<g, kMthreads, L.total, st>>>(sh, Pm, target, n, two_over_n, acts, dl, denc, partial, m->err_word); break;
         }
         e = cudaGetLastError();
     }
