@@ -132,9 +132,12 @@ __device__ __forceinline__ void stage_tc_weights(uint8_t* sm, const TcMlpLayout&
 // acts rows [0, IN) hold the encoding; the kernel writes rows IN + j*64 + o (hidden activations), dl
 // (deltas: row j*64 + o of hidden layer j, row nh*64 the output's dL/dy) and denc (IN rows), all
 // feature-major with row stride n, and one loss partial (sum of squared errors) per CTA.
-template <int IN>
+// BWD: the backward data path alone, after the precision form's forward kernel has stored the hidden
+// activations in acts and dL/dy in gyin (ReLU masks from the stored activations; no loss partials).
+template <int IN, bool BWD>
 __global__ void __launch_bounds__(kMthreads, 1) k_mlp_f32tc(const __grid_constant__ MlpShape sh, const float* __restrict__ Pm,
-                                                         const float* __restrict__ target, int64_t n, float two_over_n,
+                                                         const float* __restrict__ target, const float* __restrict__ gyin,
+                                                         int64_t n, float two_over_n,
                                                          float* __restrict__ acts, float* __restrict__ dl,
                                                          float* __restrict__ denc, double* __restrict__ partial,
                                                          int* __restrict__ err) {
@@ -203,14 +206,28 @@ __global__ void __launch_bounds__(kMthreads, 1) k_mlp_f32tc(const __grid_constan
 #pragma unroll
         for (int k = 0; k < HI; ++k) x[k] = in_range ? acts[(int64_t)(h * HI + k) * n + i] : 0.0f;
     };
-    load_x(blockIdx.x);
+    if (!BWD) load_x(blockIdx.x);
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t i = tile * kMt + r;
         const bool valid = i < n;
-        put_half<IN>(a_hi, a_lo, r, h, x);
-        load_x(tile + gridDim.x);  // the next tile's encoding stays in flight during this one
         float v[32];
         uint32_t mk[kTcMaxHidden] = {};  // ReLU masks of this thread's 32 units per hidden layer
+        float gy = 0.0f;
+        if constexpr (BWD) {
+#pragma unroll
+            for (int j = 0; j < kTcMaxHidden; ++j) {
+                if (j >= nh) break;
+#pragma unroll
+                for (int q = 0; q < 32; ++q)
+                    if (valid && acts[(int64_t)(IN + j * kMw + 32 * h + q) * n + i] > 0.0f) mk[j] |= 1u << q;
+            }
+            if (valid) {
+                gy = gyin[i];
+                if (h == 0) dl[(int64_t)(nh * kMw) * n + i] = gy;
+            }
+        } else {
+        put_half<IN>(a_hi, a_lo, r, h, x);
+        load_x(tile + gridDim.x);  // the next tile's encoding stays in flight during this one
         // forward: z = W a + b, a = ReLU(z)
 #pragma unroll
         for (int j = 0; j < kTcMaxHidden; ++j) {
@@ -236,7 +253,6 @@ __global__ void __launch_bounds__(kMthreads, 1) k_mlp_f32tc(const __grid_constan
         ypart[h * kMt + r] = part;
         __syncthreads();
         const float y = ypart[r] + ypart[kMt + r];
-        float gy = 0.0f;
         if (valid) {
             const float d = y - target[i];
             gy = two_over_n * d;
@@ -244,6 +260,7 @@ __global__ void __launch_bounds__(kMthreads, 1) k_mlp_f32tc(const __grid_constan
                 lsum += (double)d * (double)d;
                 dl[(int64_t)(nh * kMw) * n + i] = gy;
             }
+        }
         }
         // delta of the last hidden layer: wout * dL/dy where its unit was active
         uint32_t ml = 0u;
@@ -284,16 +301,28 @@ __global__ void __launch_bounds__(kMthreads, 1) k_mlp_f32tc(const __grid_constan
     tc::fence_before_sync();
     const double tot = block_sum(lsum);  // synchronises the CTA
     if (t == 0) {
-        partial[blockIdx.x] = tot;
+        if (!BWD) partial[blockIdx.x] = tot;
         if (bad) raise_error(err, 0x7C0A);
     }
     if (warp == 0) tc::tmem_dealloc(tmem, 64);
 }
-// The fused float32 MLP pass over n samples (one CTA per SM, persistent over 128-sample tiles).  Returns
-// false, launching nothing, when the model's shape is not handled here; otherwise *grid receives the
-// number of loss partials written (at most max_partials).
-bool launch_mlp_f32tc(fhash_model* m, const float* target, int64_t n, float* acts, float* dl, float* denc,
-                      double* partial, int max_partials, int* grid, cudaStream_t st, cudaError_t* err) {
+template <int IN, bool BWD>
+static cudaError_t launch_in(const MlpShape& sh, int g, int smem, const float* Pm, const float* target,
+                             const float* gyin, int64_t n, float* acts, float* dl, float* denc, double* partial,
+                             int* err, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute((const void*)k_mlp_f32tc<IN, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_mlp_f32tc<IN, BWD><<<g, kMthreads, smem, st>>>(sh, Pm, target, gyin, n, 2.0f / (float)n, acts, dl, denc, partial, err);
+    return cudaGetLastError();
+}
+
+// The fused float32 MLP pass over n samples (one CTA per SM, persistent over 128-sample tiles): forward,
+// loss and backward data path, or with gyin != nullptr the backward data path alone (the precision
+// form, whose forward kernel stored the activations and dL/dy = gyin).  Returns false, launching
+// nothing, when the model's shape is not handled here; otherwise *grid receives the number of CTAs
+// (the loss partials written by the full pass, at most max_partials).
+bool launch_mlp_f32tc(fhash_model* m, const float* target, const float* gyin, int64_t n, float* acts, float* dl,
+                      float* denc, double* partial, int max_partials, int* grid, cudaStream_t st, cudaError_t* err) {
     *err = cudaSuccess;
     const MlpShape& sh = m->mlp;
     if (sh.width != kMw || sh.nh < 1 || sh.nh > kTcMaxHidden || (sh.in != 16 && sh.in != 32 && sh.in != 64) ||
@@ -304,17 +333,15 @@ bool launch_mlp_f32tc(fhash_model* m, const float* target, int64_t n, float* act
     const int64_t ntiles = (n + kMt - 1) / kMt;
     const int g = (int)std::min<int64_t>(std::min<int64_t>(ntiles, num_sms()), max_partials);
     const float* Pm = m->param + m->n_table;
-    const float two_over_n = 2.0f / (float)n;
-    const void* fn = sh.in == 16 ? (const void*)k_mlp_f32tc<16> : sh.in == 32 ? (const void*)k_mlp_f32tc<32>
-                                                                             : (const void*)k_mlp_f32tc<64>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
-    if (e == cudaSuccess) {
-        switch (sh.in) {
-            case 16: k_mlp_f32tc<16><<<g, kMthreads, L.total, st>>>(sh, Pm, target, n, two_over_n, acts, dl, denc, partial, m->err_word); break;
-            case 32: k_mlp_f32tc<32><<<g, kMthreads, L.total, st>>>(sh, Pm, target, n, two_over_n, acts, dl, denc, partial, m->err_word); break;
-            default: k_mlp_f32tc<64><<<g, kMthreads, L.total, st>>>(sh, Pm, target, n, two_over_n, acts, dl, denc, partial, m->err_word); break;
-        }
-        e = cudaGetLastError();
+    const bool bwd = gyin != nullptr;
+    cudaError_t e;
+    switch (sh.in) {
+        case 16: e = bwd ? launch_in<16, true>(sh, g, L.total, Pm, target, gyin, n, acts, dl, denc, partial, m->err_word, st)
+                         : launch_in<16, false>(sh, g, L.total, Pm, target, gyin, n, acts, dl, denc, partial, m->err_word, st); break;
+        case 32: e = bwd ? launch_in<32, true>(sh, g, L.total, Pm, target, gyin, n, acts, dl, denc, partial, m->err_word, st)
+                         : launch_in<32, false>(sh, g, L.total, Pm, target, gyin, n, acts, dl, denc, partial, m->err_word, st); break;
+        default: e = bwd ? launch_in<64, true>(sh, g, L.total, Pm, target, gyin, n, acts, dl, denc, partial, m->err_word, st)
+                         : launch_in<64, false>(sh, g, L.total, Pm, target, gyin, n, acts, dl, denc, partial, m->err_word, st); break;
     }
     *grid = g;
     *err = e;

@@ -434,8 +434,8 @@ __global__ void k_loss2(const double* __restrict__ partial, int nb, int64_t n, d
 }
 
 cudaError_t run_tc_any(fhash_model* m, bool train, FusedArgs& a);
-bool launch_mlp_f32tc(fhash_model* m, const float* target, int64_t n, float* acts, float* dl, float* denc,
-                      double* partial, int max_partials, int* grid, cudaStream_t st, cudaError_t* err);
+bool launch_mlp_f32tc(fhash_model* m, const float* target, const float* gyin, int64_t n, float* acts, float* dl,
+                      float* denc, double* partial, int max_partials, int* grid, cudaStream_t st, cudaError_t* err);
 bool launch_dw_tc(fhash_model* m, const float* acts, const float* dl, int64_t n, float* wpart, size_t wpart_bytes,
                   int* nchunk_out, cudaStream_t st, cudaError_t* err, bool split3);
 
@@ -562,7 +562,7 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
         // shape allows; otherwise the float32 SIMT tile kernels
         int g = 0;
         cudaError_t e = cudaSuccess;
-        if (launch_mlp_f32tc(m, target, n, acts, dl, denc, lpart, nb, &g, st, &e)) {
+        if (launch_mlp_f32tc(m, target, nullptr, n, acts, dl, denc, lpart, nb, &g, st, &e)) {
             FH_CUDA(e);
             nb = g;
             fused_mlp = true;
@@ -576,6 +576,15 @@ fhash_status launch_grads2(fhash_model* m, const float* coords, const float* tar
     k_loss2<<<1, 256, 0, st>>>(lpart, nb, n, loss_dev);
     FH_CUDA(cudaGetLastError());
     // backward: MLP data path, table scatter, weight gradients
+    if (!fused_mlp && m->shadow) {
+        // precision form: the backward data path on the tensor cores from the stored activations and dL/dy
+        int g = 0;
+        cudaError_t e = cudaSuccess;
+        if (launch_mlp_f32tc(m, target, gy, n, acts, dl, denc, lpart, nb, &g, st, &e)) {
+            FH_CUDA(e);
+            fused_mlp = true;
+        }
+    }
     if (!fused_mlp) {
         const int bb = tile_grid;
         FH_CUDA(cudaFuncSetAttribute((const void*)k_mlp_bwd_t, cudaFuncAttributeMaxDynamicSharedMemorySize, tsmem));
