@@ -956,7 +956,8 @@ def main():
                         hbm_algorithmic_frac=phases[top]["frac"])
     value = job_rate(world, B * K, elapsed)
     deferred = adam_stats["first_deferred_level"] >= 0
-    per_step = (8 if not bf16 else 7) + (3 + 3 if deferred else 1)
+    # float32 without the fused tensor-core MLP: separate forward and backward MLP kernels
+    per_step = (7 if (bf16 or "k_mlp_f32tc" in kern) else 8) + (3 + 3 if deferred else 1)
 
     out = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -979,10 +980,11 @@ def main():
         "adam_deferral": {"replayed_groups_per_step": replay_groups, "replayed_group_steps_per_step": replay_steps,
                           "first_deferred_level": adam_stats["first_deferred_level"],
                           "deferred_params": n_deferred},
-        # per step, float32: encode, MLP forward, loss, MLP backward, 2 scatters; precision form: fused
-        # forward, loss, MLP backward, 2 scatters; both: the tensor-core weight gradients and their
-        # reduction; then the deferred catch-up (claim, sort, replay), the previous step's Adam over the
-        # dense ranges (2 launches) and the step's scalar record, or one dense Adam launch
+        # per step, float32: encode, the fused MLP (forward, loss and backward; other shapes: forward and
+        # backward apart), loss reduction, 2 scatters; precision form: fused forward, loss reduction, MLP
+        # backward, 2 scatters; both: the tensor-core weight gradients and their reduction; then the
+        # deferred catch-up (claim, sort, replay), the previous step's Adam over the dense ranges (2
+        # launches) and the step's scalar record, or one dense Adam launch
         "gpu_launches": K * per_step,
         "roofline": roofline,
         "clocks": clk,
