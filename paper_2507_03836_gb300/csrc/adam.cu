@@ -240,34 +240,52 @@ __global__ void __launch_bounds__(256) k_defer_claim(const __grid_constant__ Lev
         if (sh_hist[i]) atomicAdd(&d.ctr->hist[i], sh_hist[i]);
 }
 
-// Counting sort of the claim list by replay-length bucket (order inside a bucket is arbitrary).
+// Counting sort of the claim list by replay-length bucket (order inside a bucket is arbitrary).  A block
+// of 256 threads takes 256 kBinPer items, so few blocks contend for the 64 bucket cursors.
+constexpr int kBinPer = 8;
 __global__ void __launch_bounds__(256) k_defer_bin(const uint2* __restrict__ items, uint2* __restrict__ binned,
                                                    DeferCtr* __restrict__ ctr, uint32_t target) {
+    static_assert(kBuckets == 64, "the offset scan below takes two warps");
     __shared__ uint32_t off[kBuckets], loc[kBuckets], base[kBuckets];
+    __shared__ uint32_t w0;
     const uint32_t n = ctr->count;
-    if (blockIdx.x * blockDim.x >= n) return;  // the grid is sized for the largest possible list
-    if (threadIdx.x == 0) {
-        uint32_t t = 0;
-        for (int b = 0; b < kBuckets; ++b) {
-            off[b] = t;
-            t += ctr->hist[b];
+    const uint32_t i0 = blockIdx.x * (256u * kBinPer);
+    if (i0 >= n) return;  // the grid is sized for the largest possible list
+    // bucket offsets: exclusive prefix sum of the histogram, one bucket per thread of the first two warps
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < kBuckets) {
+        const uint32_t hv = ctr->hist[threadIdx.x];
+        uint32_t inc = hv;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
         }
+        off[threadIdx.x] = inc - hv;
+        loc[threadIdx.x] = 0;
+        if (threadIdx.x == 31) w0 = inc;
     }
-    for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) loc[b] = 0;
     __syncthreads();
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    uint2 it = make_uint2(0, 0);
-    uint32_t b = 0, r = 0;
-    const bool have = i < n;
-    if (have) {
-        it = items[i];
-        b = len_bucket(target - it.y);
-        r = atomicAdd(&loc[b], 1u);
+    if (threadIdx.x >= 32 && threadIdx.x < kBuckets) off[threadIdx.x] += w0;
+    uint2 it[kBinPer];
+    uint32_t bk[kBinPer], rk[kBinPer];
+#pragma unroll
+    for (int k = 0; k < kBinPer; ++k) {
+        const uint32_t i = i0 + k * 256u + threadIdx.x;
+        if (i < n) {
+            it[k] = items[i];
+            bk[k] = len_bucket(target - it[k].y);
+            rk[k] = atomicAdd(&loc[bk[k]], 1u);
+        }
     }
     __syncthreads();
     if (threadIdx.x < kBuckets && loc[threadIdx.x]) base[threadIdx.x] = atomicAdd(&ctr->cursor[threadIdx.x], loc[threadIdx.x]);
     __syncthreads();
-    if (have) binned[off[b] + base[b] + r] = it;
+#pragma unroll
+    for (int k = 0; k < kBinPer; ++k) {
+        const uint32_t i = i0 + k * 256u + threadIdx.x;
+        if (i < n) binned[off[bk[k]] + base[bk[k]] + rk[k]] = it[k];
+    }
 }
 
 // Replays steps from + 1 .. to of the 8 floats starting at float index f: the first with the
@@ -520,7 +538,7 @@ static fhash_status catch_up(fhash_model* m, const float* coords, int64_t n, cud
         default: return set_error(FHASH_EINVAL, "F=%d unsupported", m->lv.F);
     }
     FH_CUDA(cudaGetLastError());
-    k_defer_bin<<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(items, binned, ctr, target);
+    k_defer_bin<<<(unsigned)((cap + 256 * kBinPer - 1) / (256 * kBinPer)), 256, 0, st>>>(items, binned, ctr, target);
     FH_CUDA(cudaGetLastError());
     tev_record(m, TEV_CLAIM, st);
     if (m->dense_pending) {
