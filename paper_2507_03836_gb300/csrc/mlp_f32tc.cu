@@ -3,9 +3,9 @@
 // 3xTF32 split (hi*hi + hi*lo + lo*hi, Ootomo and Yokota 2022), so the results keep float32 accuracy.
 //
 // A tile's samples are the TMEM lanes.  Two threads share a sample: warps 0-3 take columns 0-31 of
-// its rows and warps 4-7 columns 32-63 (warp w reads TMEM lane quarter w % 4), so an accumulator row is
-// two threads' registers after tcgen05.ld, and 8 warps per SM hide the epilogues' latency.  Every GEMM has the samples as
-// M = 128 and K-major operands in the 128-byte swizzle layout:
+// its rows and warps 4-7 columns 32-63 (warp w reads TMEM lane quarter w % 4), so an accumulator row
+// is two threads' registers after tcgen05.ld, and 8 warps per SM hide the epilogues' latency.  Every
+// GEMM has the samples as M = 128 and K-major operands in the 128-byte swizzle layout:
 //   forward layer j:   z[s][o] = sum_c a[s][c] W_j[o][c]     A = activations, B = W_j as stored;
 //   backward layer j:  p[s][c] = sum_o d[s][o] W_j[o][c]     A = deltas,      B = W_j transposed.
 // The weights of every hidden layer, both ways and split into hi and lo, are staged once per CTA; the
@@ -15,6 +15,9 @@
 // outputs are the ones the split kernels write, feature-major [row][n] and coalesced across the
 // threads: the hidden activations (for the weight gradients), the deltas of every layer and
 // d(loss)/d(encoding) (for the table scatter), plus one loss partial per CTA.
+//
+// The precision (bf16) form runs its own forward kernel and uses the backward data path alone (the BWD
+// instantiation: masks from the stored activations).
 //
 // Shapes: encoding width IN in {16, 32, 64}, hidden width 64, up to kTcMaxHidden hidden layers (the
 // weights of both directions must fit in shared memory); others take the float32 SIMT kernels.
