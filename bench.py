@@ -974,9 +974,9 @@ def main():
                          "scatters reach it at random" % (16.0 * n_params / 1e9)},
         "phases_ms": {"catch_up_claim_sort": claim_ms, "catch_up_replay": replay_ms, "encode": encode_ms,
                       "mlp_fwd_loss_bwd": mlp_ms, "scatter": scatter_ms, "weight_grads": dw_ms,
-                      "adam_dense": dense_ms, "adam_scalars": tab_ms if overlapped else 0.0,
-                      "note": "adam_dense runs on a second stream beside catch_up_replay (not on the step's "
-                              "critical path)" if overlapped else "phases in sequence on one stream"},
+                      "adam_dense": dense_ms, "adam_scalars": tab_ms if overlapped else 0.0},
+        "phases_note": "adam_dense runs on a second stream beside catch_up_replay (not on the step's critical "
+                       "path)" if overlapped else "phases in sequence on one stream",
         "adam_deferral": {"replayed_groups_per_step": replay_groups, "replayed_group_steps_per_step": replay_steps,
                           "first_deferred_level": adam_stats["first_deferred_level"],
                           "deferred_params": n_deferred},
